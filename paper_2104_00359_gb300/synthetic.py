@@ -1,0 +1,232 @@
+"""Seeded synthetic scenes shaped like the paper's workloads.
+
+The paper evaluates on meshes, HDR environment maps and reference renders that
+are not distributed with it (Section 4, "Evaluation Dataset").  These
+generators stand in for them: every array is drawn from
+``numpy.random.default_rng(seed)`` in float64 and rounded to float32, so the
+CUDA path and the FP64 oracle consume bit-identical inputs.
+
+This module holds scene construction only (grids, capsule chains, height
+fields, random draws).  It contains none of the shading method's arithmetic:
+no spherical harmonics, no visibility, no exponentials.  It is the one module
+that both the oracle-based tests and the CUDA path import.
+
+Every generator returns a ``dict`` with float32 numpy arrays:
+
+* ``points``  [P, 3]  shading-point positions
+* ``normals`` [P, 3]  unit normals
+* ``albedo``  [P, 3]  diffuse albedo per colour channel
+* ``centers`` [N, 3]  sphere centres
+* ``radii``   [N]     sphere radii
+* ``light``   [3, K]  SH lighting per colour channel, K = n_bands**2
+* ``n_bands`` int
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "plane_grid_scene",
+    "capsule_body_scene",
+    "height_field_scene",
+    "random_scene",
+    "perturb_scene",
+    "sh_lighting",
+]
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).astype(np.float32))
+
+
+def sh_lighting(rng, n_bands, sigma=0.3, dc=1.0, band_decay=False):
+    """Per-channel SH lighting coefficients [3, K]: N(0, sigma) with the l=0
+    term set to ``dc``.  With ``band_decay`` the band-l coefficients are
+    divided by (l + 1)."""
+    K = n_bands * n_bands
+    L = rng.normal(0.0, sigma, size=(3, K))
+    if band_decay:
+        band = np.floor(np.sqrt(np.arange(K))).astype(np.int64)
+        L = L / (band + 1.0)[None, :]
+    L[:, 0] = dc
+    return L
+
+
+def plane_grid_scene(seed=0, grid=32, n_spheres=8, n_bands=4):
+    """Plane z=0 over [-1,1]^2 sampled at ``grid`` x ``grid`` pixel centres,
+    normals (0,0,1), albedo 0.5; sphere centres uniform in
+    [-0.8,0.8]^2 x [0.1,0.6], radii uniform in [0.05,0.2]; lighting N(0,0.3)
+    per channel with l=0 term 1.0.  Draw order: centres, radii, lighting."""
+    rng = np.random.default_rng(seed)
+    t = -1.0 + (2.0 * np.arange(grid) + 1.0) / grid
+    X, Y = np.meshgrid(t, t, indexing="xy")
+    P = grid * grid
+    points = np.stack([X.ravel(), Y.ravel(), np.zeros(P)], axis=1)
+    normals = np.tile([0.0, 0.0, 1.0], (P, 1))
+    albedo = np.full((P, 3), 0.5)
+    lo = np.array([-0.8, -0.8, 0.1])
+    hi = np.array([0.8, 0.8, 0.6])
+    centers = lo + (hi - lo) * rng.random((n_spheres, 3))
+    radii = rng.uniform(0.05, 0.2, size=n_spheres)
+    light = sh_lighting(rng, n_bands)
+    return dict(points=_f32(points), normals=_f32(normals), albedo=_f32(albedo),
+                centers=_f32(centers), radii=_f32(radii), light=_f32(light),
+                n_bands=n_bands)
+
+
+def _bone_chain(rng, n_bones, lo, hi, step=(0.12, 0.22)):
+    """Random-walk joint chain kept inside the box [lo, hi] by reflection."""
+    joints = [lo + (hi - lo) * (0.3 + 0.4 * rng.random(3))]
+    for _ in range(n_bones):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        nxt = joints[-1] + d * rng.uniform(*step)
+        nxt = np.where(nxt < lo, 2 * lo - nxt, nxt)
+        nxt = np.where(nxt > hi, 2 * hi - nxt, nxt)
+        joints.append(nxt)
+    return np.array(joints)
+
+
+def capsule_body_scene(seed=1, res=512, n_bones=20, spheres_per_bone=5,
+                       n_bands=4, capsule_samples=24):
+    """Human-scale G-buffer: an orthographic top-down ``res`` x ``res`` depth
+    map over [-1,1]^2 of a 20-bone random-walk chain of capsules whose joints
+    lie in a 2 m box and stay at least 0.15 above the ground plane z=0.
+
+    Each bone carries ``spheres_per_bone`` occluder spheres evenly spaced on
+    its axis (radii uniform in [0.02, 0.12]); the capsule radius is the
+    largest of them plus 0.01.  The capsule surface is taken as the union of
+    ``capsule_samples`` spheres of that radius along the axis, so each pixel's
+    first hit and unit normal are analytic ray-sphere results.  Pixels that
+    miss the body hit the ground plane (normal +z).  Albedo is uniform in
+    [0.2, 0.9] per channel.  Lighting: N(0,0.3), l=0 term 1.0.
+    """
+    rng = np.random.default_rng(seed)
+    lo = np.array([-0.85, -0.85, 0.15 + 0.13])
+    hi = np.array([0.85, 0.85, 1.6])
+    joints = _bone_chain(rng, n_bones, lo, hi)
+    ts = (np.arange(spheres_per_bone) + 0.5) / spheres_per_bone
+    centers, radii, cap_r = [], [], []
+    for b in range(n_bones):
+        a, e = joints[b], joints[b + 1]
+        r = rng.uniform(0.02, 0.12, size=spheres_per_bone)
+        for t, ri in zip(ts, r):
+            centers.append(a + t * (e - a))
+            radii.append(ri)
+        cap_r.append(r.max() + 0.01)
+    centers = np.array(centers)
+    radii = np.array(radii)
+
+    t = -1.0 + (2.0 * np.arange(res) + 1.0) / res
+    X, Y = np.meshgrid(t, t, indexing="xy")
+    X = X.ravel()
+    Y = Y.ravel()
+    P = X.size
+    zbest = np.zeros(P)
+    nrm = np.tile([0.0, 0.0, 1.0], (P, 1))
+    us = np.linspace(0.0, 1.0, capsule_samples)
+    for b in range(n_bones):
+        a, e, R = joints[b], joints[b + 1], cap_r[b]
+        for u in us:
+            c = a + u * (e - a)
+            h2 = R * R - (X - c[0]) ** 2 - (Y - c[1]) ** 2
+            hit = h2 > 0.0
+            z = np.where(hit, c[2] + np.sqrt(np.maximum(h2, 0.0)), -np.inf)
+            better = z > zbest
+            if better.any():
+                zbest = np.where(better, z, zbest)
+                idx = np.nonzero(better)[0]
+                nrm[idx, 0] = (X[idx] - c[0]) / R
+                nrm[idx, 1] = (Y[idx] - c[1]) / R
+                nrm[idx, 2] = (z[idx] - c[2]) / R
+    points = np.stack([X, Y, zbest], axis=1)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    albedo = rng.uniform(0.2, 0.9, size=(P, 3))
+    light = sh_lighting(rng, n_bands)
+    return dict(points=_f32(points), normals=_f32(nrm), albedo=_f32(albedo),
+                centers=_f32(centers), radii=_f32(radii), light=_f32(light),
+                n_bands=n_bands)
+
+
+def height_field_scene(seed=3, res=1024, n_spheres=300, n_bands=8, n_bumps=16):
+    """Height field z = h(x, y) over [-1,1]^2 on a ``res`` x ``res`` grid, h a
+    sum of ``n_bumps`` random Gaussian bumps, analytic unit normals; spheres
+    hover over the field at h + U[0.05, 0.8] with radii log-uniform in
+    [0.01, 0.2]; albedo uniform in [0.2, 0.9]; lighting N(0,0.3)/(l+1) with
+    l=0 term 1.0."""
+    rng = np.random.default_rng(seed)
+    amp = rng.uniform(-0.25, 0.25, n_bumps)
+    mu = rng.uniform(-1.0, 1.0, (n_bumps, 2))
+    sig = rng.uniform(0.1, 0.4, n_bumps)
+
+    def h_and_grad(x, y):
+        h = np.zeros_like(x)
+        hx = np.zeros_like(x)
+        hy = np.zeros_like(x)
+        for a, (mx, my), s in zip(amp, mu, sig):
+            g = a * np.exp(-((x - mx) ** 2 + (y - my) ** 2) / (2 * s * s))
+            h += g
+            hx += -g * (x - mx) / (s * s)
+            hy += -g * (y - my) / (s * s)
+        return h, hx, hy
+
+    t = -1.0 + (2.0 * np.arange(res) + 1.0) / res
+    X, Y = np.meshgrid(t, t, indexing="xy")
+    X = X.ravel()
+    Y = Y.ravel()
+    H, HX, HY = h_and_grad(X, Y)
+    points = np.stack([X, Y, H], axis=1)
+    nrm = np.stack([-HX, -HY, np.ones_like(H)], axis=1)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    albedo = rng.uniform(0.2, 0.9, size=(X.size, 3))
+    cxy = rng.uniform(-1.0, 1.0, (n_spheres, 2))
+    ch, _, _ = h_and_grad(cxy[:, 0], cxy[:, 1])
+    cz = ch + rng.uniform(0.05, 0.8, n_spheres)
+    centers = np.concatenate([cxy, cz[:, None]], axis=1)
+    radii = np.exp(rng.uniform(np.log(0.01), np.log(0.2), n_spheres))
+    light = sh_lighting(rng, n_bands, band_decay=True)
+    return dict(points=_f32(points), normals=_f32(nrm), albedo=_f32(albedo),
+                centers=_f32(centers), radii=_f32(radii), light=_f32(light),
+                n_bands=n_bands)
+
+
+def random_scene(seed, n_points, n_spheres, n_bands, box=1.0, r_range=(0.03, 0.25),
+                 inside_fraction=0.0):
+    """Points uniform in a cube of half-width ``box`` with random unit normals,
+    spheres uniform in the same cube.  ``inside_fraction`` of the points are
+    moved inside a random sphere (the clamped, point-inside-sphere case)."""
+    rng = np.random.default_rng(seed)
+    points = rng.uniform(-box, box, (n_points, 3))
+    normals = rng.normal(size=(n_points, 3))
+    normals /= np.linalg.norm(normals, axis=1, keepdims=True)
+    albedo = rng.uniform(0.2, 0.9, (n_points, 3))
+    centers = rng.uniform(-box, box, (n_spheres, 3))
+    radii = rng.uniform(*r_range, n_spheres)
+    if n_spheres > 0 and inside_fraction > 0:
+        m = rng.random(n_points) < inside_fraction
+        j = rng.integers(0, n_spheres, n_points)
+        d = rng.normal(size=(n_points, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        q = centers[j] + d * (radii[j] * rng.uniform(0.0, 0.9, n_points))[:, None]
+        points = np.where(m[:, None], q, points)
+    light = sh_lighting(rng, n_bands)
+    return dict(points=_f32(points), normals=_f32(normals), albedo=_f32(albedo),
+                centers=_f32(centers), radii=_f32(radii), light=_f32(light),
+                n_bands=n_bands)
+
+
+def perturb_scene(scene, seed, center_sigma=0.01, light_sigma=0.05,
+                  albedo_range=(0.9, 1.1)):
+    """Copy of ``scene`` with centres + N(0, center_sigma), lighting +
+    N(0, light_sigma) and albedo scaled by U[albedo_range]: the target of the
+    L2 analysis-by-synthesis loss."""
+    rng = np.random.default_rng(seed)
+    out = dict(scene)
+    out["centers"] = _f32(scene["centers"].astype(np.float64)
+                          + rng.normal(0, center_sigma, scene["centers"].shape))
+    out["light"] = _f32(scene["light"].astype(np.float64)
+                        + rng.normal(0, light_sigma, scene["light"].shape))
+    out["albedo"] = _f32(scene["albedo"].astype(np.float64)
+                         * rng.uniform(*albedo_range, scene["albedo"].shape))
+    return out

@@ -1,0 +1,401 @@
+"""Pins of the FP64 oracle against facts fixed outside it: textbook constants,
+closed forms, library routines with other definitions, quadrature of the
+paper's integrals, invariants, and brute force on tiny inputs.
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign or index, a transposed operand) fails it."""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import shs_oracle as O
+from paper_2104_00359_gb300 import synthetic as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "rh2001_constants.txt")
+
+
+def _golden(kind):
+    out = {}
+    with open(GOLDEN) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, i, v = line.split()[:3]
+            if k == kind:
+                out[int(i)] = float(v)
+    return out
+
+
+def _rand_dirs(rng, n):
+    d = rng.normal(size=(n, 3))
+    return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def _scipy_real_sh(n_bands, dirs):
+    """Real SH from scipy's complex Y_l^m (which carries the Condon-Shortley
+    phase (-1)^m): y_l,+m = sqrt2 (-1)^m Re Y_l^m, y_l,-m = sqrt2 (-1)^m Im Y_l^m."""
+    from scipy.special import sph_harm_y
+    theta = np.arccos(np.clip(dirs[:, 2], -1, 1))
+    phi = np.mod(np.arctan2(dirs[:, 1], dirs[:, 0]), 2 * np.pi)
+    out = np.zeros((dirs.shape[0], n_bands * n_bands))
+    for l in range(n_bands):
+        for m in range(l + 1):
+            Y = sph_harm_y(l, m, theta, phi)
+            if m == 0:
+                out[:, l * l + l] = Y.real
+            else:
+                out[:, l * l + l + m] = math.sqrt(2) * (-1) ** m * Y.real
+                out[:, l * l + l - m] = math.sqrt(2) * (-1) ** m * Y.imag
+    return out
+
+
+# --------------------------------------------------------------------------- O1
+
+def test_sh_textbook_constants():
+    """Ramamoorthi & Hanrahan 2001, Eq. 3 (tests/golden/rh2001_constants.txt)."""
+    g = _golden("sh")
+    rng = np.random.default_rng(10)
+    d = _rand_dirs(rng, 50)
+    x, y, z = d[:, 0], d[:, 1], d[:, 2]
+    poly = [np.ones_like(x), y, z, x, x * y, y * z, 3 * z * z - 1, x * z, x * x - y * y]
+    Y = O.real_sh(3, d)
+    for i in range(9):
+        np.testing.assert_allclose(Y[:, i], g[i] * poly[i], rtol=2e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_sh_matches_scipy(n):
+    rng = np.random.default_rng(11)
+    d = _rand_dirs(rng, 200)
+    np.testing.assert_allclose(O.real_sh(n, d), _scipy_real_sh(n, d), atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_sh_orthonormal(n):
+    dirs, w = O.sphere_quadrature(n + 2, 2 * n + 4)
+    Y = O.real_sh(n, dirs)
+    G = (Y * w[:, None]).T @ Y
+    np.testing.assert_allclose(G, np.eye(n * n), atol=1e-13)
+
+
+def test_sh_addition_theorem():
+    """sum_m y_lm(a) y_lm(b) = (2l+1)/(4 pi) P_l(a.b)."""
+    from numpy.polynomial import legendre as leg
+    rng = np.random.default_rng(12)
+    a = _rand_dirs(rng, 40)
+    b = _rand_dirs(rng, 40)
+    Ya, Yb = O.real_sh(8, a), O.real_sh(8, b)
+    cosg = np.sum(a * b, axis=1)
+    for l in range(8):
+        sl = slice(l * l, (l + 1) * (l + 1))
+        lhs = np.sum(Ya[:, sl] * Yb[:, sl], axis=1)
+        rhs = (2 * l + 1) / (4 * np.pi) * leg.legval(cosg, np.eye(l + 1)[l])
+        np.testing.assert_allclose(lhs, rhs, atol=1e-12)
+
+
+def test_sh_gradient_fd():
+    rng = np.random.default_rng(13)
+    d = _rand_dirs(rng, 30)
+    G = O.real_sh_grad(8, d)
+    h = 1e-6
+    for c in range(3):
+        e = np.zeros(3)
+        e[c] = h
+        fd = (O.real_sh(8, d + e) - O.real_sh(8, d - e)) / (2 * h)
+        np.testing.assert_allclose(G[:, :, c], fd, atol=1e-7)
+
+
+# --------------------------------------------------------------------------- O2
+
+@pytest.mark.parametrize("n", [4, 6, 8])
+def test_gaunt_structure(n):
+    C = O.gaunt_tensor(n)
+    K = n * n
+    np.testing.assert_allclose(C[0], np.eye(K) / math.sqrt(4 * math.pi), atol=1e-14)
+    np.testing.assert_allclose(C, C.transpose(0, 2, 1), atol=1e-14)
+    np.testing.assert_allclose(C, C.transpose(1, 0, 2), atol=1e-14)
+    lb = O.band_of(K)
+    li, lj, lk = np.meshgrid(lb, lb, lb, indexing="ij")
+    forbidden = ((li + lj + lk) % 2 == 1) | (li > lj + lk) | (lj > li + lk) | (lk > li + lj)
+    assert np.all(C[forbidden] == 0.0)
+
+
+def test_gaunt_pointwise_product():
+    """For band limits la + lb <= n-1, sum_i (a*b)_i y_i(w) = a~(w) b~(w) exactly
+    at arbitrary directions: pins every C_ijk with l_j <= 3, l_k <= 4 (n=8)."""
+    n = 8
+    C = O.gaunt_tensor(n)
+    rng = np.random.default_rng(14)
+    a = np.zeros(64)
+    a[:16] = rng.normal(size=16)
+    b = np.zeros(64)
+    b[:25] = rng.normal(size=25)
+    ab = O.sh_product(C, a, b)
+    d = _rand_dirs(rng, 100)
+    Y = _scipy_real_sh(n, d)
+    np.testing.assert_allclose(Y @ ab, (Y @ a) * (Y @ b), atol=1e-11)
+
+
+def test_gaunt_matches_sympy_real_gaunt():
+    """Against sympy's closed-form real Gaunt coefficients (Wigner-3j route,
+    Homeier's real basis: no Condon-Shortley phase, m < 0 <-> sin, the same
+    basis as the oracle): every entry for n = 3, a random sample for n = 5."""
+    pytest.importorskip("sympy")
+    from sympy.physics.wigner import real_gaunt
+    rng = np.random.default_rng(15)
+    for n, count in ((3, None), (5, 500)):
+        K = n * n
+        lm = [(l, m) for l in range(n) for m in range(-l, l + 1)]
+        C = O.gaunt_tensor(n)
+        idx = [(i, j, k) for i in range(K) for j in range(K) for k in range(K)]
+        sel = range(len(idx)) if count is None else rng.choice(len(idx), count, replace=False)
+        for s in sel:
+            i, j, k = idx[s]
+            ref = float(real_gaunt(lm[i][0], lm[j][0], lm[k][0], lm[i][1], lm[j][1], lm[k][1]))
+            assert abs(C[i, j, k] - ref) < 1e-13, (lm[i], lm[j], lm[k])
+
+
+# --------------------------------------------------------------------------- O3
+
+def test_cosine_zh_closed_form():
+    """A_hat_l = sqrt(4pi/(2l+1)) h_l: pi, 2pi/3, pi/4, 0, -pi/24, 0, pi/64, 0
+    (Ramamoorthi & Hanrahan 2001, Eq. 8-9)."""
+    A = O.zh_rotation_scale(8)[[0, 1, 4, 9, 16, 25, 36, 49]] * O.clamped_cosine_zh(8)
+    ref = np.array([np.pi, 2 * np.pi / 3, np.pi / 4, 0, -np.pi / 24, 0, np.pi / 64, 0])
+    np.testing.assert_allclose(A, ref, atol=1e-14)
+    g = _golden("ahat")
+    for l, v in g.items():
+        assert abs(A[l] - v) < 1e-6
+
+
+def test_cosine_lobe_projection():
+    """H(n) equals the projection of max(n . w, 0) (Eq. 10) by fine quadrature."""
+    rng = np.random.default_rng(16)
+    nrm = _rand_dirs(rng, 3)
+    H = O.cosine_lobe(6, nrm)
+    dirs, w = O.sphere_quadrature(600, 1200)
+    Y = _scipy_real_sh(6, dirs)
+    for p in range(3):
+        proj = (w * np.maximum(dirs @ nrm[p], 0.0)) @ Y
+        np.testing.assert_allclose(H[p], proj, atol=2e-5)
+
+
+# --------------------------------------------------------------------------- O4
+
+def test_log_cap_dc_is_cap_solid_angle():
+    """g_0 = -eps * Omega_cap / sqrt(4 pi), Omega_cap = 2 pi (1 - cos alpha)."""
+    ca = np.linspace(0.0, 1.0, 11)
+    zh = O.log_cap_zh(4, 3.0, ca)
+    np.testing.assert_allclose(zh[:, 0], -3.0 * 2 * np.pi * (1 - ca) / math.sqrt(4 * np.pi), atol=1e-14)
+
+
+def test_log_cap_rotated_projection():
+    """Per-sphere log-visibility F_j equals the projection of -eps 1[w.s >= cos a]
+    computed by brute-force quadrature in world directions (no rotation used)."""
+    cfg = O.Config(n_bands=5, epsilon=3.0)
+    pts = np.array([[0.1, -0.2, 0.05], [0.0, 0.0, 0.0]])
+    ctr = np.array([0.4, 0.3, 0.6])
+    r = 0.35
+    f = O.log_visibility(cfg, pts, ctr[None], np.array([r]))
+    dirs, w = O.sphere_quadrature(1500, 3000)
+    Y = _scipy_real_sh(5, dirs)
+    for p in range(2):
+        d = ctr - pts[p]
+        D = np.linalg.norm(d)
+        ca = math.sqrt(1 - (r / D) ** 2)
+        ind = -3.0 * (dirs @ (d / D) >= ca)
+        np.testing.assert_allclose(f[p], (w * ind) @ Y, atol=3e-3)
+
+
+def test_point_inside_sphere_is_hemisphere():
+    """Reading: D <= r clamps the cap to a hemisphere toward the centre."""
+    cfg = O.Config(n_bands=4)
+    pts = np.array([[0.0, 0.0, 0.0]])
+    f_in = O.log_visibility(cfg, pts, np.array([[0.0, 0.0, 0.1]]), np.array([0.3]))
+    f_on = O.log_visibility(cfg, pts, np.array([[0.0, 0.0, 0.3]]), np.array([0.3]))
+    np.testing.assert_allclose(f_in, f_on, atol=1e-14)
+    assert abs(f_in[0, 0] - (-3.0 * 2 * np.pi / math.sqrt(4 * np.pi))) < 1e-13
+
+
+def test_log_visibility_sphere_order_invariant():
+    sc = S.random_scene(17, 20, 6, 4)
+    cfg = O.Config(n_bands=4)
+    perm = np.random.default_rng(0).permutation(6)
+    a = O.log_visibility(cfg, sc["points"].astype(float), sc["centers"].astype(float), sc["radii"].astype(float))
+    b = O.log_visibility(cfg, sc["points"].astype(float), sc["centers"][perm].astype(float), sc["radii"][perm].astype(float))
+    np.testing.assert_allclose(a, b, atol=1e-13)
+
+
+# --------------------------------------------------------------------------- O6
+
+def test_exp_of_constant_is_exact():
+    cfg = O.Config(n_bands=4)
+    C = O.gaunt_tensor(4)
+    f = np.zeros((3, 16))
+    f[:, 0] = [-2.0, 0.0, 1.5]
+    V, _ = O.sh_exp(cfg, C, f)
+    ref = np.zeros((3, 16))
+    ref[:, 0] = np.exp(f[:, 0] / math.sqrt(4 * np.pi)) * math.sqrt(4 * np.pi)
+    np.testing.assert_allclose(V, ref, rtol=1e-15, atol=1e-15)
+
+
+def test_exp_scaling_rule():
+    cfg = O.Config(n_bands=2, exp_tau=1.0, exp_kmax=5)
+    f = np.zeros((6, 4))
+    f[:, 1] = [0.0, 0.5, 1.0, 1.01, 4.0, 100.0]
+    assert list(O.exp_scaling_k(cfg, f)) == [0, 0, 0, 1, 2, 5]
+
+
+def test_optimal_linear_approximation_is_gaussian_least_squares():
+    """a = b = exp(s^2/2) minimise E[(e^X - a - b X)^2] for X ~ N(0, s^2)
+    (Gauss-Hermite least squares), with s^2 = |g|^2 / (4 pi) the mean square of
+    g over the sphere -- the reading of Ren et al.'s optimal linear step."""
+    from numpy.polynomial.hermite_e import hermegauss
+    t, w = hermegauss(60)
+    w = w / w.sum()
+    cfg = O.Config(n_bands=3, fixed_k=0)
+    C = O.gaunt_tensor(3)
+    g = np.zeros((1, 9))
+    g[0, 1:] = np.random.default_rng(18).normal(0, 0.3, 8)
+    V, ex = O.sh_exp(cfg, C, g)
+    s2 = np.sum(g * g) / (4 * np.pi)
+    X = t * math.sqrt(s2)
+    A = np.stack([np.ones_like(X), X], axis=1) * np.sqrt(w)[:, None]
+    coef = np.linalg.lstsq(A, np.exp(X) * np.sqrt(w), rcond=None)[0]
+    np.testing.assert_allclose(V[0, 0] / math.sqrt(4 * np.pi), coef[0], rtol=1e-12)
+    np.testing.assert_allclose(V[0, 1:], coef[1] * g[0, 1:], rtol=1e-12)
+
+
+def test_exp_converges_to_projected_exponential():
+    """With many squarings the result converges to the SH projection of
+    exp(f~(w)); for a low-band f and n = 8 the low bands match quadrature."""
+    n = 8
+    cfg = O.Config(n_bands=n, fixed_k=14)
+    C = O.gaunt_tensor(n)
+    rng = np.random.default_rng(19)
+    f = np.zeros((1, 64))
+    f[0, :4] = rng.normal(0, 0.5, 4)
+    V, _ = O.sh_exp(cfg, C, f)
+    dirs, w = O.sphere_quadrature(60, 120)
+    Y = _scipy_real_sh(n, dirs)
+    ref = (w * np.exp(Y @ f[0])) @ Y
+    np.testing.assert_allclose(V[0, :9], ref[:9], atol=2e-4)
+
+
+# --------------------------------------------------------------------------- O7
+
+def test_shading_equals_triple_integral():
+    """B = a (L . (V*H)) equals a * int L~ V~ H~ dw (Eq. 2 with band-limited
+    factors), evaluated by quadrature without C."""
+    sc = S.random_scene(20, 12, 5, 4)
+    cfg = O.Config(n_bands=4)
+    fw = O.shade_forward(cfg, **{k: sc[k] for k in ("points", "normals", "albedo", "centers", "radii", "light")})
+    dirs, w = O.sphere_quadrature(10, 20)
+    Y = _scipy_real_sh(4, dirs)
+    L = sc["light"].astype(float)
+    for p in range(12):
+        integ = (w * (Y @ fw["V"][p]) * (Y @ fw["H"][p]))[None, :] * (L @ Y.T)
+        ref = sc["albedo"][p].astype(float) * integ.sum(axis=1)
+        np.testing.assert_allclose(fw["radiance"][p], ref, rtol=1e-12, atol=1e-13)
+
+
+def test_unoccluded_closed_form():
+    """No spheres: B_c = a_c sum_lm A_hat_l L_c,lm y_lm(n) (irradiance formula,
+    Ramamoorthi & Hanrahan 2001), independent of C and of the exp step."""
+    sc = S.random_scene(21, 50, 0, 4)
+    cfg = O.Config(n_bands=4)
+    fw = O.shade_forward(cfg, sc["points"], sc["normals"], sc["albedo"], np.zeros((0, 3)),
+                         np.zeros(0), sc["light"])
+    Ahat = np.array([np.pi, 2 * np.pi / 3, np.pi / 4, 0.0])[O.band_of(16)]
+    nrm = sc["normals"].astype(float)
+    Y = _scipy_real_sh(4, nrm / np.linalg.norm(nrm, axis=1, keepdims=True))
+    ref = sc["albedo"].astype(float) * ((Y * Ahat) @ sc["light"].astype(float).T)
+    np.testing.assert_allclose(fw["radiance"], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_single_sphere_on_axis_constant_light():
+    """Sphere straight above the normal, constant radiance l: the ideal
+    soft-blocker integral is a l pi (1 - (1 - e^-eps) sin^2 alpha).  The SH
+    method approximates it within its band limit (report; loose gate)."""
+    for n in (4, 8):
+        cfg = O.Config(n_bands=n)
+        K = n * n
+        light = np.zeros((3, K))
+        light[:, 0] = math.sqrt(4 * np.pi)
+        for sin_a in (0.2, 0.35, 0.5, 0.7):
+            ctr = np.array([[0.0, 0.0, 1.0]])
+            fw = O.shade_forward(cfg, np.zeros((1, 3)), np.array([[0.0, 0.0, 1.0]]),
+                                 np.ones((1, 3)), ctr, np.array([sin_a]), light)
+            ideal = np.pi * (1 - (1 - math.exp(-3.0)) * sin_a ** 2)
+            err = abs(fw["radiance"][0, 0] - ideal) / ideal
+            # measured: n=4 up to 17 %, n=8 up to 4 % (band limit + exp reading)
+            assert err < (0.2 if n == 4 else 0.08), (n, sin_a, err)
+
+
+def test_rotation_equivariance():
+    """Rotating points, normals and spheres and SH-rotating the lighting leaves
+    B unchanged (every step is rotation-covariant; OL depends on |g| only)."""
+    from scipy.spatial.transform import Rotation
+    n = 4
+    sc = S.random_scene(22, 15, 5, n)
+    cfg = O.Config(n_bands=n)
+    R = Rotation.random(random_state=3).as_matrix()
+    dirs, w = O.sphere_quadrature(n + 2, 2 * n + 4)
+    M = (O.real_sh(n, dirs) * w[:, None]).T @ O.real_sh(n, dirs @ R)   # L'(w) = L(R^T w)
+    a = O.shade_forward(cfg, sc["points"], sc["normals"], sc["albedo"], sc["centers"], sc["radii"], sc["light"])
+    b = O.shade_forward(cfg, sc["points"].astype(float) @ R.T, sc["normals"].astype(float) @ R.T,
+                        sc["albedo"], sc["centers"].astype(float) @ R.T, sc["radii"],
+                        sc["light"].astype(float) @ M.T, k=a["k"])
+    np.testing.assert_allclose(b["radiance"], a["radiance"], rtol=1e-10, atol=1e-12)
+
+
+def test_linearity_in_light_and_albedo():
+    sc = S.random_scene(23, 10, 4, 4)
+    cfg = O.Config(n_bands=4)
+    args = [sc[k] for k in ("points", "normals", "albedo", "centers", "radii")]
+    L1 = sc["light"].astype(float)
+    L2 = np.random.default_rng(1).normal(size=L1.shape)
+    B1 = O.shade_forward(cfg, *args, L1)["radiance"]
+    B2 = O.shade_forward(cfg, *args, L2)["radiance"]
+    B12 = O.shade_forward(cfg, *args, 2 * L1 - 0.5 * L2)["radiance"]
+    np.testing.assert_allclose(B12, 2 * B1 - 0.5 * B2, atol=1e-12)
+    args2 = list(args)
+    args2[2] = 3 * sc["albedo"].astype(float)
+    np.testing.assert_allclose(O.shade_forward(cfg, *args2, L1)["radiance"], 3 * B1, atol=1e-12)
+
+
+def test_monte_carlo_brute_force_report():
+    """Eq. 2 by Monte Carlo with the softened blocker (Eq. 13) on a few plane
+    points of the 32x32 scene: the SH result tracks it within its band limit."""
+    sc = S.plane_grid_scene()
+    cfg = O.Config(n_bands=4)
+    sel = np.arange(0, 1024, 97)
+    fw = O.shade_forward(cfg, sc["points"][sel], sc["normals"][sel], sc["albedo"][sel],
+                         sc["centers"], sc["radii"], sc["light"])
+    rng = np.random.default_rng(24)
+    nsamp = 200_000
+    dirs = _rand_dirs(rng, nsamp)
+    Y = _scipy_real_sh(4, dirs)
+    Lw = Y @ sc["light"].astype(float).T                      # [S, 3]
+    ctr = sc["centers"].astype(float)
+    rad = sc["radii"].astype(float)
+    errs = []
+    for p, idx in enumerate(sel):
+        x = sc["points"][idx].astype(float)
+        nrm = sc["normals"][idx].astype(float)
+        logv = np.zeros(nsamp)
+        for c, r in zip(ctr, rad):
+            d = c - x
+            D = np.linalg.norm(d)
+            ca = math.sqrt(max(1 - (r / D) ** 2, 0.0)) if D > r else 0.0
+            logv -= 3.0 * (dirs @ (d / D) >= ca)
+        integrand = Lw * (np.exp(logv) * np.maximum(dirs @ nrm, 0.0))[:, None]
+        mc = sc["albedo"][idx].astype(float) * integrand.mean(axis=0) * 4 * np.pi
+        errs.append(np.max(np.abs(mc - fw["radiance"][p]) / np.abs(mc).max()))
+    # Band-limit error of the method itself, not parity: measured mean ~0.1,
+    # worst ~0.38 (a point inside a sphere, hemisphere cap at n = 4).
+    print("MC relative errors:", np.round(errs, 3))
+    assert np.mean(errs) < 0.2 and max(errs) < 0.5, errs
