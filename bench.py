@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark: shaded point-sphere pairs per second, forward + backward.
+
+Workload: the human-scale G-buffer -- 512 x 512 shading points from a
+synthetic capsule-body depth map, 100 occluder spheres, 16 SH coefficients
+(n = 4 bands) x 3 colour channels.  One step is one analysis-by-synthesis
+pass of the whole shading path: the forward shading (per-pair log-visibility,
+SH exponential, cosine lobe, triple product, lighting) followed by the L2 loss
+against a perturbed target render and the adjoint pass (gradients for
+lighting, albedo, sphere centres and radii).  Units: P x N pairs per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 oracle on the host cores instead (a
+deliberately slow baseline, bounded sample of the same workload).
+Under torchrun each rank shades its own copy of the workload (weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+# The oracle baseline is timed single-threaded; pin BLAS pools before numpy loads.
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "shaded point-sphere pairs/sec fwd+bwd (512², 100 spheres, 16 SH coeffs); p50/p99 latency"
+WORKLOAD = "capsule-body G-buffer 512x512 points, 100 spheres, n_bands=4 (16 SH coeffs x 3 ch), fwd + L2 loss + bwd"
+N_BANDS = 4
+SMS = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def gaunt_nnz(n):
+    """(nnz of C_ijk, nnz over j <= k) for n bands -- for the flop model."""
+    sys.path.insert(0, os.path.join(ROOT, "paper_2104_00359_gb300", "csrc"))
+    try:
+        import gen_tables
+        g = gen_tables.gaunt_monomial(n)
+    finally:
+        sys.path.pop(0)
+    nnz_sym = len(g)
+    nnz = sum(1 if j == k else 2 for (_, j, k) in g)
+    return nnz, nnz_sym
+
+
+def flop_model(n, n_spheres, k_mean):
+    """Algorithmic FP32 flops per shading point (stated in the design doc):
+    pair terms 4n^2+5n+14 (fwd) and 9n^2+10n+50 (bwd) per sphere; tails
+    2 nnz_sym k + 2 nnz + 10K (fwd) and 2 nnz_sym k + 2 nnz k + 6 nnz + 18K (bwd)."""
+    K = n * n
+    nnz, nnz_sym = gaunt_nnz(n)
+    pf = 4 * n * n + 5 * n + 14
+    pb = 9 * n * n + 10 * n + 50
+    tf = 2 * nnz_sym * k_mean + 2 * nnz + 10 * K
+    tb = 2 * nnz_sym * k_mean + 2 * nnz * k_mean + 6 * nnz + 18 * K
+    return dict(fwd=n_spheres * pf + tf, bwd=n_spheres * pb + tb)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def bench_ours(args, world, rank, local, dist):
+    import torch
+    from paper_2104_00359_gb300 import Config, Scene, synthetic, _lib
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = _lib.load()
+    sc = synthetic.capsule_body_scene(seed=1 + 1000 * rank, n_bands=N_BANDS)
+    tgt_sc = synthetic.perturb_scene(sc, seed=2 + 1000 * rank)
+    P = sc["points"].shape[0]
+    Nsph = sc["centers"].shape[0]
+    T = {k: torch.from_numpy(sc[k]).to(dev) for k in ("points", "normals", "albedo", "centers", "radii", "light")}
+    cfg = Config(n_bands=N_BANDS, deterministic=not args.atomic)
+    # target render with the perturbed scene through the same library
+    tscene = Scene(torch.from_numpy(tgt_sc["centers"]).to(dev), torch.from_numpy(tgt_sc["radii"]).to(dev),
+                   torch.from_numpy(tgt_sc["light"]).to(dev), cfg)
+    target = tscene.shade(T["points"], T["normals"], torch.from_numpy(tgt_sc["albedo"]).to(dev))
+    torch.cuda.synchronize()
+    tscene.close()
+
+    scene = Scene(T["centers"], T["radii"], T["light"], cfg)
+    saved = scene.new_saved(P, dev)
+    radiance = torch.empty((P, 3), device=dev)
+    want = ("light", "albedo", "centers", "radii")
+    g = scene._grad_buffers(P, dev, want)
+    loss = torch.empty((), device=dev)
+    stream = torch.cuda.current_stream()
+    sp = _lib.ptr
+    sptr = _lib.ctypes.c_void_p(stream.cuda_stream)
+
+    def step():
+        _lib.check(lib.shs_shade(scene.handle, P, sp(T["points"]), sp(T["normals"]), sp(T["albedo"]),
+                                 sp(radiance), sp(saved), sptr), "shs_shade")
+        ev_mid.record(stream)
+        _lib.check(lib.shs_shade_backward_l2(scene.handle, P, sp(T["points"]), sp(T["normals"]),
+                                             sp(T["albedo"]), sp(saved), sp(radiance), sp(target), sp(loss),
+                                             sp(g["d_light"]), sp(g["d_albedo"]), sp(g["d_centers"]),
+                                             sp(g["d_radii"]), None, None, sptr), "shs_shade_backward_l2")
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    W, K = args.warmup, args.steps
+    ev_mid = torch.cuda.Event(enable_timing=True)
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = lib.shs_launch_count()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for i in range(K):
+            flush.zero_()
+            starts[i].record(stream)
+            ev_mid = mids[i]
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+    launches = lib.shs_launch_count() - launches0
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    fwd_ms = [s.elapsed_time(m) for s, m in zip(starts, mids)]
+    bwd_ms = [m.elapsed_time(e) for m, e in zip(mids, ends)]
+    mean_ms = statistics.fmean(step_ms)
+    if dist:
+        t = torch.tensor([mean_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mean_ms = float(t.item())
+    pairs = P * Nsph
+    value = world * pairs / (mean_ms * 1e-3)
+    kvals = scene.saved_views(saved, P)[1].float()
+    k_mean = float(kvals.mean())
+    fm = flop_model(N_BANDS, Nsph, k_mean)
+    bwd_mean = statistics.fmean(bwd_ms)
+    fwd_mean = statistics.fmean(fwd_ms)
+    peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = P * fm["bwd"] / (bwd_mean * 1e-3) / 1e12
+    achieved_fwd = P * fm["fwd"] / (fwd_mean * 1e-3) / 1e12
+    srt = sorted(step_ms)
+    p50 = srt[len(srt) // 2]
+    p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
+
+    # end to end through the public API with pinned host buffers
+    host = {k: torch.from_numpy(sc[k]).pin_memory() for k in ("points", "normals", "albedo")}
+    host_tgt = target.cpu().pin_memory()
+    out_h = {k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in g.items() if v is not None}
+    loss_h = torch.empty((), dtype=torch.float32).pin_memory()
+    dbuf = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    dtgt = torch.empty_like(target)
+
+    def e2e_step():
+        for k in host:
+            dbuf[k].copy_(host[k], non_blocking=True)
+        dtgt.copy_(host_tgt, non_blocking=True)
+        _lib.check(lib.shs_shade(scene.handle, P, sp(dbuf["points"]), sp(dbuf["normals"]), sp(dbuf["albedo"]),
+                                 sp(radiance), sp(saved), sptr), "shs_shade")
+        _lib.check(lib.shs_shade_backward_l2(scene.handle, P, sp(dbuf["points"]), sp(dbuf["normals"]),
+                                             sp(dbuf["albedo"]), sp(saved), sp(radiance), sp(dtgt), sp(loss),
+                                             sp(g["d_light"]), sp(g["d_albedo"]), sp(g["d_centers"]),
+                                             sp(g["d_radii"]), None, None, sptr), "shs_shade_backward_l2")
+        for k, v in out_h.items():
+            v.copy_(g[k], non_blocking=True)
+        loss_h.copy_(loss, non_blocking=True)
+        stream.synchronize()
+
+    KE = max(3, min(K, 200))
+    for _ in range(3):
+        e2e_step()
+    if dist:
+        dist.barrier()
+    te0 = time.perf_counter()
+    for _ in range(KE):
+        e2e_step()
+    te1 = time.perf_counter()
+    e2e_s = (te1 - te0) / KE
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = sum(v.numel() * 4 for v in host.values()) + host_tgt.numel() * 4
+    d2h = sum(v.numel() * 4 for v in out_h.values()) + 4
+    status = scene.device_status()
+    scene.close()
+    peaks = load_peaks()
+    return dict(
+        metric=METRIC, value=value, unit="pairs/s", n_gpus=world, steps=K, warmup=W,
+        ms_per_step=mean_ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+        data="synthetic", impl="ours",
+        config={"workload": WORKLOAD, "points": P, "spheres": Nsph, "sh_coeffs": N_BANDS ** 2,
+                "pairs_per_step": pairs, "l2_flush_between_steps": True,
+                "deterministic_reduction": not args.atomic, "parallelism": f"replicas{world}"},
+        latency_ms={"p50": p50, "p99": p99, "fwd_mean": fwd_mean, "bwd_mean": bwd_mean},
+        roofline={"bound": "alu", "kernel": "backward (pair adjoints + tail adjoint)",
+                  "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                  "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                  "flops_per_point": fm["bwd"], "k_mean": k_mean,
+                  "forward": {"achieved": achieved_fwd, "frac": achieved_fwd / peak,
+                              "flops_per_point": fm["fwd"]}},
+        e2e={"value": world * pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+             "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
+        gpu_launches=int(launches), clocks=clk.summary(), device_status=status,
+        wall_s_timed=t1 - t0, hbm_peak_gbs=peaks.get("hbm_gbs"),
+        cpu_baseline=cpu_baseline(args) if (rank == 0 and world == 1 and not args.no_cpu) else None,
+    )
+
+
+def _oracle_step(O, cfg, sc, idx, dB_seed=0):
+    args = [sc[k][idx] for k in ("points", "normals", "albedo")] + [sc["centers"], sc["radii"], sc["light"]]
+    fw = O.shade_forward(cfg, *args)
+    dB = np.random.default_rng(dB_seed).normal(size=(len(idx), 3))
+    O.shade_backward(cfg, *args, dB)
+    return fw
+
+
+def cpu_baseline(args, budget_s=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    from oracle import shs_oracle as O
+    from paper_2104_00359_gb300 import synthetic
+    sc = synthetic.capsule_body_scene(seed=1, n_bands=N_BANDS)
+    cfg = O.Config(n_bands=N_BANDS)
+    rng = np.random.default_rng(0)
+    t = time.perf_counter()
+    _oracle_step(O, cfg, sc, rng.choice(sc["points"].shape[0], 256, replace=False))
+    per_pt = (time.perf_counter() - t) / 256
+    n = int(max(256, min(16384, budget_s / per_pt)))
+    idx = rng.choice(sc["points"].shape[0], n, replace=False)
+    t = time.perf_counter()
+    _oracle_step(O, cfg, sc, idx)
+    dt = time.perf_counter() - t
+    pairs = n * sc["centers"].shape[0]
+    return {"value": pairs / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} random points of the 512x512 capsule-body G-buffer x 100 spheres, "
+                      f"fwd + bwd, float64 numpy, 1 thread, {dt:.1f} s"}
+
+
+def bench_reference(args, world, rank):
+    """The oracle as the reference arm: same metric and workload, bounded
+    per-step samples so K + W steps end within a couple of minutes."""
+    if rank != 0:
+        return None
+    from oracle import shs_oracle as O
+    from paper_2104_00359_gb300 import synthetic
+    sc = synthetic.capsule_body_scene(seed=1, n_bands=N_BANDS)
+    cfg = O.Config(n_bands=N_BANDS)
+    rng = np.random.default_rng(0)
+    t = time.perf_counter()
+    _oracle_step(O, cfg, sc, rng.choice(sc["points"].shape[0], 128, replace=False))
+    per_pt = (time.perf_counter() - t) / 128
+    total_budget = 90.0
+    n = int(max(1, min(4096, total_budget / max(1, args.steps + args.warmup) / per_pt)))
+    for _ in range(args.warmup):
+        _oracle_step(O, cfg, sc, rng.choice(sc["points"].shape[0], n, replace=False))
+    times = []
+    for _ in range(args.steps):
+        idx = rng.choice(sc["points"].shape[0], n, replace=False)
+        t = time.perf_counter()
+        _oracle_step(O, cfg, sc, idx)
+        times.append(time.perf_counter() - t)
+    Nsph = sc["centers"].shape[0]
+    mean_s = statistics.fmean(times)
+    value = n * Nsph / mean_s
+    srt = sorted(times)
+    sample = f"{n} random points per step of the 512x512 capsule-body G-buffer x 100 spheres, fwd + bwd, float64 numpy, 1 thread"
+    return dict(metric=METRIC, value=value, unit="pairs/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=mean_s * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", impl="reference",
+                config={"workload": WORKLOAD, "points": int(sc["points"].shape[0]), "spheres": Nsph,
+                        "sh_coeffs": N_BANDS ** 2, "points_per_step_sampled": n},
+                latency_ms={"p50": srt[len(srt) // 2] * 1e3, "p99": srt[min(len(srt) - 1, int(0.99 * (len(srt) - 1)))] * 1e3},
+                cpu_baseline={"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample},
+                e2e={"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--atomic", action="store_true", help="unordered (atomic) scene-gradient reduction")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world, rank, local, dist = dist_init(args)
+    if args.impl == "reference":
+        res = bench_reference(args, world, rank)
+    else:
+        res = bench_ours(args, world, rank, local, dist)
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

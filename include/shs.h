@@ -1,0 +1,164 @@
+/*
+ * shs.h -- C ABI of the spherical-harmonics soft-shadow shading library.
+ *
+ * Method: Lyu et al., "Efficient and Differentiable Shadow Computation for
+ * Inverse Problems" (arXiv 2104.00359).  For every shading point x with normal
+ * n and albedo a, the library evaluates
+ *
+ *     B_c(x) = a_c(x) * ( L_c . (V(x) * H(x)) )                  (Sec. 3.2, Eq. 8)
+ *
+ * where L_c are the SH lighting coefficients of colour channel c (Eq. 9),
+ * H(x) is the SH projection of the clamped cosine max(n . w, 0) obtained by
+ * rotating its zonal coefficients to n (Eq. 10-11), "*" is the SH triple
+ * product truncated to n_bands bands (Eq. 6-7), and V(x) is the SH visibility
+ * built from the sphere occluders (Sec. 3.3.2, Eq. 12-13): each sphere's
+ * softened blocker (e^-epsilon inside its cap, 1 outside) contributes the
+ * zonal SH of its logarithm rotated toward the sphere centre; the
+ * contributions are summed and exponentiated in SH space (DC isolation,
+ * scaling by 2^-k, optimal linear approximation, k squarings).
+ *
+ * SH basis: real orthonormal spherical harmonics without the Condon-Shortley
+ * phase, linear index i = l*l + l + m (m > 0 <-> cos(m phi), m < 0 <->
+ * sin(|m| phi)), K = n_bands * n_bands coefficients.  Lighting coefficients
+ * passed to the library are in this basis.
+ *
+ * Conventions for every entry point below:
+ *   - All arrays are float32, contiguous, row-major, and live in DEVICE memory
+ *     (cudaMalloc or equivalent) unless a parameter says otherwise.  Pointers
+ *     must be 4-byte aligned; [P,3] arrays are x,y,z triples per point.
+ *   - The caller owns every array it passes.  A scene copies its spheres and
+ *     lighting into device memory the library owns; they stay resident until
+ *     shs_scene_destroy.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*, NULL =
+ *     legacy default stream) and returns before it completes.  Calls that use
+ *     the same scene must be ordered on one stream: a scene's scratch memory
+ *     is shared by its calls.
+ *   - Outputs are overwritten, never accumulated.  Gradients with respect to
+ *     scene parameters are sums over the call's points.
+ *   - Errors are returned as shs_status; no C++ exception crosses the ABI.
+ *     shs_last_error() gives a thread-local message for the last failure.
+ *     Invalid arguments are rejected before any work is enqueued.
+ *   - NaN/Inf inputs are not checked; they propagate into the outputs.
+ */
+#ifndef SHS_H
+#define SHS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct shs_scene_s* shs_scene_t;
+
+typedef enum {
+    SHS_OK = 0,
+    SHS_ERR_INVALID_ARG = 1, /* bad size, NULL where required, out-of-range config */
+    SHS_ERR_UNSUPPORTED = 2, /* valid request this build does not implement      */
+    SHS_ERR_OOM = 3,         /* device allocation failed                          */
+    SHS_ERR_CUDA = 4,        /* a CUDA runtime call failed (see shs_last_error)   */
+    SHS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                */
+    SHS_ERR_BUSY = 6         /* resource in use                                   */
+} shs_status;
+
+/* Arithmetic of the SH contractions (the pair terms and the exponent's scaling
+ * always run in float32). */
+enum { SHS_FP32 = 0, SHS_TF32 = 1, SHS_BF16 = 2 };
+
+typedef struct {
+    int32_t n_bands;       /* SH bands n, 1..8; K = n*n (paper uses 8, Sec. 3.2)          */
+    float epsilon;         /* softened-blocker exponent, e^-eps inside a cap (Eq. 13: 3)  */
+    float exp_tau;         /* scaling threshold: k = least k >= 0 with |f_hat| <= tau 2^k */
+    int32_t exp_kmax;      /* cap on k, 0..16                                             */
+    int32_t fixed_k;       /* >= 0: use this k for every point; < 0: per-point k          */
+    int32_t precision;     /* SHS_FP32 (SHS_TF32 / SHS_BF16: tensor-core contractions)    */
+    int32_t deterministic; /* 1: scene gradients reduced in a fixed order                  */
+    int32_t reserved;      /* must be 0                                                   */
+} shs_config;
+
+/* Fills *cfg with n_bands=4, epsilon=3, exp_tau=1, exp_kmax=16, fixed_k=-1,
+ * precision=SHS_FP32, deterministic=1. */
+shs_status shs_config_default(shs_config* cfg);
+
+/* Creates a resident scene of n_spheres occluder spheres (Sec. 3.3.1: the
+ * geometry is approximated by a sphere set) and SH lighting (Eq. 9).
+ *   centers: [N,3] sphere centres, radii: [N] radii (must be >= 0; device
+ *   memory, so not checked), light: [3,K] per-channel SH coefficients.
+ *   0 <= n_spheres <= 1024; n_spheres == 0 is unoccluded shading, and then
+ *   centers/radii may be NULL.  *out receives the handle.
+ * Allocates device memory for the spheres, lighting and the scratch buffers
+ * the backward pass reduces into; returns SHS_ERR_OOM if that fails. */
+shs_status shs_scene_create(const shs_config* cfg, int32_t n_spheres,
+                            const float* centers, const float* radii,
+                            const float* light, void* stream, shs_scene_t* out);
+
+/* Replaces centres, radii and/or lighting (NULL = unchanged) on `stream`. */
+shs_status shs_scene_update(shs_scene_t scene, const float* centers,
+                            const float* radii, const float* light, void* stream);
+
+/* Frees the scene after synchronising the device.  NULL is accepted. */
+shs_status shs_scene_destroy(shs_scene_t scene);
+
+/* Reads the scene's configuration and sphere count. */
+shs_status shs_scene_info(shs_scene_t scene, shs_config* cfg, int32_t* n_spheres);
+
+/* Bytes of the optional per-point state that shs_shade can save for the
+ * backward pass (the log-visibility f, K floats, and the squaring count k, per
+ * point).  Without it the backward pass recomputes f from the spheres. */
+size_t shs_saved_bytes(shs_scene_t scene, int64_t n_points);
+
+/* Forward shading, Eq. 8, for P = n_points points.
+ *   points, normals, albedo: [P,3]; normals need not be unit length (they are
+ *   normalised inside).  radiance: [P,3] output.  saved: NULL or a device
+ *   buffer of shs_saved_bytes(scene, P) bytes, 16-byte aligned.
+ * P == 0 is a no-op. */
+shs_status shs_shade(shs_scene_t scene, int64_t n_points, const float* points,
+                     const float* normals, const float* albedo, float* radiance,
+                     void* saved, void* stream);
+
+/* Reverse-mode adjoint of shs_shade (Sec. 3.5: the radiance is differentiable
+ * with respect to geometry, lighting and albedo).  Given d_radiance = dLoss/dB
+ * [P,3], writes
+ *   d_light   [3,K]  sum over points,      d_albedo  [P,3],
+ *   d_centers [N,3]  sum over points,      d_radii   [N],
+ *   d_points  [P,3],                       d_normals [P,3].
+ * Any output pointer may be NULL to skip that gradient.  `saved` is the buffer
+ * shs_shade filled for the same inputs, or NULL to recompute.  The number of
+ * squarings k is piecewise constant, so no gradient flows through it; no
+ * gradient flows through a clamped cap (point inside a sphere). */
+shs_status shs_shade_backward(shs_scene_t scene, int64_t n_points, const float* points,
+                              const float* normals, const float* albedo, const void* saved,
+                              const float* d_radiance, float* d_light, float* d_albedo,
+                              float* d_centers, float* d_radii, float* d_points,
+                              float* d_normals, void* stream);
+
+/* The analysis-by-synthesis step's loss and backward pass in one launch
+ * (Sec. 3.5, Eq. 15 with per-point radiance): loss = 1/2 sum (B - target)^2,
+ * d_radiance = B - target, then the gradients of shs_shade_backward.
+ *   radiance: [P,3] output of shs_shade for the same inputs; target: [P,3];
+ *   loss: device float, written.  Other arguments as in shs_shade_backward. */
+shs_status shs_shade_backward_l2(shs_scene_t scene, int64_t n_points, const float* points,
+                                 const float* normals, const float* albedo, const void* saved,
+                                 const float* radiance, const float* target, float* loss,
+                                 float* d_light, float* d_albedo, float* d_centers,
+                                 float* d_radii, float* d_points, float* d_normals,
+                                 void* stream);
+
+/* Synchronises `stream`, then reports and clears the scene's device-side
+ * status word: 0 = no error, otherwise a shs_status a kernel raised (e.g.
+ * SHS_ERR_TIMEOUT when a bounded wait for staged data gave up). */
+shs_status shs_scene_device_status(shs_scene_t scene, void* stream, int32_t* device_status);
+
+/* Number of kernel launches the library enqueued since the process started
+ * (all scenes, all threads). */
+int64_t shs_launch_count(void);
+
+const char* shs_status_string(shs_status status);
+const char* shs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHS_H */

@@ -287,6 +287,9 @@ def sh_exp(cfg, C, f, k=None):
     P, K = f.shape
     if k is None:
         k = exp_scaling_k(cfg, f)
+    k = np.asarray(k, dtype=np.int64)
+    if P and (k.min() < 0 or k.max() > 64):
+        raise ValueError("squaring count out of range")
     e0 = np.exp(f[:, 0] / SQRT_FOUR_PI)
     fh = f.copy()
     fh[:, 0] = 0.0
@@ -336,7 +339,10 @@ def shade_backward(cfg, points, normals, albedo, centers, radii, light, d_radian
     """Gradients of sum(d_radiance * B) w.r.t. every input, in float64.
 
     Returns dict with d_light [3,K], d_albedo [P,3], d_centers [N,3],
-    d_radii [N], d_points [P,3], d_normals [P,3] and the forward dict."""
+    d_radii [N], d_points [P,3], d_normals [P,3] and the forward dict.  For the
+    three sums over points it also returns ``abs_<name>``: the sum over points
+    of the absolute per-point terms, the scale that bounds rounding error in
+    any evaluation order."""
     n = cfg.n_bands
     K = n * n
     C = gaunt_tensor(n)
@@ -354,6 +360,7 @@ def shade_backward(cfg, points, normals, albedo, centers, radii, light, d_radian
     LW = W @ L.T                                   # [P, 3]
     d_albedo = dB * LW
     d_light = (alb * dB).T @ W                     # [3, K]
+    abs_d_light = np.abs(alb * dB).T @ np.abs(W)
     dW = (alb * dB) @ L                            # [P, K]
 
     # W = V * H
@@ -391,6 +398,8 @@ def shade_backward(cfg, points, normals, albedo, centers, radii, light, d_radian
     d_points = np.zeros_like(pts)
     d_centers = np.zeros_like(ctr)
     d_radii = np.zeros_like(rad)
+    abs_d_centers = np.zeros_like(ctr)
+    abs_d_radii = np.zeros_like(rad)
     for j in range(ctr.shape[0]):
         d, D, valid, s, ca = cap_cosine(pts, ctr[j], rad[j])
         sh = d / D[:, None]
@@ -417,6 +426,9 @@ def shade_backward(cfg, points, normals, albedo, centers, radii, light, d_radian
         dr = np.where(valid, dr, 0.0)
         d_centers[j] = dd.sum(axis=0)
         d_radii[j] = dr.sum()
+        abs_d_centers[j] = np.abs(dd).sum(axis=0)
+        abs_d_radii[j] = np.abs(dr).sum()
         d_points -= dd
     return dict(d_light=d_light, d_albedo=d_albedo, d_centers=d_centers, d_radii=d_radii,
-                d_points=d_points, d_normals=d_normals, df=df, forward=fw)
+                d_points=d_points, d_normals=d_normals, df=df, forward=fw,
+                abs_d_light=abs_d_light, abs_d_centers=abs_d_centers, abs_d_radii=abs_d_radii)

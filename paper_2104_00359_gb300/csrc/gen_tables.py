@@ -1,0 +1,428 @@
+#!/usr/bin/env python3
+"""Generate the unrolled spherical-harmonics device code used by the CUDA
+kernels (``generated/shs_sh_gen.cuh``).
+
+For each supported band count n (K = n^2 coefficients) it emits:
+
+* ``ybar(x, y, z, Y)``: the un-normalised real SH polynomials
+  Ybar_lm = Pbar_l^|m|(z) * {C_m, S_m}(x, y) where C_m + i S_m = (x + i y)^m and
+  Pbar_l^m = d^m P_l / dz^m (no Condon-Shortley phase).  The normalised basis
+  (Sec. 3.2, Eq. 3) is y_i = NORM[i] * Ybar_i.
+* ``ybar_vjp(x, y, z, w, gx, gy, gz)``: the gradient of sum_i w_i Ybar_i with
+  respect to (x, y, z), emitted by reverse-mode differentiation of the
+  straight-line code above.
+* ``mul(a, b, o)``: the truncated SH triple product o = a * b,
+  o_i = sum_jk C_ijk a_j b_k (Eq. 7), unrolled over the nonzero C_ijk.
+* ``sqr(a, o)``: o = a * a using the j <-> k symmetry of C.
+* tables: NORM[i], AHAT[l] (clamped-cosine convolution constants, Eq. 10-11).
+
+C_ijk is computed here by exact integration of monomials over the sphere,
+  int x^a y^b z^c dw = 4 pi (a-1)!! (b-1)!! (c-1)!! / (a+b+c+1)!!  (a, b, c even),
+applied to the products of the SH polynomials -- a different route from any
+quadrature.  Run ``python gen_tables.py`` to rewrite the header; the build
+checks that the committed header is current.
+"""
+
+from __future__ import annotations
+
+import math
+import os
+import sys
+from fractions import Fraction
+
+import numpy as np
+
+BANDS = (1, 2, 3, 4, 5, 6, 7, 8)
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(HERE, "generated", "shs_sh_gen.cuh")
+
+
+# ---------------------------------------------------------------------------
+# exact polynomials: dict {(a, b, c): Fraction} for x^a y^b z^c
+# ---------------------------------------------------------------------------
+
+def p_add(p, q, s=1):
+    r = dict(p)
+    for k, v in q.items():
+        r[k] = r.get(k, 0) + s * v
+        if r[k] == 0:
+            del r[k]
+    return r
+
+
+def p_mul(p, q):
+    r = {}
+    for (a1, b1, c1), v1 in p.items():
+        for (a2, b2, c2), v2 in q.items():
+            k = (a1 + a2, b1 + b2, c1 + c2)
+            r[k] = r.get(k, 0) + v1 * v2
+    return {k: v for k, v in r.items() if v != 0}
+
+
+def p_scale(p, s):
+    return {k: v * s for k, v in p.items() if v * s != 0}
+
+
+X = {(1, 0, 0): Fraction(1)}
+Y = {(0, 1, 0): Fraction(1)}
+Z = {(0, 0, 1): Fraction(1)}
+ONE = {(0, 0, 0): Fraction(1)}
+
+
+def ybar_polys(n):
+    """Exact Ybar_i polynomials (index i = l^2 + l + m) by the same recurrences
+    the emitted code uses."""
+    Cm, Sm = [ONE], [{}]
+    for m in range(1, n):
+        Cm.append(p_add(p_mul(X, Cm[-1]), p_mul(Y, Sm[-1]), -1))
+        Sm.append(p_add(p_mul(X, Sm[-1]), p_mul(Y, Cm[-2])))
+    Pb = {}
+    for m in range(n):
+        Pb[(m, m)] = {(0, 0, 0): Fraction(math.prod(range(1, 2 * m, 2)))}
+        if m + 1 < n:
+            Pb[(m + 1, m)] = p_scale(p_mul(Z, Pb[(m, m)]), 2 * m + 1)
+        for l in range(m + 2, n):
+            t = p_add(p_scale(p_mul(Z, Pb[(l - 1, m)]), 2 * l - 1),
+                      p_scale(Pb[(l - 2, m)], l + m - 1), -1)
+            Pb[(l, m)] = p_scale(t, Fraction(1, l - m))
+    out = [None] * (n * n)
+    for l in range(n):
+        out[l * l + l] = Pb[(l, 0)]
+        for m in range(1, l + 1):
+            out[l * l + l + m] = p_mul(Pb[(l, m)], Cm[m])
+            out[l * l + l - m] = p_mul(Pb[(l, m)], Sm[m])
+    return out
+
+
+def dfact(k):
+    return math.prod(range(k, 0, -2)) if k > 0 else 1
+
+
+def sphere_moment(a, b, c):
+    """int_{S^2} x^a y^b z^c dw / (4 pi), exact."""
+    if a % 2 or b % 2 or c % 2:
+        return Fraction(0)
+    return Fraction(dfact(a - 1) * dfact(b - 1) * dfact(c - 1), dfact(a + b + c + 1))
+
+
+def norms(n):
+    """NORM[i] with y_i = NORM[i] * Ybar_i."""
+    out = []
+    for l in range(n):
+        for m in range(-l, l + 1):
+            am = abs(m)
+            N = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - am) / math.factorial(l + am))
+            out.append(N * (math.sqrt(2.0) if am else 1.0))
+    return out
+
+
+def gaunt_monomial(n):
+    """C_ijk = NORM_i NORM_j NORM_k int Ybar_i Ybar_j Ybar_k dw, with the
+    integral taken monomial by monomial from the closed form above.
+
+    Dense float64 arrays over exponent triples: Q_jk = Ybar_j Ybar_k (exponents
+    < 2n-1), R_i[b] = sum_a Ybar_i[a] M[a + b] (M the sphere moments), and
+    C_ijk = <R_i, Q_jk>.  Returns {(i, j, k): value} for j <= k, value != 0."""
+    K = n * n
+    P = ybar_polys(n)
+    N = norms(n)
+    e2, e3 = 2 * n - 1, 3 * n - 2
+    M = np.zeros((e3, e3, e3))
+    for a in range(0, e3, 2):
+        for b in range(0, e3, 2):
+            for c in range(0, e3, 2):
+                M[a, b, c] = 4.0 * math.pi * float(sphere_moment(a, b, c))
+    dense = np.zeros((K, n, n, n))
+    for i, p in enumerate(P):
+        for (a, b, c), v in p.items():
+            dense[i, a, b, c] = float(v)
+    R = np.zeros((K, e2, e2, e2))
+    for i, p in enumerate(P):
+        for (a, b, c), v in p.items():
+            R[i] += float(v) * M[a:a + e2, b:b + e2, c:c + e2]
+    pairs = [(j, k) for j in range(K) for k in range(j, K)]
+    Q = np.zeros((len(pairs), e2, e2, e2))
+    for q, (j, k) in enumerate(pairs):
+        for (a, b, c), v in P[j].items():
+            Q[q, a:a + n, b:b + n, c:c + n] += float(v) * dense[k]
+    G = R.reshape(K, -1) @ Q.reshape(len(pairs), -1).T
+    lb = [int(math.isqrt(i)) for i in range(K)]
+    out = {}
+    for i in range(K):
+        for q, (j, k) in enumerate(pairs):
+            li, lj, lk = lb[i], lb[j], lb[k]
+            if (li + lj + lk) % 2 or li > lj + lk or lj > li + lk or lk > li + lj:
+                continue
+            v = N[i] * N[j] * N[k] * G[i, q]
+            if abs(v) > 1e-12:
+                out[(i, j, k)] = v
+    return out
+
+
+def ahat(n):
+    """A_hat_l = 2 pi int_0^1 t P_l(t) dt, exact from P_l's coefficients."""
+    out = []
+    for l in range(n):
+        # P_l power coefficients via Bonnet recurrence in Fractions
+        p0, p1 = [Fraction(1)], [Fraction(0), Fraction(1)]
+        if l == 0:
+            c = p0
+        elif l == 1:
+            c = p1
+        else:
+            for ll in range(1, l):
+                nxt = [Fraction(0)] * (ll + 2)
+                for i, v in enumerate(p1):
+                    nxt[i + 1] += Fraction(2 * ll + 1, ll + 1) * v
+                for i, v in enumerate(p0):
+                    nxt[i] -= Fraction(ll, ll + 1) * v
+                p0, p1 = p1, nxt
+            c = p1
+        integ = sum(v / (i + 2) for i, v in enumerate(c))
+        out.append(2.0 * math.pi * float(integ))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# straight-line code builder with constant folding and reverse mode
+# ---------------------------------------------------------------------------
+
+class Code:
+    def __init__(self, prefix):
+        self.ops = []          # (name, kind, args)
+        self.prefix = prefix
+        self.count = 0
+
+    def _new(self, kind, args):
+        name = f"{self.prefix}{self.count}"
+        self.count += 1
+        self.ops.append((name, kind, args))
+        return ("v", name)
+
+    @staticmethod
+    def const(v):
+        return ("c", float(v))
+
+    def mul(self, a, b):
+        if a[0] == "c" and b[0] == "c":
+            return self.const(a[1] * b[1])
+        if a[0] == "c":
+            a, b = b, a
+        if b[0] == "c":
+            if b[1] == 0.0:
+                return self.const(0.0)
+            if b[1] == 1.0:
+                return a
+        return self._new("mul", (a, b))
+
+    def add(self, a, b, sb=1.0):
+        if b[0] == "c" and b[1] == 0.0:
+            return a
+        if a[0] == "c" and a[1] == 0.0:
+            return b if sb == 1.0 else self.mul(b, self.const(sb))
+        if a[0] == "c" and b[0] == "c":
+            return self.const(a[1] + sb * b[1])
+        return self._new("add", (a, b, sb))
+
+
+def fmt(v):
+    if v[0] == "c":
+        r = repr(float(np.float32(v[1])))
+        if "e" not in r and "." not in r and "inf" not in r and "nan" not in r:
+            r += ".0"
+        return r + "f"
+    return v[1]
+
+
+def build_ybar(n):
+    code = Code("t")
+    x, y, z = ("v", "x"), ("v", "y"), ("v", "z")
+    C = [code.const(1.0)]
+    S = [code.const(0.0)]
+    for m in range(1, n):
+        C.append(code.add(code.mul(x, C[-1]), code.mul(y, S[-1]), -1.0))
+        S.append(code.add(code.mul(x, S[-1]), code.mul(y, C[-2])))
+    Pb = {}
+    for m in range(n):
+        Pb[(m, m)] = code.const(math.prod(range(1, 2 * m, 2)))
+        if m + 1 < n:
+            Pb[(m + 1, m)] = code.mul(code.mul(z, Pb[(m, m)]), code.const(2 * m + 1))
+        for l in range(m + 2, n):
+            a = code.mul(code.mul(z, Pb[(l - 1, m)]), code.const((2 * l - 1) / (l - m)))
+            b = code.mul(Pb[(l - 2, m)], code.const((l + m - 1) / (l - m)))
+            Pb[(l, m)] = code.add(a, b, -1.0)
+    outs = [None] * (n * n)
+    for l in range(n):
+        outs[l * l + l] = Pb[(l, 0)]
+        for m in range(1, l + 1):
+            outs[l * l + l + m] = code.mul(Pb[(l, m)], C[m])
+            outs[l * l + l - m] = code.mul(Pb[(l, m)], S[m])
+    return code, outs
+
+
+def emit_forward(code, outs, target):
+    lines = []
+    for name, kind, args in code.ops:
+        if kind == "mul":
+            lines.append(f"const float {name} = {fmt(args[0])} * {fmt(args[1])};")
+        else:
+            a, b, sb = args
+            op = "+" if sb > 0 else "-"
+            if abs(sb) == 1.0:
+                lines.append(f"const float {name} = {fmt(a)} {op} {fmt(b)};")
+            else:
+                lines.append(f"const float {name} = fmaf({fmt(code.const(sb))}, {fmt(b)}, {fmt(a)});")
+    for i, o in enumerate(outs):
+        lines.append(f"{target}[{i}] = {fmt(o)};")
+    return lines
+
+
+def emit_vjp(code, outs):
+    """Reverse sweep: adjoints of x, y, z for the scalar sum_i w[i] * out_i."""
+    adj = {}      # var name -> list of terms (strings)
+
+    def acc(var, term):
+        if var[0] == "c":
+            return
+        adj.setdefault(var[1], []).append(term)
+
+    for i, o in enumerate(outs):
+        acc(o, f"w[{i}]")
+    lines = []
+    for name, kind, args in reversed(code.ops):
+        terms = adj.get(name)
+        if not terms:
+            continue
+        g = f"a_{name}"
+        lines.append(f"const float {g} = {' + '.join(terms)};")
+        if kind == "mul":
+            a, b = args
+            if b[0] == "c":
+                acc(a, f"{fmt(b)} * {g}")
+            elif a[0] == "c":
+                acc(b, f"{fmt(a)} * {g}")
+            else:
+                acc(a, f"{fmt(b)} * {g}")
+                acc(b, f"{fmt(a)} * {g}")
+        else:
+            a, b, sb = args
+            acc(a, g)
+            if sb == 1.0:
+                acc(b, g)
+            elif sb == -1.0:
+                acc(b, f"-{g}")
+            else:
+                acc(b, f"{fmt(code.const(sb))} * {g}")
+    for v, nm in (("x", "gx"), ("y", "gy"), ("z", "gz")):
+        terms = adj.get(v)
+        lines.append(f"{nm} = {' + '.join(terms) if terms else '0.0f'};")
+    return lines
+
+
+def emit_gaunt(n, C):
+    K = n * n
+    mul_lines, sqr_lines = [], []
+    by_i = {i: [] for i in range(K)}
+    for (i, j, k), v in sorted(C.items()):
+        by_i[i].append((j, k, v))
+    for i in range(K):
+        terms_m, terms_s = [], []
+        for j, k, v in by_i[i]:
+            c = fmt(("c", v))
+            if j == k:
+                terms_m.append((c, f"a[{j}] * b[{j}]"))
+                terms_s.append((c, f"a[{j}] * a[{j}]"))
+            else:
+                terms_m.append((c, f"(a[{j}] * b[{k}] + a[{k}] * b[{j}])"))
+                terms_s.append((fmt(("c", 2 * v)), f"a[{j}] * a[{k}]"))
+        for lines, terms in ((mul_lines, terms_m), (sqr_lines, terms_s)):
+            if not terms:
+                lines.append(f"o[{i}] = 0.0f;")
+                continue
+            expr = f"{terms[0][0]} * {terms[0][1]}"
+            for c, t in terms[1:]:
+                expr = f"fmaf({c}, {t}, {expr})"
+            lines.append(f"o[{i}] = {expr};")
+    return mul_lines, sqr_lines
+
+
+def indent(lines, k=8):
+    return "\n".join(" " * k + ln for ln in lines)
+
+
+def generate():
+    parts = [
+        "// Generated by gen_tables.py -- do not edit.",
+        "// Real SH polynomials, their reverse-mode gradients, and the truncated",
+        "// SH triple product (Sec. 3.2, Eq. 3 and Eq. 6-7), unrolled per band count.",
+        "#pragma once",
+        "",
+        "namespace shsgen {",
+        "",
+        "template <int NB> struct SH;",
+        "",
+    ]
+    for n in BANDS:
+        K = n * n
+        C = gaunt_monomial(n)
+        code, outs = build_ybar(n)
+        fwd = emit_forward(code, outs, "Y")
+        vjp = emit_forward(code, [], "Y") + emit_vjp(code, outs)
+        mul_l, sqr_l = emit_gaunt(n, C)
+        N = norms(n)
+        A = ahat(n)
+        parts.append(f"template <> struct SH<{n}> {{")
+        parts.append(f"    static constexpr int K = {K};")
+        parts.append(f"    static constexpr int NNZ_SYM = {len(C)};   // entries (i, j <= k)")
+        parts.append("    __device__ __forceinline__ static float norm(int i) {")
+        parts.append("        switch (i) {")
+        for i, v in enumerate(N):
+            parts.append(f"            case {i}: return {fmt(('c', v))};")
+        parts.append("            default: return 0.0f;")
+        parts.append("        }")
+        parts.append("    }")
+        parts.append("    __device__ __forceinline__ static float ahat(int l) {")
+        parts.append("        switch (l) {")
+        for l, v in enumerate(A):
+            parts.append(f"            case {l}: return {fmt(('c', v))};")
+        parts.append("            default: return 0.0f;")
+        parts.append("        }")
+        parts.append("    }")
+        parts.append("    __device__ __forceinline__ static void ybar(float x, float y, float z, float* Y) {")
+        parts.append("        (void)x; (void)y; (void)z;")
+        parts.append(indent(fwd))
+        parts.append("    }")
+        parts.append("    __device__ __forceinline__ static void ybar_vjp(float x, float y, float z, const float* w,")
+        parts.append("                                                    float& gx, float& gy, float& gz) {")
+        parts.append("        (void)x; (void)y; (void)z; (void)w;")
+        parts.append(indent([ln for ln in vjp if not ln.startswith("Y[")]))
+        parts.append("    }")
+        parts.append("    __device__ __forceinline__ static void mul(const float* a, const float* b, float* o) {")
+        parts.append(indent(mul_l))
+        parts.append("    }")
+        parts.append("    __device__ __forceinline__ static void sqr(const float* a, float* o) {")
+        parts.append(indent(sqr_l))
+        parts.append("    }")
+        parts.append("};")
+        parts.append("")
+    parts.append("}  // namespace shsgen")
+    parts.append("")
+    return "\n".join(parts)
+
+
+def main(argv):
+    text = generate()
+    if "--check" in argv:
+        cur = open(OUT).read() if os.path.exists(OUT) else ""
+        if cur != text:
+            print("generated header is stale; run gen_tables.py", file=sys.stderr)
+            return 1
+        return 0
+    os.makedirs(os.path.dirname(OUT), exist_ok=True)
+    with open(OUT, "w") as fh:
+        fh.write(text)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main(sys.argv[1:]))

@@ -1,0 +1,401 @@
+// C ABI of the shading library (declared in include/shs.h): argument
+// validation, scene memory, and dispatch to the per-band-count kernels.
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "shs.h"
+#include "shs_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+std::atomic<int64_t> g_launches{0};
+
+shs_status fail(shs_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+shs_status cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(SHS_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(SHS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+namespace shs {
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+__global__ void pack_spheres_kernel(const float* c, const float* r, float4* out, int n, bool has_c,
+                                    bool has_r) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    float4 v = out[j];
+    if (has_c) {
+        v.x = c[3 * j];
+        v.y = c[3 * j + 1];
+        v.z = c[3 * j + 2];
+    }
+    if (has_r) v.w = r[j];
+    out[j] = v;
+}
+}  // namespace
+
+cudaError_t launch_pack_spheres(const float* centers, const float* radii, float4* out, int n,
+                                bool has_c, bool has_r, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    pack_spheres_kernel<<<(n + 127) / 128, 128, 0, s>>>(centers, radii, out, n, has_c, has_r);
+    count_launch();
+    return cudaGetLastError();
+}
+}  // namespace shs
+
+struct shs_scene_s {
+    shs_config cfg;
+    int n_spheres;
+    int K, Kpad;
+    int device;
+    int max_grid;          // persistent backward grid
+    int partial_stride;    // floats per block partial
+    float4* spheres;       // [max(N,1)]
+    float* light;          // [3][Kpad]
+    int* status;           // device status word
+    float* partials;       // [max_grid][partial_stride] (deterministic) or accumulator
+    unsigned int* counter;
+};
+
+namespace {
+
+using shs::BwdArgs;
+using shs::FwdArgs;
+using shs::SceneView;
+
+template <template <int> class F, typename... A>
+cudaError_t dispatch(int nb, A&&... args) {
+    switch (nb) {
+        case 1: return F<1>::run(args...);
+        case 2: return F<2>::run(args...);
+        case 3: return F<3>::run(args...);
+        case 4: return F<4>::run(args...);
+        case 5: return F<5>::run(args...);
+        case 6: return F<6>::run(args...);
+        case 7: return F<7>::run(args...);
+        case 8: return F<8>::run(args...);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NB> struct Fwd {
+    static cudaError_t run(const FwdArgs& a, cudaStream_t s) { return shs::launch_forward<NB>(a, s); }
+};
+template <int NB> struct Bwd {
+    static cudaError_t run(const BwdArgs& a, cudaStream_t s) { return shs::launch_backward<NB>(a, s); }
+};
+
+int blocks_per_sm(int nb, int n) {
+    switch (nb) {
+        case 1: return shs::backward_blocks_per_sm<1>(n);
+        case 2: return shs::backward_blocks_per_sm<2>(n);
+        case 3: return shs::backward_blocks_per_sm<3>(n);
+        case 4: return shs::backward_blocks_per_sm<4>(n);
+        case 5: return shs::backward_blocks_per_sm<5>(n);
+        case 6: return shs::backward_blocks_per_sm<6>(n);
+        case 7: return shs::backward_blocks_per_sm<7>(n);
+        case 8: return shs::backward_blocks_per_sm<8>(n);
+        default: return 1;
+    }
+}
+
+shs_status check_config(const shs_config* c) {
+    if (!c) return fail(SHS_ERR_INVALID_ARG, "config is NULL");
+    if (c->n_bands < 1 || c->n_bands > 8) return fail(SHS_ERR_INVALID_ARG, "n_bands %d not in 1..8", c->n_bands);
+    if (!(c->epsilon >= 0.f) || !(c->epsilon < 1e30f)) return fail(SHS_ERR_INVALID_ARG, "epsilon must be finite and >= 0");
+    if (!(c->exp_tau > 0.f) || !(c->exp_tau < 1e30f)) return fail(SHS_ERR_INVALID_ARG, "exp_tau must be finite and > 0");
+    if (c->exp_kmax < 0 || c->exp_kmax > shs::kMaxK) return fail(SHS_ERR_INVALID_ARG, "exp_kmax not in 0..%d", shs::kMaxK);
+    if (c->fixed_k > shs::kMaxK) return fail(SHS_ERR_INVALID_ARG, "fixed_k > %d", shs::kMaxK);
+    if (c->precision != SHS_FP32 && c->precision != SHS_TF32 && c->precision != SHS_BF16)
+        return fail(SHS_ERR_INVALID_ARG, "unknown precision %d", c->precision);
+    if (c->precision != SHS_FP32) return fail(SHS_ERR_UNSUPPORTED, "only SHS_FP32 is implemented");
+    if (c->deterministic != 0 && c->deterministic != 1) return fail(SHS_ERR_INVALID_ARG, "deterministic must be 0 or 1");
+    if (c->reserved != 0) return fail(SHS_ERR_INVALID_ARG, "reserved must be 0");
+    return SHS_OK;
+}
+
+SceneView view_of(const shs_scene_s* s) {
+    SceneView v;
+    v.spheres = s->spheres;
+    v.light = s->light;
+    v.n_spheres = s->n_spheres;
+    v.light_stride = s->Kpad;
+    v.neg_2pi_eps = -2.0f * 3.14159265358979323846f * s->cfg.epsilon;
+    v.tau2 = s->cfg.exp_tau * s->cfg.exp_tau;
+    v.kmax = s->cfg.exp_kmax;
+    v.fixed_k = s->cfg.fixed_k;
+    v.status = s->status;
+    return v;
+}
+
+shs_status set_light(shs_scene_s* s, const float* light, cudaStream_t st) {
+    cudaError_t e = cudaMemcpy2DAsync(s->light, s->Kpad * sizeof(float), light, s->K * sizeof(float),
+                                      s->K * sizeof(float), 3, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? SHS_OK : cuda_fail(e, "copy lighting");
+}
+
+void free_scene(shs_scene_s* s) {
+    if (!s) return;
+    cudaFree(s->spheres);
+    cudaFree(s->light);
+    cudaFree(s->status);
+    cudaFree(s->partials);
+    cudaFree(s->counter);
+    delete s;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+extern "C" {
+
+shs_status shs_config_default(shs_config* cfg) {
+    if (!cfg) return fail(SHS_ERR_INVALID_ARG, "config is NULL");
+    cfg->n_bands = 4;
+    cfg->epsilon = 3.0f;
+    cfg->exp_tau = 1.0f;
+    cfg->exp_kmax = 16;
+    cfg->fixed_k = -1;
+    cfg->precision = SHS_FP32;
+    cfg->deterministic = 1;
+    cfg->reserved = 0;
+    return SHS_OK;
+}
+
+shs_status shs_scene_create(const shs_config* cfg, int32_t n_spheres, const float* centers,
+                            const float* radii, const float* light, void* stream, shs_scene_t* out) {
+    if (!out) return fail(SHS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    shs_status st = check_config(cfg);
+    if (st != SHS_OK) return st;
+    if (n_spheres < 0 || n_spheres > shs::kMaxSpheres)
+        return fail(SHS_ERR_INVALID_ARG, "n_spheres %d not in 0..%d", n_spheres, shs::kMaxSpheres);
+    if (n_spheres > 0 && (!centers || !radii)) return fail(SHS_ERR_INVALID_ARG, "centers/radii are NULL");
+    if (!light) return fail(SHS_ERR_INVALID_ARG, "light is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    shs_scene_s* sc = new (std::nothrow) shs_scene_s();
+    if (!sc) return fail(SHS_ERR_OOM, "host allocation failed");
+    sc->cfg = *cfg;
+    sc->n_spheres = n_spheres;
+    sc->K = cfg->n_bands * cfg->n_bands;
+    sc->Kpad = (sc->K + 3) / 4 * 4;
+    cudaError_t e = cudaGetDevice(&sc->device);
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sc->device);
+    if (e != cudaSuccess) {
+        delete sc;
+        return cuda_fail(e, "query device");
+    }
+    sc->max_grid = sms * blocks_per_sm(cfg->n_bands, n_spheres);
+    sc->partial_stride = static_cast<int>(align_up(3 * sc->K + 1 + 4 * n_spheres, 4));
+    const size_t partial_floats =
+        cfg->deterministic ? static_cast<size_t>(sc->max_grid) * sc->partial_stride : sc->partial_stride;
+    e = cudaMalloc(&sc->spheres, sizeof(float4) * (n_spheres > 0 ? n_spheres : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&sc->light, sizeof(float) * 3 * sc->Kpad);
+    if (e == cudaSuccess) e = cudaMalloc(&sc->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&sc->partials, sizeof(float) * partial_floats);
+    if (e == cudaSuccess) e = cudaMalloc(&sc->counter, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc->light, 0, sizeof(float) * 3 * sc->Kpad, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc->status, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc->partials, 0, sizeof(float) * partial_floats, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc->counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) {
+        free_scene(sc);
+        return cuda_fail(e, "allocate scene");
+    }
+    e = shs::launch_pack_spheres(centers, radii, sc->spheres, n_spheres, true, true, s);
+    if (e != cudaSuccess) {
+        free_scene(sc);
+        return cuda_fail(e, "pack spheres");
+    }
+    st = set_light(sc, light, s);
+    if (st != SHS_OK) {
+        free_scene(sc);
+        return st;
+    }
+    *out = sc;
+    return SHS_OK;
+}
+
+shs_status shs_scene_update(shs_scene_t sc, const float* centers, const float* radii,
+                            const float* light, void* stream) {
+    if (!sc) return fail(SHS_ERR_INVALID_ARG, "scene is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((centers || radii) && sc->n_spheres > 0) {
+        cudaError_t e = shs::launch_pack_spheres(centers, radii, sc->spheres, sc->n_spheres,
+                                                 centers != nullptr, radii != nullptr, s);
+        if (e != cudaSuccess) return cuda_fail(e, "pack spheres");
+    }
+    if (light) return set_light(sc, light, s);
+    return SHS_OK;
+}
+
+shs_status shs_scene_destroy(shs_scene_t sc) {
+    if (!sc) return SHS_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_scene(sc);
+    return e == cudaSuccess ? SHS_OK : cuda_fail(e, "synchronise before destroy");
+}
+
+shs_status shs_scene_info(shs_scene_t sc, shs_config* cfg, int32_t* n_spheres) {
+    if (!sc) return fail(SHS_ERR_INVALID_ARG, "scene is NULL");
+    if (cfg) *cfg = sc->cfg;
+    if (n_spheres) *n_spheres = sc->n_spheres;
+    return SHS_OK;
+}
+
+size_t shs_saved_bytes(shs_scene_t sc, int64_t n_points) {
+    if (!sc || n_points <= 0) return 0;
+    return align_up(static_cast<size_t>(sc->K) * n_points * sizeof(float), 16) +
+           align_up(static_cast<size_t>(n_points) * sizeof(int), 16);
+}
+
+static void split_saved(shs_scene_t sc, int64_t P, void* saved, float** f, int** k) {
+    if (!saved) {
+        *f = nullptr;
+        *k = nullptr;
+        return;
+    }
+    *f = static_cast<float*>(saved);
+    *k = reinterpret_cast<int*>(static_cast<char*>(saved) +
+                                align_up(static_cast<size_t>(sc->K) * P * sizeof(float), 16));
+}
+
+shs_status shs_shade(shs_scene_t sc, int64_t n_points, const float* points, const float* normals,
+                     const float* albedo, float* radiance, void* saved, void* stream) {
+    if (!sc) return fail(SHS_ERR_INVALID_ARG, "scene is NULL");
+    if (n_points < 0) return fail(SHS_ERR_INVALID_ARG, "n_points < 0");
+    if (n_points == 0) return SHS_OK;
+    if (!points || !normals || !albedo || !radiance) return fail(SHS_ERR_INVALID_ARG, "NULL input/output array");
+    if (saved && (reinterpret_cast<uintptr_t>(saved) & 15u)) return fail(SHS_ERR_INVALID_ARG, "saved not 16-byte aligned");
+    FwdArgs a;
+    a.sc = view_of(sc);
+    a.n_points = n_points;
+    a.points = points;
+    a.normals = normals;
+    a.albedo = albedo;
+    a.radiance = radiance;
+    split_saved(sc, n_points, saved, &a.saved_f, &a.saved_k);
+    cudaError_t e = dispatch<Fwd>(sc->cfg.n_bands, a, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SHS_OK : cuda_fail(e, "launch forward");
+}
+
+static shs_status backward_common(shs_scene_t sc, int64_t n_points, const float* points,
+                                  const float* normals, const float* albedo, const void* saved,
+                                  const float* d_radiance, const float* radiance, const float* target,
+                                  float* loss, float* d_light, float* d_albedo, float* d_centers,
+                                  float* d_radii, float* d_points, float* d_normals, void* stream) {
+    if (!sc) return fail(SHS_ERR_INVALID_ARG, "scene is NULL");
+    if (n_points < 0) return fail(SHS_ERR_INVALID_ARG, "n_points < 0");
+    if (saved && (reinterpret_cast<uintptr_t>(saved) & 15u)) return fail(SHS_ERR_INVALID_ARG, "saved not 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n_points == 0) {
+        // empty sums: zero the scene-level outputs
+        cudaError_t e = cudaSuccess;
+        if (d_light) e = cudaMemsetAsync(d_light, 0, sizeof(float) * 3 * sc->K, s);
+        if (e == cudaSuccess && d_centers && sc->n_spheres) e = cudaMemsetAsync(d_centers, 0, sizeof(float) * 3 * sc->n_spheres, s);
+        if (e == cudaSuccess && d_radii && sc->n_spheres) e = cudaMemsetAsync(d_radii, 0, sizeof(float) * sc->n_spheres, s);
+        if (e == cudaSuccess && loss) e = cudaMemsetAsync(loss, 0, sizeof(float), s);
+        return e == cudaSuccess ? SHS_OK : cuda_fail(e, "zero empty outputs");
+    }
+    if (!points || !normals || !albedo) return fail(SHS_ERR_INVALID_ARG, "NULL input array");
+    BwdArgs a;
+    a.sc = view_of(sc);
+    a.n_points = n_points;
+    a.points = points;
+    a.normals = normals;
+    a.albedo = albedo;
+    float* sf;
+    int* sk;
+    split_saved(sc, n_points, const_cast<void*>(saved), &sf, &sk);
+    a.saved_f = sf;
+    a.saved_k = sk;
+    a.d_radiance = d_radiance;
+    a.radiance = radiance;
+    a.target = target;
+    a.loss = loss;
+    a.d_light = d_light;
+    a.d_albedo = d_albedo;
+    a.d_centers = sc->n_spheres ? d_centers : nullptr;
+    a.d_radii = sc->n_spheres ? d_radii : nullptr;
+    a.d_points = d_points;
+    a.d_normals = d_normals;
+    a.partials = sc->partials;
+    a.counter = sc->cfg.deterministic ? nullptr : sc->counter;
+    a.partial_stride = sc->partial_stride;
+    const int64_t tiles = (n_points + shs::kBlock - 1) / shs::kBlock;
+    a.grid = static_cast<int>(tiles < sc->max_grid ? tiles : sc->max_grid);
+    cudaError_t e = dispatch<Bwd>(sc->cfg.n_bands, a, s);
+    return e == cudaSuccess ? SHS_OK : cuda_fail(e, "launch backward");
+}
+
+shs_status shs_shade_backward(shs_scene_t sc, int64_t n_points, const float* points,
+                              const float* normals, const float* albedo, const void* saved,
+                              const float* d_radiance, float* d_light, float* d_albedo,
+                              float* d_centers, float* d_radii, float* d_points, float* d_normals,
+                              void* stream) {
+    if (n_points > 0 && !d_radiance) return fail(SHS_ERR_INVALID_ARG, "d_radiance is NULL");
+    return backward_common(sc, n_points, points, normals, albedo, saved, d_radiance, nullptr, nullptr,
+                           nullptr, d_light, d_albedo, d_centers, d_radii, d_points, d_normals, stream);
+}
+
+shs_status shs_shade_backward_l2(shs_scene_t sc, int64_t n_points, const float* points,
+                                 const float* normals, const float* albedo, const void* saved,
+                                 const float* radiance, const float* target, float* loss,
+                                 float* d_light, float* d_albedo, float* d_centers, float* d_radii,
+                                 float* d_points, float* d_normals, void* stream) {
+    if (n_points > 0 && (!radiance || !target)) return fail(SHS_ERR_INVALID_ARG, "radiance/target is NULL");
+    return backward_common(sc, n_points, points, normals, albedo, saved, nullptr, radiance, target, loss,
+                           d_light, d_albedo, d_centers, d_radii, d_points, d_normals, stream);
+}
+
+shs_status shs_scene_device_status(shs_scene_t sc, void* stream, int32_t* device_status) {
+    if (!sc || !device_status) return fail(SHS_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, sc->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc->status, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "read device status");
+    *device_status = v;
+    return SHS_OK;
+}
+
+int64_t shs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* shs_status_string(shs_status st) {
+    switch (st) {
+        case SHS_OK: return "ok";
+        case SHS_ERR_INVALID_ARG: return "invalid argument";
+        case SHS_ERR_UNSUPPORTED: return "unsupported";
+        case SHS_ERR_OOM: return "out of device memory";
+        case SHS_ERR_CUDA: return "CUDA error";
+        case SHS_ERR_TIMEOUT: return "device wait timed out";
+        case SHS_ERR_BUSY: return "busy";
+        default: return "unknown status";
+    }
+}
+
+const char* shs_last_error(void) { return g_err; }
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// Internal interface between the C ABI (shs_api.cu) and the per-band-count
+// kernel translation units (shs_kern.cu compiled once per n_bands).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace shs {
+
+constexpr int kBlock = 128;          // threads per block, one shading point each
+constexpr int kMaxSpheres = 1024;    // spheres staged in shared memory at once
+constexpr int kMaxK = 16;            // cap on the number of squarings
+
+// Device-side status codes (same values as shs_status).
+constexpr int kDevOk = 0;
+constexpr int kDevTimeout = 5;
+
+// Scene constants a kernel needs, passed by value.
+struct SceneView {
+    const float4* spheres;   // [N] (cx, cy, cz, r), 16-byte aligned
+    const float* light;      // [3][Kpad], Kpad = K rounded up to a multiple of 4
+    int n_spheres;
+    int light_stride;        // Kpad
+    float neg_2pi_eps;       // -2 pi epsilon
+    float tau2;              // exp_tau^2
+    int kmax;
+    int fixed_k;
+    int* status;             // device status word
+};
+
+struct FwdArgs {
+    SceneView sc;
+    int64_t n_points;
+    const float* points;
+    const float* normals;
+    const float* albedo;
+    float* radiance;
+    float* saved_f;          // [K][P] or null
+    int* saved_k;            // [P] or null
+};
+
+struct BwdArgs {
+    SceneView sc;
+    int64_t n_points;
+    const float* points;
+    const float* normals;
+    const float* albedo;
+    const float* saved_f;    // [K][P] or null (recompute)
+    const int* saved_k;      // [P] or null
+    const float* d_radiance; // [P,3] or null when target is set
+    const float* radiance;   // [P,3] (l2 mode)
+    const float* target;     // [P,3] (l2 mode) or null
+    float* loss;             // l2 mode
+    float* d_light;
+    float* d_albedo;
+    float* d_centers;
+    float* d_radii;
+    float* d_points;
+    float* d_normals;
+    float* partials;         // [grid][stride] scratch
+    unsigned int* counter;   // scratch, zero between launches
+    int partial_stride;
+    int grid;                // persistent grid size
+};
+
+template <int NB> cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
+template <int NB> cudaError_t launch_backward(const BwdArgs& a, cudaStream_t s);
+template <int NB> int backward_blocks_per_sm(int n_spheres);
+cudaError_t launch_pack_spheres(const float* centers, const float* radii, float4* out, int n,
+                                bool has_c, bool has_r, cudaStream_t s);
+
+void count_launch();
+
+}  // namespace shs

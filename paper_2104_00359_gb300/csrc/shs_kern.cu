@@ -1,0 +1,634 @@
+// Forward and adjoint shading kernels for one band count, compiled once per
+// n_bands with -DSHS_NB=n.
+//
+// Forward (Sec. 3.2-3.3, Eq. 8-13), one thread per shading point:
+//   f(x)  = sum_j rotate( ZH of log V'_j , (c_j - x)/|c_j - x| )     pair loop
+//   V(x)  = exp*(f)   (DC isolation, 2^-k scaling, optimal linear step,
+//                      k squarings with the triple product)
+//   H(x)  = rotate( ZH of max(z, 0), n(x) )
+//   B_c   = a_c * L_c . (V * H)
+// Adjoint: the same steps in reverse, recomputing each sphere's terms instead
+// of storing them; scene gradients are reduced warp -> block -> scene scratch.
+//
+// Per-sphere log-visibility (Sec. 3.3.2, Eq. 13): with s = sin(alpha) =
+// min(r / D, 1) and c = cos(alpha), the ZH of -eps * 1[w_z >= c] has
+// coefficients -2 pi eps N_l0 int_c^1 P_l(t) dt, and rotating to direction s_hat
+// gives F_lm = -2 pi eps (int_c^1 P_l) y_lm(s_hat).  The integral is
+//   int_c^1 P_0 = 1 - c,   int_c^1 P_l = (1 - c^2) P_l'(c) / (l (l + 1))  (l >= 1),
+// both from Legendre's equation; d/dc int_c^1 P_l = -P_l(c).
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "generated/shs_sh_gen.cuh"
+#include "shs_internal.h"
+
+#ifndef SHS_NB
+#error "compile with -DSHS_NB=<n_bands>"
+#endif
+
+namespace shs {
+namespace {
+
+constexpr int NB = SHS_NB;
+constexpr int K = NB * NB;
+constexpr int KPAD = (K + 3) / 4 * 4;
+constexpr int NWARP = kBlock / 32;
+using SH = shsgen::SH<NB>;
+
+constexpr float kSqrt4Pi = 3.5449077018110318f;
+constexpr float kInvSqrt4Pi = 0.28209479177387814f;
+constexpr float kInv8Pi = 0.039788735772973836f;
+constexpr float kInv4Pi = 0.07957747154594767f;
+
+__host__ __device__ constexpr int band_of(int i) {
+    int l = 0;
+    while ((l + 1) * (l + 1) <= i) ++l;
+    return l;
+}
+
+__device__ __forceinline__ float fast_sqrt(float x) {   // sqrt(x) = x / sqrt(x), x >= 0
+    return x * rsqrtf(fmaxf(x, 1e-30f));
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Stage the scene's sphere array and lighting into shared memory with bulk
+// asynchronous copies completing on one mbarrier.  Every thread waits with a
+// bound (about one second); the result is block-uniform: false means the copy
+// did not complete, the status word is set and the block must not use the
+// staged data.
+__device__ bool stage_scene(const SceneView& sc, float4* s_sph, float* s_light, uint64_t* bar) {
+    const uint32_t sph_bytes = static_cast<uint32_t>(sc.n_spheres) * 16u;
+    const uint32_t light_bytes = 3u * KPAD * 4u;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     ::"r"(smem_addr(bar)), "r"(sph_bytes + light_bytes) : "memory");
+        if (sph_bytes)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                ::"r"(smem_addr(s_sph)), "l"(sc.spheres), "r"(sph_bytes), "r"(smem_addr(bar))
+                : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+            ::"r"(smem_addr(s_light)), "l"(sc.light), "r"(light_bytes), "r"(smem_addr(bar))
+            : "memory");
+    }
+    bool done = false;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 26) && !done; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.b32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok) : "r"(smem_addr(bar)), "r"(0u) : "memory");
+        done = ok != 0;
+        if (!done && global_ns() - t0 > 1000000000ull) break;
+    }
+    const bool any_failed = __syncthreads_or(!done);
+    if (any_failed && threadIdx.x == 0) atomicExch(sc.status, kDevTimeout);
+    return !any_failed;
+}
+
+// Legendre P_l(c) and P_l'(c) for l < NB (Bonnet recurrence and
+// P'_{l+1} = P'_{l-1} + (2l+1) P_l).
+__device__ __forceinline__ void legendre(float c, float* P, float* dP) {
+    P[0] = 1.f;
+    dP[0] = 0.f;
+    if (NB > 1) {
+        P[1] = c;
+        dP[1] = 1.f;
+    }
+#pragma unroll
+    for (int l = 1; l + 1 < NB; ++l) {
+        P[l + 1] = fmaf((2.f * l + 1.f) / (l + 1.f) * c, P[l], -(float(l) / (l + 1.f)) * P[l - 1]);
+        dP[l + 1] = fmaf(2.f * l + 1.f, P[l], dP[l - 1]);
+    }
+}
+
+// G_l = int_c^1 P_l(t) dt for l < NB; s2 = 1 - c^2 (passed in because it is
+// known more accurately than 1 - c*c).
+__device__ __forceinline__ void cap_integrals(float c, float s2, const float* dP, float* G) {
+    G[0] = 1.f - c;
+#pragma unroll
+    for (int l = 1; l < NB; ++l) G[l] = s2 * dP[l] * (1.f / float(l * (l + 1)));
+}
+
+struct PairGeom {
+    float dx, dy, dz, invD, invD2, s2, c;
+    bool open;
+};
+
+__device__ __forceinline__ PairGeom pair_geometry(float px, float py, float pz, float4 sp) {
+    PairGeom g;
+    g.dx = sp.x - px;
+    g.dy = sp.y - py;
+    g.dz = sp.z - pz;
+    const float D2 = fmaf(g.dx, g.dx, fmaf(g.dy, g.dy, g.dz * g.dz));
+    g.invD = D2 > 0.f ? rsqrtf(D2) : 0.f;     // D = 0: every term below vanishes
+    g.invD2 = g.invD * g.invD;
+    const float r2i = sp.w * sp.w * g.invD2;
+    g.open = r2i < 1.f;
+    g.s2 = fminf(r2i, 1.f);                   // point inside the sphere: hemisphere cap
+    g.c = fast_sqrt(1.f - g.s2);
+    return g;
+}
+
+// acc_i += G_l(i) * Ybar_i(s_hat): the un-normalised log-visibility of one pair.
+__device__ __forceinline__ void pair_forward(float px, float py, float pz, float4 sp, float* acc) {
+    const PairGeom g = pair_geometry(px, py, pz, sp);
+    float P[NB], dP[NB], G[NB];
+    legendre(g.c, P, dP);
+    cap_integrals(g.c, g.s2, dP, G);
+    float Y[K];
+    SH::ybar(g.dx * g.invD, g.dy * g.invD, g.dz * g.invD, Y);
+#pragma unroll
+    for (int i = 0; i < K; ++i) acc[i] = fmaf(G[band_of(i)], Y[i], acc[i]);
+}
+
+// Adjoint of one pair given dfp_i = dLoss/df_i * (-2 pi eps) * NORM_i.
+// Returns the gradient with respect to the sphere centre (the point gets the
+// negative) and the radius.
+__device__ __forceinline__ void pair_backward(float px, float py, float pz, float4 sp,
+                                              const float* dfp, float& gcx, float& gcy,
+                                              float& gcz, float& gr) {
+    const PairGeom g = pair_geometry(px, py, pz, sp);
+    float P[NB], dP[NB], G[NB];
+    legendre(g.c, P, dP);
+    cap_integrals(g.c, g.s2, dP, G);
+    const float sx = g.dx * g.invD, sy = g.dy * g.invD, sz = g.dz * g.invD;
+    float Y[K];
+    SH::ybar(sx, sy, sz, Y);
+    float dG[NB];
+#pragma unroll
+    for (int l = 0; l < NB; ++l) dG[l] = 0.f;
+    float w[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        dG[band_of(i)] = fmaf(dfp[i], Y[i], dG[band_of(i)]);
+        w[i] = dfp[i] * G[band_of(i)];
+    }
+    float gx, gy, gz;
+    SH::ybar_vjp(sx, sy, sz, w, gx, gy, gz);
+    float dc = 0.f;
+#pragma unroll
+    for (int l = 0; l < NB; ++l) dc = fmaf(-dG[l], P[l], dc);
+    // c = sqrt(1 - s2): d c / d s2 = -1 / (2 c); clamped caps carry no gradient
+    const float ds2 = g.open ? __fdividef(-0.5f * dc, g.c) : 0.f;
+    gr = ds2 * 2.f * sp.w * g.invD2;                 // s2 = r^2 / D^2
+    const float dD2 = -ds2 * g.s2 * g.invD2;
+    const float sg = sx * gx + sy * gy + sz * gz;    // s_hat = d / D: tangential part
+    gcx = fmaf(gx - sx * sg, g.invD, 2.f * dD2 * g.dx);
+    gcy = fmaf(gy - sy * sg, g.invD, 2.f * dD2 * g.dy);
+    gcz = fmaf(gz - sz * sg, g.invD, 2.f * dD2 * g.dz);
+}
+
+// Number of squarings: least k >= 0 with |f_hat| <= tau 2^k, capped at kmax.
+__device__ __forceinline__ int scaling_k(const SceneView& sc, float nrm2) {
+    if (sc.fixed_k >= 0) return sc.fixed_k;
+    int k = 0;
+    float thr = sc.tau2;
+    while (k < sc.kmax && nrm2 > thr) {
+        ++k;
+        thr *= 4.f;
+    }
+    return k;
+}
+
+// Clamped-cosine SH for a (not necessarily unit) normal; also returns the unit
+// normal and 1/|n| for the adjoint.
+__device__ __forceinline__ void cosine_lobe(float nx, float ny, float nz, float* H, float& ux,
+                                            float& uy, float& uz, float& inv_len) {
+    const float n2 = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+    inv_len = n2 > 0.f ? rsqrtf(n2) : 0.f;
+    ux = nx * inv_len;
+    uy = ny * inv_len;
+    uz = nz * inv_len;
+    float Y[K];
+    SH::ybar(ux, uy, uz, Y);
+#pragma unroll
+    for (int i = 0; i < K; ++i) H[i] = SH::ahat(band_of(i)) * SH::norm(i) * Y[i];
+}
+
+// Scale the raw pair sums to the log-visibility f.
+__device__ __forceinline__ void finish_f(const SceneView& sc, const float* acc, float* f) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) f[i] = sc.neg_2pi_eps * SH::norm(i) * acc[i];
+}
+
+__device__ __forceinline__ float load_or(const float* p, int64_t i, bool live) {
+    return live ? __ldg(p + i) : 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// forward kernel
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kBlock) forward_kernel(FwdArgs a) {
+    __shared__ __align__(16) float4 s_sph[kMaxSpheres];
+    __shared__ __align__(16) float s_light[3 * KPAD];
+    __shared__ __align__(8) uint64_t s_bar;
+    if (!stage_scene(a.sc, s_sph, s_light, &s_bar)) return;
+
+    const int64_t p = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x;
+    if (p >= a.n_points) return;
+    const float px = __ldg(a.points + 3 * p), py = __ldg(a.points + 3 * p + 1),
+                pz = __ldg(a.points + 3 * p + 2);
+
+    float acc[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) acc[i] = 0.f;
+    const int N = a.sc.n_spheres;
+#pragma unroll 2
+    for (int j = 0; j < N; ++j) pair_forward(px, py, pz, s_sph[j], acc);
+
+    float f[K];
+    finish_f(a.sc, acc, f);
+    float nrm2 = 0.f;
+#pragma unroll
+    for (int i = 1; i < K; ++i) nrm2 = fmaf(f[i], f[i], nrm2);
+    const int k = scaling_k(a.sc, nrm2);
+    const float scale = ldexpf(1.f, -k);
+    const float a0 = expf(nrm2 * scale * scale * kInv8Pi);
+    float S[K];
+    S[0] = a0 * kSqrt4Pi;
+#pragma unroll
+    for (int i = 1; i < K; ++i) S[i] = a0 * (f[i] * scale);
+    for (int t = 0; t < k; ++t) {
+        float T[K];
+        SH::sqr(S, T);
+#pragma unroll
+        for (int i = 0; i < K; ++i) S[i] = T[i];
+    }
+    const float e0 = expf(f[0] * kInvSqrt4Pi);
+    float V[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) V[i] = e0 * S[i];
+
+    float H[K], ux, uy, uz, il;
+    cosine_lobe(__ldg(a.normals + 3 * p), __ldg(a.normals + 3 * p + 1), __ldg(a.normals + 3 * p + 2),
+                H, ux, uy, uz, il);
+    float W[K];
+    SH::mul(V, H, W);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float d = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) d = fmaf(s_light[c * KPAD + i], W[i], d);
+        a.radiance[3 * p + c] = __ldg(a.albedo + 3 * p + c) * d;
+    }
+    if (a.saved_f) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) a.saved_f[i * a.n_points + p] = f[i];
+        a.saved_k[p] = k;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// backward kernel
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum four values over the warp; lane l returns the total of value (l >> 3).
+__device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v3, int lane) {
+    const bool h16 = lane & 16;
+    float ka = h16 ? v2 : v0, kb = h16 ? v3 : v1;
+    ka += __shfl_xor_sync(0xffffffffu, h16 ? v0 : v2, 16);
+    kb += __shfl_xor_sync(0xffffffffu, h16 ? v1 : v3, 16);
+    const bool h8 = lane & 8;
+    float k = h8 ? kb : ka;
+    k += __shfl_xor_sync(0xffffffffu, h8 ? ka : kb, 8);
+    k += __shfl_xor_sync(0xffffffffu, k, 4);
+    k += __shfl_xor_sync(0xffffffffu, k, 2);
+    k += __shfl_xor_sync(0xffffffffu, k, 1);
+    return k;
+}
+
+// Layout of one block's reduced scene gradient (E floats):
+//   [0, 3K)          d_light, channel-major
+//   [3K]             loss
+//   [3K+1, 3K+1+4N)  per sphere (d cx, d cy, d cz, d r)
+__global__ void __launch_bounds__(kBlock) backward_kernel(BwdArgs a) {
+    extern __shared__ __align__(16) float4 dyn[];
+    __shared__ __align__(16) float s_light[3 * KPAD];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ float s_dl[NWARP][3 * K + 1];
+    __shared__ bool s_last;
+    const int N = a.sc.n_spheres;
+    float4* s_sph = dyn;                  // [N]
+    float* s_acc = reinterpret_cast<float*>(dyn + N);   // [NWARP][4N]
+    if (!stage_scene(a.sc, s_sph, s_light, &s_bar)) return;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < NWARP * 4 * N; e += kBlock) s_acc[e] = 0.f;
+    for (int e = threadIdx.x; e < NWARP * (3 * K + 1); e += kBlock) (&s_dl[0][0])[e] = 0.f;
+    __syncthreads();
+
+    const int64_t P = a.n_points;
+    const int64_t ntiles = (P + kBlock - 1) / kBlock;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t p = tile * kBlock + threadIdx.x;
+    const bool live = p < P;
+    const int64_t q = live ? p : 0;
+    const float px = load_or(a.points, 3 * q, live), py = load_or(a.points, 3 * q + 1, live),
+                pz = load_or(a.points, 3 * q + 2, live);
+
+    // ---- log-visibility f: saved by the forward pass or recomputed
+    float f[K];
+    int k;
+    if (a.saved_f) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) f[i] = load_or(a.saved_f, i * P + q, live);
+        k = live ? min(max(a.saved_k[q], 0), kMaxK) : 0;   // a foreign buffer cannot overrun hist
+    } else {
+        float acc[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) acc[i] = 0.f;
+#pragma unroll 2
+        for (int j = 0; j < N; ++j) pair_forward(px, py, pz, s_sph[j], acc);
+        finish_f(a.sc, acc, f);
+        k = -1;
+    }
+    float nrm2 = 0.f;
+#pragma unroll
+    for (int i = 1; i < K; ++i) nrm2 = fmaf(f[i], f[i], nrm2);
+    if (k < 0) k = scaling_k(a.sc, nrm2);
+
+    // ---- recompute the exponential, keeping the operand of every squaring
+    const float scale = ldexpf(1.f, -k);
+    const float a0 = expf(nrm2 * scale * scale * kInv8Pi);
+    float g[K];
+    g[0] = 0.f;
+#pragma unroll
+    for (int i = 1; i < K; ++i) g[i] = f[i] * scale;
+    float S[K];
+    S[0] = a0 * kSqrt4Pi;
+#pragma unroll
+    for (int i = 1; i < K; ++i) S[i] = a0 * g[i];
+    float hist[kMaxK][K];
+    for (int t = 0; t < k; ++t) {
+        float T[K];
+        SH::sqr(S, T);
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            hist[t][i] = S[i];
+            S[i] = T[i];
+        }
+    }
+    const float e0 = expf(f[0] * kInvSqrt4Pi);
+    float V[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) V[i] = e0 * S[i];
+    float H[K], ux, uy, uz, il;
+    cosine_lobe(load_or(a.normals, 3 * q, live), load_or(a.normals, 3 * q + 1, live),
+                load_or(a.normals, 3 * q + 2, live), H, ux, uy, uz, il);
+    float W[K];
+    SH::mul(V, H, W);
+
+    // ---- shading adjoint: B_c = a_c L_c . W
+    float dB[3], alb[3], loss = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        alb[c] = load_or(a.albedo, 3 * q + c, live);
+        if (a.target) {
+            const float r = load_or(a.radiance, 3 * q + c, live) - load_or(a.target, 3 * q + c, live);
+            dB[c] = r;
+            loss = fmaf(0.5f * r, r, loss);
+        } else {
+            dB[c] = load_or(a.d_radiance, 3 * q + c, live);
+        }
+    }
+    float dW[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) dW[i] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float u = alb[c] * dB[c];
+        float lw = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const float L = s_light[c * KPAD + i];
+            lw = fmaf(L, W[i], lw);
+            dW[i] = fmaf(u, L, dW[i]);
+        }
+        if (live && a.d_albedo) a.d_albedo[3 * q + c] = dB[c] * lw;
+        if (a.d_light) {
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const float v = warp_sum(u * W[i]);
+                if (lane == 0) s_dl[warp][c * K + i] += v;
+            }
+        }
+    }
+    if (a.target) {
+        const float v = warp_sum(loss);
+        if (lane == 0) s_dl[warp][3 * K] += v;
+    }
+    float dV[K], dH[K];
+    SH::mul(dW, H, dV);                     // C is symmetric: adjoint of a*b is d*b
+    SH::mul(dW, V, dH);
+
+    // ---- normal adjoint through H = A_hat_l NORM_i Ybar_i(n / |n|)
+    if (live && a.d_normals) {
+        float wn[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) wn[i] = dH[i] * SH::ahat(band_of(i)) * SH::norm(i);
+        float gx, gy, gz;
+        SH::ybar_vjp(ux, uy, uz, wn, gx, gy, gz);
+        const float ug = ux * gx + uy * gy + uz * gz;
+        a.d_normals[3 * q] = (gx - ux * ug) * il;
+        a.d_normals[3 * q + 1] = (gy - uy * ug) * il;
+        a.d_normals[3 * q + 2] = (gz - uz * ug) * il;
+    }
+
+    // ---- exponential adjoint
+    float de0 = 0.f, dS[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        de0 = fmaf(dV[i], S[i], de0);
+        dS[i] = e0 * dV[i];
+    }
+    for (int t = k - 1; t >= 0; --t) {
+        float Ht[K], T[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) Ht[i] = hist[t][i];
+        SH::mul(dS, Ht, T);
+#pragma unroll
+        for (int i = 0; i < K; ++i) dS[i] = 2.f * T[i];
+    }
+    float da = dS[0] * kSqrt4Pi;
+#pragma unroll
+    for (int i = 1; i < K; ++i) da = fmaf(dS[i], g[i], da);
+    float dfp[K];
+    dfp[0] = de0 * e0 * kInvSqrt4Pi;
+#pragma unroll
+    for (int i = 1; i < K; ++i) dfp[i] = fmaf(a0, dS[i], da * a0 * kInv4Pi * g[i]) * scale;
+#pragma unroll
+    for (int i = 0; i < K; ++i) dfp[i] *= a.sc.neg_2pi_eps * SH::norm(i);
+
+    // ---- pair adjoints
+    const bool want_sph = a.d_centers || a.d_radii;
+    if (want_sph || a.d_points) {
+        float gpx = 0.f, gpy = 0.f, gpz = 0.f;
+        float* my_acc = s_acc + warp * 4 * N;
+#pragma unroll 1
+        for (int j = 0; j < N; ++j) {
+            float gcx, gcy, gcz, gr;
+            pair_backward(px, py, pz, s_sph[j], dfp, gcx, gcy, gcz, gr);
+            gpx -= gcx;
+            gpy -= gcy;
+            gpz -= gcz;
+            if (want_sph) {
+                const float v = warp_sum4(gcx, gcy, gcz, gr, lane);
+                if ((lane & 7) == 0) my_acc[4 * j + (lane >> 3)] += v;
+            }
+        }
+        if (live && a.d_points) {
+            a.d_points[3 * q] = gpx;
+            a.d_points[3 * q + 1] = gpy;
+            a.d_points[3 * q + 2] = gpz;
+        }
+    }
+    }  // tile loop
+
+    // ---- block reduction, then one scene-level reduction
+    __syncthreads();
+    const int E = 3 * K + 1 + 4 * N;
+    float* out = a.partials + static_cast<size_t>(blockIdx.x) * a.partial_stride;
+    const bool det = a.counter == nullptr;
+    for (int e = threadIdx.x; e < E; e += kBlock) {
+        float v = 0.f;
+        if (e <= 3 * K) {
+#pragma unroll
+            for (int w = 0; w < NWARP; ++w) v += s_dl[w][e];
+        } else {
+            const int s = e - (3 * K + 1);
+#pragma unroll
+            for (int w = 0; w < NWARP; ++w) v += s_acc[w * 4 * N + s];
+        }
+        if (det) out[e] = v;
+        else atomicAdd(a.partials + e, v);
+    }
+    if (det) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int e = threadIdx.x; e < E; e += kBlock) {
+        const float v = __ldcg(a.partials + e);
+        a.partials[e] = 0.f;
+        if (e < 3 * K) {
+            if (a.d_light) a.d_light[e] = v;
+        } else if (e == 3 * K) {
+            if (a.loss) *a.loss = v;
+        } else {
+            const int s = e - (3 * K + 1), j = s >> 2, comp = s & 3;
+            if (comp < 3) {
+                if (a.d_centers) a.d_centers[3 * j + comp] = v;
+            } else if (a.d_radii) {
+                a.d_radii[j] = v;
+            }
+        }
+    }
+    if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+// Deterministic finish: out[e] = sum over blocks b (in order) of partials[b][e].
+// One warp per 32 consecutive elements and per slice of blocks; the slices are
+// then added in fixed order.
+__global__ void __launch_bounds__(256) reduce_partials_kernel(BwdArgs a, int nblk) {
+    __shared__ float s[8][33];
+    const int N = a.sc.n_spheres;
+    const int E = 3 * K + 1 + 4 * N;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    float v = 0.f;
+    if (e < E)
+        for (int b = warp; b < nblk; b += 8) v += __ldcg(a.partials + static_cast<size_t>(b) * a.partial_stride + e);
+    s[warp][lane] = v;
+    __syncthreads();
+    if (warp != 0 || e >= E) return;
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += s[w][lane];
+    if (e < 3 * K) {
+        if (a.d_light) a.d_light[e] = t;
+    } else if (e == 3 * K) {
+        if (a.loss) *a.loss = t;
+    } else {
+        const int q = e - (3 * K + 1), j = q >> 2, comp = q & 3;
+        if (comp < 3) {
+            if (a.d_centers) a.d_centers[3 * j + comp] = t;
+        } else if (a.d_radii) {
+            a.d_radii[j] = t;
+        }
+    }
+}
+
+size_t backward_dyn_smem(int n_spheres) {
+    return static_cast<size_t>(n_spheres) * 16u * (1 + NWARP);
+}
+
+}  // namespace
+
+template <>
+int backward_blocks_per_sm<NB>(int n_spheres) {
+    cudaFuncSetAttribute(backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(backward_dyn_smem(kMaxSpheres)));
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, backward_kernel, kBlock,
+                                                      backward_dyn_smem(n_spheres)) != cudaSuccess || nb < 1)
+        nb = 1;
+    return nb;
+}
+
+template <>
+cudaError_t launch_forward<NB>(const FwdArgs& a, cudaStream_t s) {
+    if (a.n_points <= 0) return cudaSuccess;
+    const int64_t blocks = (a.n_points + kBlock - 1) / kBlock;
+    forward_kernel<<<static_cast<unsigned>(blocks), kBlock, 0, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_backward<NB>(const BwdArgs& a, cudaStream_t s) {
+    if (a.n_points <= 0) return cudaSuccess;
+    const size_t smem = backward_dyn_smem(a.sc.n_spheres);
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        static_cast<int>(backward_dyn_smem(kMaxSpheres)));
+    cudaError_t err = attr;
+    if (err != cudaSuccess) return err;
+    backward_kernel<<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
+    count_launch();
+    err = cudaGetLastError();
+    if (err != cudaSuccess || a.counter != nullptr) return err;
+    const int E = 3 * K + 1 + 4 * a.sc.n_spheres;
+    reduce_partials_kernel<<<(E + 31) / 32, 256, 0, s>>>(a, a.grid);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace shs
