@@ -94,6 +94,30 @@ def ybar_polys(n):
     return out
 
 
+def monomials(deg):
+    """Exponent triples (a, b, c) with a + b + c = deg, in emission order."""
+    return [(a, b, deg - a - b) for a in range(deg, -1, -1) for b in range(deg - a, -1, -1)]
+
+
+def homogeneous_polys(n):
+    """Ybar_i made homogeneous of degree l_i by multiplying each lower-degree
+    term by (x^2 + y^2 + z^2)^j (equal on the unit sphere).  Returns a list of
+    dicts {(a, b, c): Fraction}."""
+    R2 = p_add(p_add(p_mul(X, X), p_mul(Y, Y)), p_mul(Z, Z))
+    out = []
+    for i, p in enumerate(ybar_polys(n)):
+        l = int(math.isqrt(i))
+        h = {}
+        for (a, b, c), v in p.items():
+            t = {(a, b, c): v}
+            for _ in range((l - a - b - c) // 2):
+                t = p_mul(t, R2)
+            h = p_add(h, t)
+        assert all(sum(k) == l for k in h)
+        out.append(h)
+    return out
+
+
 def dfact(k):
     return math.prod(range(k, 0, -2)) if k > 0 else 1
 
@@ -339,11 +363,90 @@ def emit_gaunt(n, C):
             if not terms:
                 lines.append(f"o[{i}] = 0.0f;")
                 continue
+            lines.append(f"o[{i}] = {balanced_sum(terms)};")
+    return mul_lines, sqr_lines
+
+
+def balanced_sum(terms, chains=4):
+    """sum of c * t over (c, t) as up to ``chains`` interleaved FMA chains added
+    pairwise: rounding error grows with len/chains instead of len, and the
+    chains are independent instructions."""
+    groups = [terms[g::chains] for g in range(min(chains, len(terms)))]
+    exprs = []
+    for grp in groups:
+        e = f"{grp[0][0]} * {grp[0][1]}"
+        for c, t in grp[1:]:
+            e = f"fmaf({c}, {t}, {e})"
+        exprs.append(e)
+    while len(exprs) > 1:
+        nxt = [f"({exprs[k]} + {exprs[k + 1]})" for k in range(0, len(exprs) - 1, 2)]
+        if len(exprs) % 2:
+            nxt.append(exprs[-1])
+        exprs = nxt
+    return exprs[0]
+
+
+def emit_phi(n):
+    """Code for the pair adjoint's per-band polynomials.
+
+    phi_coeffs(w, q): q holds, for each band l, the monomial coefficients of
+      Phi_l(d) = sum_m w_lm Hbar_lm(d), Hbar the homogeneous Ybar (degree l).
+    phi_eval(x, y, z, q, v, gx, gy, gz): v[l] = Phi_l(x, y, z) and its gradient
+      (gx[l], gy[l], gz[l]) for l < n, at an unnormalised direction."""
+    H = homogeneous_polys(n)
+    offs, nq = [], 0
+    for l in range(n):
+        offs.append(nq)
+        nq += len(monomials(l))
+    coef_lines = []
+    for l in range(n):
+        for ai, mono in enumerate(monomials(l)):
+            terms = []
+            for m in range(-l, l + 1):
+                i = l * l + l + m
+                v = H[i].get(mono, 0)
+                if v != 0:
+                    terms.append((fmt(("c", float(v))), f"w[{i}]"))
+            if not terms:
+                coef_lines.append(f"q[{offs[l] + ai}] = 0.0f;")
+                continue
             expr = f"{terms[0][0]} * {terms[0][1]}"
             for c, t in terms[1:]:
                 expr = f"fmaf({c}, {t}, {expr})"
-            lines.append(f"o[{i}] = {expr};")
-    return mul_lines, sqr_lines
+            coef_lines.append(f"q[{offs[l] + ai}] = {expr};")
+    ev = []
+    name = {(0, 0, 0): "1.0f"}
+    for deg in range(1, n):
+        for (a, b, c) in monomials(deg):
+            if a > 0:
+                src, f = (a - 1, b, c), "x"
+            elif b > 0:
+                src, f = (a, b - 1, c), "y"
+            else:
+                src, f = (a, b, c - 1), "z"
+            nm = f"m{a}_{b}_{c}"
+            ev.append(f"const float {nm} = {f}" + ("" if src == (0, 0, 0) else f" * {name[src]}") + ";")
+            name[(a, b, c)] = nm
+    for l in range(n):
+        monos = monomials(l)
+        vals = [f"q[{offs[l] + ai}]" + ("" if mono == (0, 0, 0) else f" * {name[mono]}")
+                for ai, mono in enumerate(monos)]
+        ev.append(f"v[{l}] = {' + '.join(vals)};")
+        for comp, g in ((0, "gx"), (1, "gy"), (2, "gz")):
+            terms = []
+            for ai, mono in enumerate(monos):
+                e = mono[comp]
+                if e == 0:
+                    continue
+                lower = list(mono)
+                lower[comp] -= 1
+                lower = tuple(lower)
+                base = f"q[{offs[l] + ai}]"
+                if e > 1:
+                    base = f"{float(e)}f * {base}"
+                terms.append(base + ("" if lower == (0, 0, 0) else f" * {name[lower]}"))
+            ev.append(f"{g}[{l}] = {' + '.join(terms) if terms else '0.0f'};")
+    return nq, coef_lines, ev
 
 
 def indent(lines, k=8):
@@ -396,6 +499,16 @@ def generate():
         parts.append("                                                    float& gx, float& gy, float& gz) {")
         parts.append("        (void)x; (void)y; (void)z; (void)w;")
         parts.append(indent([ln for ln in vjp if not ln.startswith("Y[")]))
+        parts.append("    }")
+        nq, coef_l, ev_l = emit_phi(n)
+        parts.append(f"    static constexpr int NQ = {nq};   // monomial coefficients over all bands")
+        parts.append("    __device__ __forceinline__ static void phi_coeffs(const float* w, float* q) {")
+        parts.append(indent(coef_l))
+        parts.append("    }")
+        parts.append("    __device__ __forceinline__ static void phi_eval(float x, float y, float z, const float* q,")
+        parts.append("                                                    float* v, float* gx, float* gy, float* gz) {")
+        parts.append("        (void)x; (void)y; (void)z;")
+        parts.append(indent(ev_l))
         parts.append("    }")
         parts.append("    __device__ __forceinline__ static void mul(const float* a, const float* b, float* o) {")
         parts.append(indent(mul_l))

@@ -197,6 +197,44 @@ __device__ __forceinline__ void pair_backward(float px, float py, float pz, floa
     gcz = fmaf(gz - sz * sg, g.invD, 2.f * dD2 * g.dz);
 }
 
+// Adjoint of one pair through the per-band homogeneous polynomials: with
+// Phi_l(d) = sum_m dfp_lm Hbar_lm(d) (coefficients q, see SH::phi_coeffs) the
+// pair's contribution to the loss is Psi(d, r) = sum_l G_l(c) D^-l Phi_l(d), so
+//   dPsi/dd = sum_l G_l D^-l (grad Phi_l - l Phi_l d / D^2) + 2 dPsi/dD2 d,
+// one polynomial value and gradient per band instead of the SH basis and its
+// reverse sweep.
+__device__ __forceinline__ void pair_backward_phi(float px, float py, float pz, float4 sp,
+                                                  const float* q, float& gcx, float& gcy,
+                                                  float& gcz, float& gr) {
+    const PairGeom g = pair_geometry(px, py, pz, sp);
+    float P[NB], dP[NB], G[NB];
+    legendre(g.c, P, dP);
+    cap_integrals(g.c, g.s2, dP, G);
+    float v[NB], gx[NB], gy[NB], gz[NB];
+    SH::phi_eval(g.dx, g.dy, g.dz, q, v, gx, gy, gz);
+    float ip = 1.f, dc = 0.f, ax = 0.f, ay = 0.f, az = 0.f, rad = 0.f;
+#pragma unroll
+    for (int l = 0; l < NB; ++l) {
+        const float sl = G[l] * ip;              // G_l D^-l
+        dc = fmaf(-P[l], v[l] * ip, dc);         // d/dc int_c^1 P_l = -P_l(c)
+        ax = fmaf(sl, gx[l], ax);
+        ay = fmaf(sl, gy[l], ay);
+        az = fmaf(sl, gz[l], az);
+        if (l > 0) rad = fmaf(sl * float(l), v[l], rad);
+        ip *= g.invD;
+    }
+    const float ds2 = g.open ? __fdividef(-0.5f * dc, g.c) : 0.f;
+    gr = ds2 * 2.f * sp.w * g.invD2;
+    const float coef = 2.f * (-ds2 * g.s2 * g.invD2) - rad * g.invD2;
+    gcx = fmaf(coef, g.dx, ax);
+    gcy = fmaf(coef, g.dy, ay);
+    gcz = fmaf(coef, g.dz, az);
+}
+
+// The polynomial route needs sum_l (l+1)(l+2)/2 coefficients per point; above
+// 5 bands that no longer fits in registers next to the tail state.
+constexpr bool kUsePhi = NB <= 5;
+
 // Number of squarings: least k >= 0 with |f_hat| <= tau 2^k, capped at kmax.
 __device__ __forceinline__ int scaling_k(const SceneView& sc, float nrm2) {
     if (sc.fixed_k >= 0) return sc.fixed_k;
@@ -488,18 +526,48 @@ __global__ void __launch_bounds__(kBlock) backward_kernel(BwdArgs a) {
     // ---- pair adjoints
     const bool want_sph = a.d_centers || a.d_radii;
     if (want_sph || a.d_points) {
+        float phq[kUsePhi ? SH::NQ : 1];
+        if constexpr (kUsePhi) SH::phi_coeffs(dfp, phq);
+        auto pair = [&](float4 sp, float& gcx, float& gcy, float& gcz, float& gr) {
+            if constexpr (kUsePhi) pair_backward_phi(px, py, pz, sp, phq, gcx, gcy, gcz, gr);
+            else pair_backward(px, py, pz, sp, dfp, gcx, gcy, gcz, gr);
+        };
         float gpx = 0.f, gpy = 0.f, gpz = 0.f;
         float* my_acc = s_acc + warp * 4 * N;
+        if (want_sph && N >= 32) {
+            // Skewed order: at step t lane l handles sphere (l + t) mod N, so the
+            // 32 lanes update 32 distinct slots of the warp's accumulator row
+            // with plain shared-memory read-modify-writes (no cross-lane sums).
+            float4* row = reinterpret_cast<float4*>(my_acc);
+            int j = lane;
 #pragma unroll 1
-        for (int j = 0; j < N; ++j) {
-            float gcx, gcy, gcz, gr;
-            pair_backward(px, py, pz, s_sph[j], dfp, gcx, gcy, gcz, gr);
-            gpx -= gcx;
-            gpy -= gcy;
-            gpz -= gcz;
-            if (want_sph) {
-                const float v = warp_sum4(gcx, gcy, gcz, gr, lane);
-                if ((lane & 7) == 0) my_acc[4 * j + (lane >> 3)] += v;
+            for (int t = 0; t < N; ++t) {
+                float gcx, gcy, gcz, gr;
+                pair(s_sph[j], gcx, gcy, gcz, gr);
+                gpx -= gcx;
+                gpy -= gcy;
+                gpz -= gcz;
+                float4 acc = row[j];
+                acc.x += gcx;
+                acc.y += gcy;
+                acc.z += gcz;
+                acc.w += gr;
+                row[j] = acc;
+                __syncwarp();
+                j = (j + 1 == N) ? 0 : j + 1;
+            }
+        } else {
+#pragma unroll 1
+            for (int j = 0; j < N; ++j) {
+                float gcx, gcy, gcz, gr;
+                pair(s_sph[j], gcx, gcy, gcz, gr);
+                gpx -= gcx;
+                gpy -= gcy;
+                gpz -= gcz;
+                if (want_sph) {
+                    const float v = warp_sum4(gcx, gcy, gcz, gr, lane);
+                    if ((lane & 7) == 0) my_acc[4 * j + (lane >> 3)] += v;
+                }
             }
         }
         if (live && a.d_points) {
