@@ -14,6 +14,9 @@ For each supported band count n (K = n^2 coefficients) it emits:
 * ``mul(a, b, o)``: the truncated SH triple product o = a * b,
   o_i = sum_jk C_ijk a_j b_k (Eq. 7), unrolled over the nonzero C_ijk.
 * ``sqr(a, o)``: o = a * a using the j <-> k symmetry of C.
+* the monomial-basis pair terms (``accumulate``, ``mono_to_f``) and the
+  per-band gradient polynomials of the pair adjoint (``grad_coeffs``,
+  ``grad_eval``), from the homogeneous form of Ybar (equal on the unit sphere).
 * tables: NORM[i], AHAT[l] (clamped-cosine convolution constants, Eq. 10-11).
 
 C_ijk is computed here by exact integration of monomials over the sphere,
@@ -386,37 +389,11 @@ def balanced_sum(terms, chains=4):
     return exprs[0]
 
 
-def emit_phi(n):
-    """Code for the pair adjoint's per-band polynomials.
-
-    phi_coeffs(w, q): q holds, for each band l, the monomial coefficients of
-      Phi_l(d) = sum_m w_lm Hbar_lm(d), Hbar the homogeneous Ybar (degree l).
-    phi_eval(x, y, z, q, v, gx, gy, gz): v[l] = Phi_l(x, y, z) and its gradient
-      (gx[l], gy[l], gz[l]) for l < n, at an unnormalised direction."""
-    H = homogeneous_polys(n)
-    offs, nq = [], 0
-    for l in range(n):
-        offs.append(nq)
-        nq += len(monomials(l))
-    coef_lines = []
-    for l in range(n):
-        for ai, mono in enumerate(monomials(l)):
-            terms = []
-            for m in range(-l, l + 1):
-                i = l * l + l + m
-                v = H[i].get(mono, 0)
-                if v != 0:
-                    terms.append((fmt(("c", float(v))), f"w[{i}]"))
-            if not terms:
-                coef_lines.append(f"q[{offs[l] + ai}] = 0.0f;")
-                continue
-            expr = f"{terms[0][0]} * {terms[0][1]}"
-            for c, t in terms[1:]:
-                expr = f"fmaf({c}, {t}, {expr})"
-            coef_lines.append(f"q[{offs[l] + ai}] = {expr};")
-    ev = []
+def _mono_lines(maxdeg, prefix="m"):
+    """Straight-line products for every monomial of degree 1..maxdeg in x, y, z."""
     name = {(0, 0, 0): "1.0f"}
-    for deg in range(1, n):
+    lines = []
+    for deg in range(1, maxdeg + 1):
         for (a, b, c) in monomials(deg):
             if a > 0:
                 src, f = (a - 1, b, c), "x"
@@ -424,29 +401,72 @@ def emit_phi(n):
                 src, f = (a, b - 1, c), "y"
             else:
                 src, f = (a, b, c - 1), "z"
-            nm = f"m{a}_{b}_{c}"
-            ev.append(f"const float {nm} = {f}" + ("" if src == (0, 0, 0) else f" * {name[src]}") + ";")
+            nm = f"{prefix}{a}_{b}_{c}"
+            lines.append(f"const float {nm} = {f}" + ("" if src == (0, 0, 0) else f" * {name[src]}") + ";")
             name[(a, b, c)] = nm
+    return lines, name
+
+
+def emit_monomial_route(n):
+    """Code for the monomial-basis pair terms (used for n <= 5).
+
+    accumulate(G, x, y, z, acc): acc[off_l + a] += G[l] * x^a1 y^a2 z^a3 for
+      every monomial of degree l < n (forward pair term in monomial form).
+    mono_to_f(acc, f): f_i = sum_a Hbar_i[a] acc[off_l + a], Hbar_i the
+      homogeneous Ybar_i, i.e. the un-normalised log-visibility coefficients.
+    grad_coeffs(w, gq): for bands l >= 1, the coefficients over monomials of
+      degree l-1 of the three partial derivatives of Phi_l = sum_m w_lm Hbar_lm.
+    grad_eval(x, y, z, gq, gx, gy, gz): (gx, gy, gz)[l-1] = grad Phi_l(x, y, z).
+    """
+    H = homogeneous_polys(n)
+    offs, na = [], 0
     for l in range(n):
-        monos = monomials(l)
-        vals = [f"q[{offs[l] + ai}]" + ("" if mono == (0, 0, 0) else f" * {name[mono]}")
-                for ai, mono in enumerate(monos)]
-        ev.append(f"v[{l}] = {' + '.join(vals)};")
+        offs.append(na)
+        na += len(monomials(l))
+    ml, name = _mono_lines(n - 1)
+    acc = []
+    for l in range(n):
+        for ai, mono in enumerate(monomials(l)):
+            m = "1.0f" if mono == (0, 0, 0) else name[mono]
+            acc.append(f"acc[{offs[l] + ai}] = fmaf(G[{l}], {m}, acc[{offs[l] + ai}]);")
+    m2f = []
+    for i in range(n * n):
+        l = int(math.isqrt(i))
+        terms = [(fmt(("c", float(v))), f"acc[{offs[l] + monomials(l).index(mono)}]")
+                 for mono, v in sorted(H[i].items()) if v != 0]
+        m2f.append(f"f[{i}] = {balanced_sum(terms)};")
+    goffs, ng = [], 0
+    for l in range(1, n):
+        goffs.append(ng)
+        ng += 3 * len(monomials(l - 1))
+    gc = []
+    for l in range(1, n):
+        lower = monomials(l - 1)
+        for comp in range(3):
+            for bi, beta in enumerate(lower):
+                up = list(beta)
+                up[comp] += 1
+                up = tuple(up)
+                factor = up[comp]
+                terms = []
+                for m in range(-l, l + 1):
+                    i = l * l + l + m
+                    v = H[i].get(up, 0)
+                    if v != 0:
+                        terms.append((fmt(("c", float(v) * factor)), f"w[{i}]"))
+                o = goffs[l - 1] + comp * len(lower) + bi
+                gc.append(f"gq[{o}] = {balanced_sum(terms) if terms else '0.0f'};")
+    ge_m, gname = _mono_lines(max(n - 2, 0), prefix="u")
+    ge = list(ge_m)
+    for l in range(1, n):
+        lower = monomials(l - 1)
         for comp, g in ((0, "gx"), (1, "gy"), (2, "gz")):
             terms = []
-            for ai, mono in enumerate(monos):
-                e = mono[comp]
-                if e == 0:
-                    continue
-                lower = list(mono)
-                lower[comp] -= 1
-                lower = tuple(lower)
-                base = f"q[{offs[l] + ai}]"
-                if e > 1:
-                    base = f"{float(e)}f * {base}"
-                terms.append(base + ("" if lower == (0, 0, 0) else f" * {name[lower]}"))
-            ev.append(f"{g}[{l}] = {' + '.join(terms) if terms else '0.0f'};")
-    return nq, coef_lines, ev
+            for bi, beta in enumerate(lower):
+                o = goffs[l - 1] + comp * len(lower) + bi
+                terms.append(f"gq[{o}]" + ("" if beta == (0, 0, 0) else f" * {gname[beta]}"))
+            ge.append(f"{g}[{l - 1}] = {' + '.join(terms)};")
+    return na, ng, ml, acc, m2f, gc, ge
 
 
 def indent(lines, k=8):
@@ -500,15 +520,24 @@ def generate():
         parts.append("        (void)x; (void)y; (void)z; (void)w;")
         parts.append(indent([ln for ln in vjp if not ln.startswith("Y[")]))
         parts.append("    }")
-        nq, coef_l, ev_l = emit_phi(n)
-        parts.append(f"    static constexpr int NQ = {nq};   // monomial coefficients over all bands")
-        parts.append("    __device__ __forceinline__ static void phi_coeffs(const float* w, float* q) {")
-        parts.append(indent(coef_l))
-        parts.append("    }")
-        parts.append("    __device__ __forceinline__ static void phi_eval(float x, float y, float z, const float* q,")
-        parts.append("                                                    float* v, float* gx, float* gy, float* gz) {")
+        na, ng, ml, acc_l, m2f_l, gc_l, ge_l = emit_monomial_route(n)
+        parts.append(f"    static constexpr int NA = {na};   // monomials of degree < n")
+        parts.append(f"    static constexpr int NG = {max(ng, 1)};   // gradient coefficients, bands >= 1")
+        parts.append("    __device__ __forceinline__ static void accumulate(const float* G, float x, float y, float z, float* acc) {")
         parts.append("        (void)x; (void)y; (void)z;")
-        parts.append(indent(ev_l))
+        parts.append(indent(ml + acc_l))
+        parts.append("    }")
+        parts.append("    __device__ __forceinline__ static void mono_to_f(const float* acc, float* f) {")
+        parts.append(indent(m2f_l))
+        parts.append("    }")
+        parts.append("    __device__ __forceinline__ static void grad_coeffs(const float* w, float* gq) {")
+        parts.append("        (void)w; (void)gq;")
+        parts.append(indent(gc_l))
+        parts.append("    }")
+        parts.append("    __device__ __forceinline__ static void grad_eval(float x, float y, float z, const float* gq,")
+        parts.append("                                                     float* gx, float* gy, float* gz) {")
+        parts.append("        (void)x; (void)y; (void)z; (void)gq; (void)gx; (void)gy; (void)gz;")
+        parts.append(indent(ge_l))
         parts.append("    }")
         parts.append("    __device__ __forceinline__ static void mul(const float* a, const float* b, float* o) {")
         parts.append(indent(mul_l))

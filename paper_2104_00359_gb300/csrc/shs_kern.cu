@@ -148,16 +148,29 @@ __device__ __forceinline__ PairGeom pair_geometry(float px, float py, float pz, 
     return g;
 }
 
-// acc_i += G_l(i) * Ybar_i(s_hat): the un-normalised log-visibility of one pair.
+// Up to 5 bands the pair terms are accumulated in the monomial basis: for each
+// band l the pair adds G_l(c) x^a y^b z^c (a+b+c = l) at s_hat, and the
+// harmonic combination is taken once per point (mono_to_f).  Above 5 bands the
+// number of monomials outgrows the registers and the SH basis is accumulated
+// directly.
+constexpr bool kMono = NB <= 5;
+constexpr int NACC = kMono ? SH::NA : K;
+
+// One pair's un-normalised log-visibility terms, added to acc.
 __device__ __forceinline__ void pair_forward(float px, float py, float pz, float4 sp, float* acc) {
     const PairGeom g = pair_geometry(px, py, pz, sp);
     float P[NB], dP[NB], G[NB];
     legendre(g.c, P, dP);
     cap_integrals(g.c, g.s2, dP, G);
-    float Y[K];
-    SH::ybar(g.dx * g.invD, g.dy * g.invD, g.dz * g.invD, Y);
+    const float sx = g.dx * g.invD, sy = g.dy * g.invD, sz = g.dz * g.invD;
+    if constexpr (kMono) {
+        SH::accumulate(G, sx, sy, sz, acc);
+    } else {
+        float Y[K];
+        SH::ybar(sx, sy, sz, Y);
 #pragma unroll
-    for (int i = 0; i < K; ++i) acc[i] = fmaf(G[band_of(i)], Y[i], acc[i]);
+        for (int i = 0; i < K; ++i) acc[i] = fmaf(G[band_of(i)], Y[i], acc[i]);
+    }
 }
 
 // Adjoint of one pair given dfp_i = dLoss/df_i * (-2 pi eps) * NORM_i.
@@ -197,43 +210,45 @@ __device__ __forceinline__ void pair_backward(float px, float py, float pz, floa
     gcz = fmaf(gz - sz * sg, g.invD, 2.f * dD2 * g.dz);
 }
 
-// Adjoint of one pair through the per-band homogeneous polynomials: with
-// Phi_l(d) = sum_m dfp_lm Hbar_lm(d) (coefficients q, see SH::phi_coeffs) the
-// pair's contribution to the loss is Psi(d, r) = sum_l G_l(c) D^-l Phi_l(d), so
-//   dPsi/dd = sum_l G_l D^-l (grad Phi_l - l Phi_l d / D^2) + 2 dPsi/dD2 d,
-// one polynomial value and gradient per band instead of the SH basis and its
-// reverse sweep.
-__device__ __forceinline__ void pair_backward_phi(float px, float py, float pz, float4 sp,
-                                                  const float* q, float& gcx, float& gcy,
-                                                  float& gcz, float& gr) {
+// Adjoint of one pair through the per-band homogeneous polynomials
+// Phi_l(s) = sum_m dfp_lm Hbar_lm(s) (degree l).  The pair's loss term is
+// Psi = sum_l G_l(c) Phi_l(s_hat).  Euler's identity s . grad Phi_l = l Phi_l
+// makes every needed quantity a dot product with the per-band gradients:
+//   a = sum_l G_l grad Phi_l,    b = sum_l (P_l / l) grad Phi_l   (l >= 1)
+//   dPsi/dc = -sum_l P_l Phi_l = -(s_hat . b) - Phi_0
+//   dPsi/dd = (a - (s_hat . a) s_hat) / D + 2 (dPsi/dD^2) d
+// so only the gradient polynomials (degree l-1) are evaluated per pair.
+__device__ __forceinline__ void pair_backward_grad(float px, float py, float pz, float4 sp,
+                                                   const float* gq, float q0, float& gcx,
+                                                   float& gcy, float& gcz, float& gr) {
     const PairGeom g = pair_geometry(px, py, pz, sp);
     float P[NB], dP[NB], G[NB];
     legendre(g.c, P, dP);
     cap_integrals(g.c, g.s2, dP, G);
-    float v[NB], gx[NB], gy[NB], gz[NB];
-    SH::phi_eval(g.dx, g.dy, g.dz, q, v, gx, gy, gz);
-    float ip = 1.f, dc = 0.f, ax = 0.f, ay = 0.f, az = 0.f, rad = 0.f;
+    const float sx = g.dx * g.invD, sy = g.dy * g.invD, sz = g.dz * g.invD;
+    float gx[NB], gy[NB], gz[NB];
+    SH::grad_eval(sx, sy, sz, gq, gx, gy, gz);
+    float ax = 0.f, ay = 0.f, az = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
 #pragma unroll
-    for (int l = 0; l < NB; ++l) {
-        const float sl = G[l] * ip;              // G_l D^-l
-        dc = fmaf(-P[l], v[l] * ip, dc);         // d/dc int_c^1 P_l = -P_l(c)
-        ax = fmaf(sl, gx[l], ax);
-        ay = fmaf(sl, gy[l], ay);
-        az = fmaf(sl, gz[l], az);
-        if (l > 0) rad = fmaf(sl * float(l), v[l], rad);
-        ip *= g.invD;
+    for (int l = 1; l < NB; ++l) {
+        ax = fmaf(G[l], gx[l - 1], ax);
+        ay = fmaf(G[l], gy[l - 1], ay);
+        az = fmaf(G[l], gz[l - 1], az);
+        const float pl = P[l] * (1.f / float(l));
+        bx = fmaf(pl, gx[l - 1], bx);
+        by = fmaf(pl, gy[l - 1], by);
+        bz = fmaf(pl, gz[l - 1], bz);
     }
+    const float rad = fmaf(sx, ax, fmaf(sy, ay, sz * az));
+    const float dc = -fmaf(sx, bx, fmaf(sy, by, fmaf(sz, bz, q0)));
+    // c = sqrt(1 - s2): d c / d s2 = -1 / (2 c); clamped caps carry no gradient
     const float ds2 = g.open ? __fdividef(-0.5f * dc, g.c) : 0.f;
-    gr = ds2 * 2.f * sp.w * g.invD2;
-    const float coef = 2.f * (-ds2 * g.s2 * g.invD2) - rad * g.invD2;
-    gcx = fmaf(coef, g.dx, ax);
-    gcy = fmaf(coef, g.dy, ay);
-    gcz = fmaf(coef, g.dz, az);
+    gr = ds2 * 2.f * sp.w * g.invD2;                      // s2 = r^2 / D^2
+    const float coef = -2.f * ds2 * g.s2 * g.invD2;        // 2 dPsi/dD^2
+    gcx = fmaf(fmaf(-rad, sx, ax), g.invD, coef * g.dx);
+    gcy = fmaf(fmaf(-rad, sy, ay), g.invD, coef * g.dy);
+    gcz = fmaf(fmaf(-rad, sz, az), g.invD, coef * g.dz);
 }
-
-// The polynomial route needs sum_l (l+1)(l+2)/2 coefficients per point; above
-// 5 bands that no longer fits in registers next to the tail state.
-constexpr bool kUsePhi = NB <= 5;
 
 // Number of squarings: least k >= 0 with |f_hat| <= tau 2^k, capped at kmax.
 __device__ __forceinline__ int scaling_k(const SceneView& sc, float nrm2) {
@@ -264,8 +279,15 @@ __device__ __forceinline__ void cosine_lobe(float nx, float ny, float nz, float*
 
 // Scale the raw pair sums to the log-visibility f.
 __device__ __forceinline__ void finish_f(const SceneView& sc, const float* acc, float* f) {
+    float fr[K];
+    if constexpr (kMono) {
+        SH::mono_to_f(acc, fr);
+    } else {
 #pragma unroll
-    for (int i = 0; i < K; ++i) f[i] = sc.neg_2pi_eps * SH::norm(i) * acc[i];
+        for (int i = 0; i < K; ++i) fr[i] = acc[i];
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) f[i] = sc.neg_2pi_eps * SH::norm(i) * fr[i];
 }
 
 __device__ __forceinline__ float load_or(const float* p, int64_t i, bool live) {
@@ -287,9 +309,9 @@ __global__ void __launch_bounds__(kBlock) forward_kernel(FwdArgs a) {
     const float px = __ldg(a.points + 3 * p), py = __ldg(a.points + 3 * p + 1),
                 pz = __ldg(a.points + 3 * p + 2);
 
-    float acc[K];
+    float acc[NACC];
 #pragma unroll
-    for (int i = 0; i < K; ++i) acc[i] = 0.f;
+    for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
     const int N = a.sc.n_spheres;
 #pragma unroll 2
     for (int j = 0; j < N; ++j) pair_forward(px, py, pz, s_sph[j], acc);
@@ -346,6 +368,57 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Sum NV values (NV a power of two <= 32) over the warp by halving exchanges:
+// afterwards v[0] on lane l holds the warp total of value (l >> (5 - log2 NV)).
+template <int NV>
+__device__ __forceinline__ void warp_transpose_sum(float* v, int lane) {
+#pragma unroll
+    for (int o = 16, cnt = NV; o > 0; o >>= 1) {
+        if (cnt > 1) {
+            const int half = cnt / 2;
+            const bool up = lane & o;
+#pragma unroll
+            for (int i = 0; i < half; ++i) {
+                const float send = up ? v[i] : v[i + half];
+                const float keep = up ? v[i + half] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+            cnt = half;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        }
+    }
+}
+
+constexpr int log2c(int v) { return v <= 1 ? 0 : 1 + log2c(v / 2); }
+constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : 2 * pow2_at_least((v + 1) / 2); }
+
+// Add the warp totals of vals[0..NV) into dst[0..NV) (one lane per value).
+template <int NV>
+__device__ __forceinline__ void warp_sum_into(const float* vals, float* dst, int lane) {
+#pragma unroll
+    for (int base = 0; base < NV; base += 32) {
+        const int rem = NV - base;
+        if (rem >= 32) {
+            float v[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = vals[base + i];
+            warp_transpose_sum<32>(v, lane);
+            dst[base + lane] += v[0];
+        } else {
+            constexpr int R = NV % 32 == 0 ? 32 : NV % 32;
+            constexpr int RP = pow2_at_least(R);
+            float v[RP];
+#pragma unroll
+            for (int i = 0; i < RP; ++i) v[i] = i < R ? vals[base + i] : 0.f;
+            warp_transpose_sum<RP>(v, lane);
+            constexpr int sh = 5 - log2c(RP);
+            const int idx = lane >> sh;
+            if ((lane & ((1 << sh) - 1)) == 0 && idx < R) dst[base + idx] += v[0];
+        }
+    }
+}
+
 // Sum four values over the warp; lane l returns the total of value (l >> 3).
 __device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v3, int lane) {
     const bool h16 = lane & 16;
@@ -365,7 +438,9 @@ __device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v
 //   [0, 3K)          d_light, channel-major
 //   [3K]             loss
 //   [3K+1, 3K+1+4N)  per sphere (d cx, d cy, d cz, d r)
-__global__ void __launch_bounds__(kBlock) backward_kernel(BwdArgs a) {
+// Up to 4 bands: four resident blocks per SM (<= 128 registers per thread) for
+// the pair loop; above that the tail state needs the registers.
+__global__ void __launch_bounds__(kBlock, NB <= 4 ? 4 : 1) backward_kernel(BwdArgs a) {
     extern __shared__ __align__(16) float4 dyn[];
     __shared__ __align__(16) float s_light[3 * KPAD];
     __shared__ __align__(8) uint64_t s_bar;
@@ -398,9 +473,9 @@ __global__ void __launch_bounds__(kBlock) backward_kernel(BwdArgs a) {
         for (int i = 0; i < K; ++i) f[i] = load_or(a.saved_f, i * P + q, live);
         k = live ? min(max(a.saved_k[q], 0), kMaxK) : 0;   // a foreign buffer cannot overrun hist
     } else {
-        float acc[K];
+        float acc[NACC];
 #pragma unroll
-        for (int i = 0; i < K; ++i) acc[i] = 0.f;
+        for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
 #pragma unroll 2
         for (int j = 0; j < N; ++j) pair_forward(px, py, pz, s_sph[j], acc);
         finish_f(a.sc, acc, f);
@@ -469,13 +544,16 @@ __global__ void __launch_bounds__(kBlock) backward_kernel(BwdArgs a) {
             dW[i] = fmaf(u, L, dW[i]);
         }
         if (live && a.d_albedo) a.d_albedo[3 * q + c] = dB[c] * lw;
-        if (a.d_light) {
+    }
+    if (a.d_light) {
+        float dl[3 * K];
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-                const float v = warp_sum(u * W[i]);
-                if (lane == 0) s_dl[warp][c * K + i] += v;
-            }
+        for (int c = 0; c < 3; ++c) {
+            const float u = alb[c] * dB[c];
+#pragma unroll
+            for (int i = 0; i < K; ++i) dl[c * K + i] = u * W[i];
         }
+        warp_sum_into<3 * K>(dl, &s_dl[warp][0], lane);
     }
     if (a.target) {
         const float v = warp_sum(loss);
@@ -526,10 +604,11 @@ __global__ void __launch_bounds__(kBlock) backward_kernel(BwdArgs a) {
     // ---- pair adjoints
     const bool want_sph = a.d_centers || a.d_radii;
     if (want_sph || a.d_points) {
-        float phq[kUsePhi ? SH::NQ : 1];
-        if constexpr (kUsePhi) SH::phi_coeffs(dfp, phq);
+        float gq[kMono ? SH::NG : 1];
+        if constexpr (kMono) SH::grad_coeffs(dfp, gq);
+        const float q0 = dfp[0];
         auto pair = [&](float4 sp, float& gcx, float& gcy, float& gcz, float& gr) {
-            if constexpr (kUsePhi) pair_backward_phi(px, py, pz, sp, phq, gcx, gcy, gcz, gr);
+            if constexpr (kMono) pair_backward_grad(px, py, pz, sp, gq, q0, gcx, gcy, gcz, gr);
             else pair_backward(px, py, pz, sp, dfp, gcx, gcy, gcz, gr);
         };
         float gpx = 0.f, gpy = 0.f, gpz = 0.f;
