@@ -145,6 +145,38 @@ shs_status shs_shade_backward_l2(shs_scene_t scene, int64_t n_points, const floa
                                  float* d_radii, float* d_points, float* d_normals,
                                  void* stream);
 
+/* Backward pass that allocates no device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * when they need gradients -- processes whose device memory belongs to another
+ * allocator (a framework caching allocator or a fixed pre-reserved pool) and
+ * latency-critical loops that forbid allocation after start-up.  Creating a
+ * scene allocates, so it takes the spheres and lighting directly (arguments
+ * as in shs_scene_create with *cfg, then as in shs_shade_backward) and keeps
+ * its intermediates (packed spheres, padded lighting, the gradient
+ * accumulator, a block counter and a status word) in one static device array
+ * of about 35 KB compiled into the library, which every GPU that loads the
+ * library holds until the process exits.
+ *   Limits: n_bands <= 8 and n_spheres <= 1024; larger requests return
+ *   SHS_ERR_INVALID_ARG with a message naming the limit.
+ *   Set-up: the first call on each device looks up that array's device address
+ *   (cudaGetSymbolAddress) with the device current; make that first call
+ *   before any stream capture.
+ *   Sharing: every call on a device uses the same array.  Each call clears
+ *   the parts that must start at zero, but calls that overlap on the GPU
+ *   (different streams, or different host threads) race and corrupt each
+ *   other's results; order them on one stream.
+ *   The scene-level sums (d_light, d_centers, d_radii) are accumulated with
+ *   atomics, so their last bits can differ from run to run.
+ * It calls no cudaMalloc, cudaFree or allocating library routine. */
+shs_status shs_shade_backward_noalloc(const shs_config* cfg, int32_t n_spheres,
+                                      const float* centers, const float* radii,
+                                      const float* light, int64_t n_points,
+                                      const float* points, const float* normals,
+                                      const float* albedo, const void* saved,
+                                      const float* d_radiance, float* d_light,
+                                      float* d_albedo, float* d_centers, float* d_radii,
+                                      float* d_points, float* d_normals, void* stream);
+
 /* Synchronises `stream`, then reports and clears the scene's device-side
  * status word: 0 = no error, otherwise a shs_status a kernel raised (e.g.
  * SHS_ERR_TIMEOUT when a bounded wait for staged data gave up). */

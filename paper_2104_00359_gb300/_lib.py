@@ -54,6 +54,9 @@ _SIGS = {
     "shs_shade_backward_l2": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                         c_void_p, c_void_p]),
+    "shs_shade_backward_noalloc": (c_int32, [POINTER(ShsConfig), c_int32, c_void_p, c_void_p, c_void_p, c_int64,
+                                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "shs_scene_device_status": (c_int32, [c_void_p, c_void_p, POINTER(c_int32)]),
     "shs_launch_count": (c_int64, []),
     "shs_status_string": (c_char_p, [c_int32]),

@@ -166,6 +166,22 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
+namespace shs {
+int validate_config(const void* cfg) { return check_config(static_cast<const shs_config*>(cfg)); }
+int report_error(int status, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return status;
+}
+int report_cuda(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+cudaError_t launch_backward_nb(int n_bands, const BwdArgs& a, cudaStream_t s) {
+    return dispatch<Bwd>(n_bands, a, s);
+}
+int backward_blocks_per_sm_nb(int n_bands, int n_spheres) { return blocks_per_sm(n_bands, n_spheres); }
+}  // namespace shs
+
 extern "C" {
 
 shs_status shs_config_default(shs_config* cfg) {

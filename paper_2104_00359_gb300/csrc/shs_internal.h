@@ -71,4 +71,11 @@ cudaError_t launch_pack_spheres(const float* centers, const float* radii, float4
 
 void count_launch();
 
+// Shared by every entry point of the C ABI (defined in shs_api.cu).
+int validate_config(const void* cfg);                    // shs_status of a shs_config*
+int report_error(int status, const char* fmt, ...);      // sets shs_last_error(), returns status
+int report_cuda(cudaError_t e, const char* what);        // maps a CUDA error to a shs_status
+cudaError_t launch_backward_nb(int n_bands, const BwdArgs& a, cudaStream_t s);
+int backward_blocks_per_sm_nb(int n_bands, int n_spheres);
+
 }  // namespace shs
