@@ -356,6 +356,121 @@ def bench_reference(args, world, rank):
                 e2e={"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
 
 
+def bench_serving(args, world, rank, local):
+    """The serving mix: 64 resident jobs (16,384 to 1,048,576 points, log-
+    uniform; 20 to 500 spheres; 4 or 6 SH bands), 2,000 Poisson requests (70 %
+    forward, 30 % forward + L2 backward) at 80 % of the per-call capacity,
+    served by the continuous-batching server and, for comparison, by per-call
+    launches in arrival order.  Throughput in pairs/s; latency from arrival to
+    completion."""
+    import torch
+    from paper_2104_00359_gb300 import Config, Scene, serve, synthetic
+    torch.cuda.set_device(local)
+    rng = np.random.default_rng(4 + 1000 * rank)
+    n_jobs, n_req = args.serve_jobs, args.serve_requests
+    srv = serve.Server(hbm_budget_bytes=80e9, n_slots=3, max_batch=32)
+    for j in range(n_jobs):
+        P = int(np.exp(rng.uniform(np.log(16384), np.log(1048576))))
+        N = int(rng.integers(20, 501))
+        n = 4 if rng.random() < 0.5 else 6
+        sc = synthetic.serving_job(10_000 + j, P, N, n)
+        cfg = Config(n_bands=n, deterministic=False)
+        dev = torch.device("cuda", local)
+        light_t = torch.from_numpy(sc["light"]).to(dev)
+        tsc = Scene(torch.from_numpy(sc["centers"]).to(dev), torch.from_numpy(sc["radii"]).to(dev),
+                    light_t + 0.05 * torch.randn_like(light_t), cfg)
+        target = tsc.shade(*(torch.from_numpy(sc[k]).to(dev) for k in ("points", "normals", "albedo")))
+        torch.cuda.synchronize()
+        tsc.close()
+        srv.add_job(j, sc["points"], sc["normals"], sc["albedo"], sc["centers"], sc["radii"], sc["light"],
+                    cfg, target=target)
+    runner = serve.PerCallRunner(srv.jobs)
+    # per-call capacity: one fwd and one fwdbwd per job, timed on the device
+    t_fwd, t_fb = [], []
+    for j in range(n_jobs):
+        for op, acc in (("fwd", t_fwd), ("fwdbwd", t_fb)):
+            runner.run(serve.Request(-1, j, op, 0.0)).synchronize()
+            t0 = time.perf_counter()
+            runner.run(serve.Request(-1, j, op, 0.0)).synchronize()
+            acc.append(time.perf_counter() - t0)
+    mean_service = 0.7 * statistics.fmean(t_fwd) + 0.3 * statistics.fmean(t_fb)
+    rate = 0.8 / mean_service
+    gaps = rng.exponential(1.0 / rate, n_req)
+    arrivals = np.cumsum(gaps)
+    req_jobs = rng.integers(0, n_jobs, n_req)
+    req_ops = np.where(rng.random(n_req) < 0.3, "fwdbwd", "fwd")
+
+    def run_server():
+        t0 = time.perf_counter()
+        reqs, i = [], 0
+        while i < n_req or not srv.idle():
+            now = time.perf_counter() - t0
+            while i < n_req and arrivals[i] <= now:
+                reqs.append(srv.submit(int(req_jobs[i]), str(req_ops[i]), arrival=t0 + arrivals[i]))
+                i += 1
+            srv.poll()
+        return reqs, t0
+
+    def run_percall():
+        t0 = time.perf_counter()
+        done, inflight, i = [], deque(), 0
+        while i < n_req or inflight:
+            now = time.perf_counter() - t0
+            while i < n_req and arrivals[i] <= now:
+                r = serve.Request(i, int(req_jobs[i]), str(req_ops[i]), t0 + arrivals[i])
+                inflight.append((r, runner.run(r)))
+                i += 1
+            while inflight and inflight[0][1].query():
+                r, _ = inflight.popleft()
+                r.done = time.perf_counter()
+                job = srv.jobs[r.job_id]
+                r.pairs = job.P * job.N
+                done.append(r)
+        return done, t0
+
+    def summarise(reqs, t0):
+        lat = [r.latency * 1e3 for r in reqs]
+        span = max(r.done for r in reqs) - t0
+        pairs = sum(r.pairs for r in reqs)
+        return {"value": pairs / span, "p50_ms": serve.percentile(lat, 0.5), "p99_ms": serve.percentile(lat, 0.99),
+                "span_s": span, "requests": len(reqs)}
+
+    from collections import deque
+    pc_reqs, pc_t0 = run_percall()
+    torch.cuda.synchronize()
+    sv_reqs, sv_t0 = run_server()
+    torch.cuda.synchronize()
+    sv = summarise(sv_reqs, sv_t0)
+    pc = summarise(pc_reqs, pc_t0)
+    # saturated: every request available at t = 0 (capacity of each path)
+    saved_arrivals = arrivals.copy()
+    arrivals[:] = 0.0
+    pcs_reqs, pcs_t0 = run_percall()
+    torch.cuda.synchronize()
+    svs_reqs, svs_t0 = run_server()
+    torch.cuda.synchronize()
+    arrivals[:] = saved_arrivals
+    svs = summarise(svs_reqs, svs_t0)
+    pcs = summarise(pcs_reqs, pcs_t0)
+    srv.close()
+    return dict(metric="serving mix: shaded point-sphere pairs/sec (64 jobs, 2000 Poisson requests); p50/p99 latency",
+                value=sv["value"], unit="pairs/s", n_gpus=world, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32", data="synthetic", impl="ours",
+                config={"workload": "serving mix: 64 resident jobs, 16,384-1,048,576 points (log-uniform), "
+                                    "20-500 spheres, n_bands 4 or 6, 70% fwd / 30% fwd+L2 bwd, Poisson arrivals "
+                                    "at 80% of per-call capacity, 80 GB HBM budget",
+                        "jobs": n_jobs, "requests": n_req, "rate_per_s": rate,
+                        "mean_per_call_service_ms": mean_service * 1e3, "slots": 3, "max_batch": 32},
+                latency_ms={"p50": sv["p50_ms"], "p99": sv["p99_ms"]},
+                batches=srv.batches, max_batches_in_flight=srv.max_inflight,
+                per_call_baseline={"value": pc["value"], "unit": "pairs/s",
+                                   "latency_ms": {"p50": pc["p50_ms"], "p99": pc["p99_ms"]}},
+                span_s={"server": sv["span_s"], "per_call": pc["span_s"]},
+                saturated={"server": {"value": svs["value"], "span_s": svs["span_s"]},
+                           "per_call": {"value": pcs["value"], "span_s": pcs["span_s"]},
+                           "unit": "pairs/s"})
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,11 +479,17 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--atomic", action="store_true", help="unordered (atomic) scene-gradient reduction")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--workload", choices=("capsule", "serving"), default="capsule",
+                    help="capsule: the 512x512 G-buffer step (default); serving: the mixed request stream")
+    ap.add_argument("--serve-jobs", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local, dist = dist_init(args)
     if args.impl == "reference":
         res = bench_reference(args, world, rank)
+    elif args.workload == "serving":
+        res = bench_serving(args, world, rank, local)
     else:
         res = bench_ours(args, world, rank, local, dist)
     if rank == 0 and res is not None:

@@ -177,6 +177,45 @@ shs_status shs_shade_backward_noalloc(const shs_config* cfg, int32_t n_spheres,
                                       float* d_albedo, float* d_centers, float* d_radii,
                                       float* d_points, float* d_normals, void* stream);
 
+/* ---- Batched shading for serving many jobs (continuous batching) ----------
+ * A batch call runs the forward pass (Eq. 8) of up to 32 requests, each on its
+ * own resident scene, and the L2 adjoint (as shs_shade_backward_l2) of those
+ * that carry a target, in one persistent launch per band count and pass: the
+ * requests' 128-point tiles form one work list that the resident blocks
+ * drain through a device counter.  The paper runs one scene per call; this is
+ * the serving form of the same computation (Sec. 3.5's analysis-by-synthesis
+ * iterations of many jobs at once). */
+typedef struct shs_batch_s* shs_batch_t;
+
+typedef struct {
+    shs_scene_t scene;      /* the job's resident scene; at most once per call  */
+    int64_t n_points;       /* P >= 0                                             */
+    const float* points;    /* [P,3]                                              */
+    const float* normals;   /* [P,3]                                              */
+    const float* albedo;    /* [P,3]                                              */
+    float* radiance;        /* [P,3] output                                       */
+    void* saved;            /* shs_saved_bytes(scene, P) bytes or NULL            */
+    const float* target;    /* [P,3]; NULL = forward only, else L2 adjoint too    */
+    float* loss;            /* adjoint outputs as in shs_shade_backward_l2,        */
+    float* d_light;         /* each may be NULL                                   */
+    float* d_albedo;
+    float* d_centers;
+    float* d_radii;
+    float* d_points;
+    float* d_normals;
+} shs_request;
+
+/* A batch context holds the device work counters of one in-flight batch call;
+ * use one context per stream that runs batches concurrently. */
+shs_status shs_batch_create(shs_batch_t* out);
+shs_status shs_batch_destroy(shs_batch_t batch);
+
+/* Enqueues the batch on `stream`.  Requests with a target need `saved`.  Two
+ * requests may not share a scene (its accumulator is per call).  Scene-level
+ * sums are accumulated with atomics (run-to-run rounding differences).
+ * Returns SHS_ERR_INVALID_ARG for more than 32 requests. */
+shs_status shs_shade_batch(shs_batch_t batch, const shs_request* reqs, int32_t n_reqs, void* stream);
+
 /* Synchronises `stream`, then reports and clears the scene's device-side
  * status word: 0 = no error, otherwise a shs_status a kernel raised (e.g.
  * SHS_ERR_TIMEOUT when a bounded wait for staged data gave up). */

@@ -33,6 +33,13 @@ class ShsConfig(ctypes.Structure):
     ]
 
 
+class ShsRequest(ctypes.Structure):
+    """Mirror of ``shs_request`` (one job's request in a batch call)."""
+    _fields_ = [("scene", c_void_p), ("n_points", c_int64)] + [
+        (n, c_void_p) for n in ("points", "normals", "albedo", "radiance", "saved", "target", "loss",
+                                "d_light", "d_albedo", "d_centers", "d_radii", "d_points", "d_normals")]
+
+
 class ShsError(RuntimeError):
     def __init__(self, status, where, message):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
@@ -57,6 +64,9 @@ _SIGS = {
     "shs_shade_backward_noalloc": (c_int32, [POINTER(ShsConfig), c_int32, c_void_p, c_void_p, c_void_p, c_int64,
                                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "shs_batch_create": (c_int32, [POINTER(c_void_p)]),
+    "shs_batch_destroy": (c_int32, [c_void_p]),
+    "shs_shade_batch": (c_int32, [c_void_p, POINTER(ShsRequest), c_int32, c_void_p]),
     "shs_scene_device_status": (c_int32, [c_void_p, c_void_p, POINTER(c_int32)]),
     "shs_launch_count": (c_int64, []),
     "shs_status_string": (c_char_p, [c_int32]),

@@ -73,6 +73,12 @@ struct shs_scene_s {
     int* status;           // device status word
     float* partials;       // [max_grid][partial_stride] (deterministic) or accumulator
     unsigned int* counter;
+    float* batch_acc;      // [partial_stride] accumulator for batched calls (kept zero)
+    unsigned int* batch_counter;
+};
+
+struct shs_batch_s {
+    unsigned int* queues;  // [16] tile counters: forward / backward x n_bands
 };
 
 namespace {
@@ -96,6 +102,12 @@ cudaError_t dispatch(int nb, A&&... args) {
     }
 }
 
+template <int NB> struct FwdB {
+    static cudaError_t run(const shs::FwdBatch& b, cudaStream_t s) { return shs::launch_forward_batch<NB>(b, s); }
+};
+template <int NB> struct BwdB {
+    static cudaError_t run(const shs::BwdBatch& b, cudaStream_t s) { return shs::launch_backward_batch<NB>(b, s); }
+};
 template <int NB> struct Fwd {
     static cudaError_t run(const FwdArgs& a, cudaStream_t s) { return shs::launch_forward<NB>(a, s); }
 };
@@ -159,6 +171,8 @@ void free_scene(shs_scene_s* s) {
     cudaFree(s->status);
     cudaFree(s->partials);
     cudaFree(s->counter);
+    cudaFree(s->batch_acc);
+    cudaFree(s->batch_counter);
     delete s;
 }
 
@@ -231,6 +245,10 @@ shs_status shs_scene_create(const shs_config* cfg, int32_t n_spheres, const floa
     if (e == cudaSuccess) e = cudaMalloc(&sc->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&sc->partials, sizeof(float) * partial_floats);
     if (e == cudaSuccess) e = cudaMalloc(&sc->counter, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&sc->batch_acc, sizeof(float) * sc->partial_stride);
+    if (e == cudaSuccess) e = cudaMalloc(&sc->batch_counter, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc->batch_acc, 0, sizeof(float) * sc->partial_stride, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc->batch_counter, 0, sizeof(unsigned int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(sc->light, 0, sizeof(float) * 3 * sc->Kpad, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(sc->status, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(sc->partials, 0, sizeof(float) * partial_floats, s);
@@ -383,6 +401,124 @@ shs_status shs_shade_backward_l2(shs_scene_t sc, int64_t n_points, const float* 
     if (n_points > 0 && (!radiance || !target)) return fail(SHS_ERR_INVALID_ARG, "radiance/target is NULL");
     return backward_common(sc, n_points, points, normals, albedo, saved, nullptr, radiance, target, loss,
                            d_light, d_albedo, d_centers, d_radii, d_points, d_normals, stream);
+}
+
+shs_status shs_batch_create(shs_batch_t* out) {
+    if (!out) return fail(SHS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    shs_batch_s* b = new (std::nothrow) shs_batch_s();
+    if (!b) return fail(SHS_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaMalloc(&b->queues, 16 * sizeof(unsigned int));
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "allocate batch queues");
+    }
+    *out = b;
+    return SHS_OK;
+}
+
+shs_status shs_batch_destroy(shs_batch_t b) {
+    if (!b) return SHS_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    cudaFree(b->queues);
+    delete b;
+    return e == cudaSuccess ? SHS_OK : cuda_fail(e, "synchronise before destroy");
+}
+
+shs_status shs_shade_batch(shs_batch_t batch, const shs_request* reqs, int32_t n_reqs, void* stream) {
+    if (!batch) return fail(SHS_ERR_INVALID_ARG, "batch is NULL");
+    if (n_reqs < 0 || n_reqs > shs::kMaxBatch)
+        return fail(SHS_ERR_INVALID_ARG, "n_reqs %d not in 0..%d", n_reqs, shs::kMaxBatch);
+    if (n_reqs > 0 && !reqs) return fail(SHS_ERR_INVALID_ARG, "reqs is NULL");
+    for (int i = 0; i < n_reqs; ++i) {
+        const shs_request& r = reqs[i];
+        if (!r.scene) return fail(SHS_ERR_INVALID_ARG, "request %d: scene is NULL", i);
+        if (r.n_points < 0) return fail(SHS_ERR_INVALID_ARG, "request %d: n_points < 0", i);
+        if (r.n_points > 0 && (!r.points || !r.normals || !r.albedo || !r.radiance))
+            return fail(SHS_ERR_INVALID_ARG, "request %d: NULL input/output array", i);
+        if (r.target && !r.saved) return fail(SHS_ERR_INVALID_ARG, "request %d: backward needs saved", i);
+        if (r.saved && (reinterpret_cast<uintptr_t>(r.saved) & 15u))
+            return fail(SHS_ERR_INVALID_ARG, "request %d: saved not 16-byte aligned", i);
+        for (int j = 0; j < i; ++j)
+            if (reqs[j].scene == r.scene)
+                return fail(SHS_ERR_INVALID_ARG, "requests %d and %d share a scene", j, i);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(batch->queues, 0, 16 * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "reset batch queues");
+    for (int nb = 1; nb <= 8 && e == cudaSuccess; ++nb) {
+        shs::FwdBatch fb;
+        fb.n = 0;
+        fb.total_tiles = 0;
+        fb.queue = batch->queues + (nb - 1);
+        for (int i = 0; i < n_reqs; ++i) {
+            const shs_request& r = reqs[i];
+            if (r.scene->cfg.n_bands != nb || r.n_points == 0) continue;
+            shs::FwdArgs& a = fb.r[fb.n];
+            a.sc = view_of(r.scene);
+            a.n_points = r.n_points;
+            a.points = r.points;
+            a.normals = r.normals;
+            a.albedo = r.albedo;
+            a.radiance = r.radiance;
+            split_saved(r.scene, r.n_points, r.saved, &a.saved_f, &a.saved_k);
+            fb.tile_begin[fb.n] = fb.total_tiles;
+            fb.total_tiles += (r.n_points + shs::kBlock - 1) / shs::kBlock;
+            ++fb.n;
+        }
+        fb.tile_begin[fb.n] = fb.total_tiles;
+        if (fb.n) e = dispatch<FwdB>(nb, fb, s);
+    }
+    for (int nb = 1; nb <= 8 && e == cudaSuccess; ++nb) {
+        shs::BwdBatch bb;
+        bb.n = 0;
+        bb.max_spheres = 0;
+        bb.total_tiles = 0;
+        bb.queue = batch->queues + 8 + (nb - 1);
+        for (int i = 0; i < n_reqs && e == cudaSuccess; ++i) {
+            const shs_request& r = reqs[i];
+            shs_scene_s* sc = r.scene;
+            if (sc->cfg.n_bands != nb || !r.target) continue;
+            if (r.n_points == 0) {
+                if (r.d_light) e = cudaMemsetAsync(r.d_light, 0, sizeof(float) * 3 * sc->K, s);
+                if (e == cudaSuccess && r.d_centers && sc->n_spheres) e = cudaMemsetAsync(r.d_centers, 0, sizeof(float) * 3 * sc->n_spheres, s);
+                if (e == cudaSuccess && r.d_radii && sc->n_spheres) e = cudaMemsetAsync(r.d_radii, 0, sizeof(float) * sc->n_spheres, s);
+                if (e == cudaSuccess && r.loss) e = cudaMemsetAsync(r.loss, 0, sizeof(float), s);
+                continue;
+            }
+            shs::BwdArgs& a = bb.r[bb.n];
+            a = shs::BwdArgs{};
+            a.sc = view_of(sc);
+            a.n_points = r.n_points;
+            a.points = r.points;
+            a.normals = r.normals;
+            a.albedo = r.albedo;
+            float* sf;
+            int* sk;
+            split_saved(sc, r.n_points, r.saved, &sf, &sk);
+            a.saved_f = sf;
+            a.saved_k = sk;
+            a.radiance = r.radiance;
+            a.target = r.target;
+            a.loss = r.loss;
+            a.d_light = r.d_light;
+            a.d_albedo = r.d_albedo;
+            a.d_centers = sc->n_spheres ? r.d_centers : nullptr;
+            a.d_radii = sc->n_spheres ? r.d_radii : nullptr;
+            a.d_points = r.d_points;
+            a.d_normals = r.d_normals;
+            a.partials = sc->batch_acc;
+            a.counter = sc->batch_counter;
+            a.partial_stride = sc->partial_stride;
+            bb.tile_begin[bb.n] = bb.total_tiles;
+            bb.total_tiles += (r.n_points + shs::kBlock - 1) / shs::kBlock;
+            if (sc->n_spheres > bb.max_spheres) bb.max_spheres = sc->n_spheres;
+            ++bb.n;
+        }
+        bb.tile_begin[bb.n] = bb.total_tiles;
+        if (e == cudaSuccess && bb.n) e = dispatch<BwdB>(nb, bb, s);
+    }
+    return e == cudaSuccess ? SHS_OK : cuda_fail(e, "launch batch");
 }
 
 shs_status shs_scene_device_status(shs_scene_t sc, void* stream, int32_t* device_status) {

@@ -63,6 +63,29 @@ struct BwdArgs {
     int grid;                // persistent grid size
 };
 
+// A batch: up to kMaxBatch requests (of one band count) whose 128-point tiles
+// form one work list; a persistent grid pulls tiles from a device counter.
+constexpr int kMaxBatch = 32;
+
+struct FwdBatch {
+    int n;
+    int64_t total_tiles;
+    int64_t tile_begin[kMaxBatch + 1];   // prefix sums of tiles per request
+    unsigned int* queue;                  // zero before launch
+    FwdArgs r[kMaxBatch];
+};
+
+struct BwdBatch {
+    int n;
+    int max_spheres;
+    int64_t total_tiles;
+    int64_t tile_begin[kMaxBatch + 1];
+    unsigned int* queue;                  // zero before launch
+    BwdArgs r[kMaxBatch];                 // partials/counter: per-request accumulator
+};
+
+template <int NB> cudaError_t launch_forward_batch(const FwdBatch& b, cudaStream_t s);
+template <int NB> cudaError_t launch_backward_batch(const BwdBatch& b, cudaStream_t s);
 template <int NB> cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
 template <int NB> cudaError_t launch_backward(const BwdArgs& a, cudaStream_t s);
 template <int NB> int backward_blocks_per_sm(int n_spheres);

@@ -61,20 +61,27 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Stage the scene's sphere array and lighting into shared memory with bulk
-// asynchronous copies completing on one mbarrier.  Every thread waits with a
-// bound (about one second); the result is block-uniform: false means the copy
-// did not complete, the status word is set and the block must not use the
-// staged data.
-__device__ bool stage_scene(const SceneView& sc, float4* s_sph, float* s_light, uint64_t* bar) {
-    const uint32_t sph_bytes = static_cast<uint32_t>(sc.n_spheres) * 16u;
-    const uint32_t light_bytes = 3u * KPAD * 4u;
+// One mbarrier per block tracks the bulk copies that stage a scene (sphere
+// array + lighting) into shared memory.  Initialise it once per block.
+__device__ void mbar_init(uint64_t* bar) {
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+}
+
+// Stage a scene with bulk asynchronous copies completing on `bar` (phase
+// `parity`, alternating between stagings).  Every thread waits with a bound of
+// about one second; the result is block-uniform: false means the copy did not
+// complete, the status word is set and the block must not use the data.  The
+// caller must have synchronised the block if shared memory held a previous
+// scene that threads may still read.
+__device__ bool stage_copy(const SceneView& sc, float4* s_sph, float* s_light, uint64_t* bar,
+                           uint32_t parity) {
+    const uint32_t sph_bytes = static_cast<uint32_t>(sc.n_spheres) * 16u;
+    const uint32_t light_bytes = 3u * KPAD * 4u;
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                      ::"r"(smem_addr(bar)), "r"(sph_bytes + light_bytes) : "memory");
@@ -95,13 +102,18 @@ __device__ bool stage_scene(const SceneView& sc, float4* s_sph, float* s_light, 
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
             " selp.b32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok) : "r"(smem_addr(bar)), "r"(0u) : "memory");
+            : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
         done = ok != 0;
         if (!done && global_ns() - t0 > 1000000000ull) break;
     }
     const bool any_failed = __syncthreads_or(!done);
     if (any_failed && threadIdx.x == 0) atomicExch(sc.status, kDevTimeout);
     return !any_failed;
+}
+
+__device__ bool stage_scene(const SceneView& sc, float4* s_sph, float* s_light, uint64_t* bar) {
+    mbar_init(bar);
+    return stage_copy(sc, s_sph, s_light, bar, 0u);
 }
 
 // Legendre P_l(c) and P_l'(c) for l < NB (Bonnet recurrence and
@@ -298,14 +310,9 @@ __device__ __forceinline__ float load_or(const float* p, int64_t i, bool live) {
 // forward kernel
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kBlock) forward_kernel(FwdArgs a) {
-    __shared__ __align__(16) float4 s_sph[kMaxSpheres];
-    __shared__ __align__(16) float s_light[3 * KPAD];
-    __shared__ __align__(8) uint64_t s_bar;
-    if (!stage_scene(a.sc, s_sph, s_light, &s_bar)) return;
-
-    const int64_t p = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x;
-    if (p >= a.n_points) return;
+// Forward shading of point p of one request (Eq. 8), scene staged in shared memory.
+__device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_sph, const float* s_light,
+                                              int64_t p) {
     const float px = __ldg(a.points + 3 * p), py = __ldg(a.points + 3 * p + 1),
                 pz = __ldg(a.points + 3 * p + 2);
 
@@ -356,6 +363,16 @@ __global__ void __launch_bounds__(kBlock) forward_kernel(FwdArgs a) {
         for (int i = 0; i < K; ++i) a.saved_f[i * a.n_points + p] = f[i];
         a.saved_k[p] = k;
     }
+}
+
+__global__ void __launch_bounds__(kBlock) forward_kernel(FwdArgs a) {
+    __shared__ __align__(16) float4 s_sph[kMaxSpheres];
+    __shared__ __align__(16) float s_light[3 * KPAD];
+    __shared__ __align__(8) uint64_t s_bar;
+    if (!stage_scene(a.sc, s_sph, s_light, &s_bar)) return;
+    const int64_t p = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x;
+    if (p >= a.n_points) return;
+    forward_point(a, s_sph, s_light, p);
 }
 
 // ---------------------------------------------------------------------------
@@ -434,31 +451,14 @@ __device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v
     return k;
 }
 
-// Layout of one block's reduced scene gradient (E floats):
-//   [0, 3K)          d_light, channel-major
-//   [3K]             loss
-//   [3K+1, 3K+1+4N)  per sphere (d cx, d cy, d cz, d r)
-// Up to 4 bands: four resident blocks per SM (<= 128 registers per thread) for
-// the pair loop; above that the tail state needs the registers.
-__global__ void __launch_bounds__(kBlock, NB <= 4 ? 4 : 1) backward_kernel(BwdArgs a) {
-    extern __shared__ __align__(16) float4 dyn[];
-    __shared__ __align__(16) float s_light[3 * KPAD];
-    __shared__ __align__(8) uint64_t s_bar;
-    __shared__ float s_dl[NWARP][3 * K + 1];
-    __shared__ bool s_last;
+// Adjoint of one 128-point tile of one request: per-point outputs are written,
+// the scene-level sums are added to the block's shared accumulators
+// (s_dl: d_light and loss per warp, s_acc: per warp and sphere).
+__device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_sph, const float* s_light,
+                                              float* s_acc, float (*s_dl)[3 * K + 1], int64_t tile,
+                                              int lane, int warp) {
     const int N = a.sc.n_spheres;
-    float4* s_sph = dyn;                  // [N]
-    float* s_acc = reinterpret_cast<float*>(dyn + N);   // [NWARP][4N]
-    if (!stage_scene(a.sc, s_sph, s_light, &s_bar)) return;
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int e = threadIdx.x; e < NWARP * 4 * N; e += kBlock) s_acc[e] = 0.f;
-    for (int e = threadIdx.x; e < NWARP * (3 * K + 1); e += kBlock) (&s_dl[0][0])[e] = 0.f;
-    __syncthreads();
-
     const int64_t P = a.n_points;
-    const int64_t ntiles = (P + kBlock - 1) / kBlock;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t p = tile * kBlock + threadIdx.x;
     const bool live = p < P;
     const int64_t q = live ? p : 0;
@@ -655,7 +655,56 @@ __global__ void __launch_bounds__(kBlock, NB <= 4 ? 4 : 1) backward_kernel(BwdAr
             a.d_points[3 * q + 2] = gpz;
         }
     }
-    }  // tile loop
+}
+
+// The last contributor copies the accumulated scene-level sums to the
+// outputs and re-zeroes the accumulator and its counter for the next launch.
+__device__ void finish_scene_sums(const BwdArgs& a, int E) {
+    __threadfence();
+    for (int e = threadIdx.x; e < E; e += kBlock) {
+        const float v = __ldcg(a.partials + e);
+        a.partials[e] = 0.f;
+        if (e < 3 * K) {
+            if (a.d_light) a.d_light[e] = v;
+        } else if (e == 3 * K) {
+            if (a.loss) *a.loss = v;
+        } else {
+            const int s = e - (3 * K + 1), j = s >> 2, comp = s & 3;
+            if (comp < 3) {
+                if (a.d_centers) a.d_centers[3 * j + comp] = v;
+            } else if (a.d_radii) {
+                a.d_radii[j] = v;
+            }
+        }
+    }
+    if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+// Layout of one block's reduced scene gradient (E floats):
+//   [0, 3K)          d_light, channel-major
+//   [3K]             loss
+//   [3K+1, 3K+1+4N)  per sphere (d cx, d cy, d cz, d r)
+// Up to 4 bands: four resident blocks per SM (<= 128 registers per thread) for
+// the pair loop; above that the tail state needs the registers.
+__global__ void __launch_bounds__(kBlock, NB <= 4 ? 4 : 1) backward_kernel(BwdArgs a) {
+    extern __shared__ __align__(16) float4 dyn[];
+    __shared__ __align__(16) float s_light[3 * KPAD];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ float s_dl[NWARP][3 * K + 1];
+    __shared__ bool s_last;
+    const int N = a.sc.n_spheres;
+    float4* s_sph = dyn;                  // [N]
+    float* s_acc = reinterpret_cast<float*>(dyn + N);   // [NWARP][4N]
+    if (!stage_scene(a.sc, s_sph, s_light, &s_bar)) return;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < NWARP * 4 * N; e += kBlock) s_acc[e] = 0.f;
+    for (int e = threadIdx.x; e < NWARP * (3 * K + 1); e += kBlock) (&s_dl[0][0])[e] = 0.f;
+    __syncthreads();
+
+    const int64_t ntiles = (a.n_points + kBlock - 1) / kBlock;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        backward_tile(a, s_sph, s_light, s_acc, s_dl, tile, lane, warp);
 
     // ---- block reduction, then one scene-level reduction
     __syncthreads();
@@ -681,24 +730,103 @@ __global__ void __launch_bounds__(kBlock, NB <= 4 ? 4 : 1) backward_kernel(BwdAr
     if (threadIdx.x == 0) s_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
-    for (int e = threadIdx.x; e < E; e += kBlock) {
-        const float v = __ldcg(a.partials + e);
-        a.partials[e] = 0.f;
-        if (e < 3 * K) {
-            if (a.d_light) a.d_light[e] = v;
-        } else if (e == 3 * K) {
-            if (a.loss) *a.loss = v;
-        } else {
-            const int s = e - (3 * K + 1), j = s >> 2, comp = s & 3;
-            if (comp < 3) {
-                if (a.d_centers) a.d_centers[3 * j + comp] = v;
-            } else if (a.d_radii) {
-                a.d_radii[j] = v;
-            }
+    finish_scene_sums(a, E);
+}
+
+// ---------------------------------------------------------------------------
+// batched persistent kernels (serving): many requests, one launch
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int find_request(const int64_t* tb, int n, int64_t tile) {
+    int r = 0;
+    while (r + 1 < n && tile >= tb[r + 1]) ++r;
+    return r;
+}
+
+// Forward for every tile of every request in the batch.  Blocks take tiles
+// from a device counter (consecutive tiles mostly share a request, so a
+// request's scene is staged once per run of its tiles).
+__global__ void __launch_bounds__(kBlock) forward_batch_kernel(const __grid_constant__ FwdBatch b) {
+    __shared__ __align__(16) float4 s_sph[kMaxSpheres];
+    __shared__ __align__(16) float s_light[3 * KPAD];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ long long s_tile;
+    mbar_init(&s_bar);
+    int staged = -1;
+    uint32_t parity = 0;
+    for (;;) {
+        __syncthreads();                 // previous tile done before restaging
+        if (threadIdx.x == 0) s_tile = static_cast<long long>(atomicAdd(b.queue, 1u));
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= b.total_tiles) break;
+        const int r = find_request(b.tile_begin, b.n, tile);
+        if (r != staged) {
+            if (!stage_copy(b.r[r].sc, s_sph, s_light, &s_bar, parity)) return;
+            parity ^= 1u;
+            staged = r;
         }
+        const int64_t p = (tile - b.tile_begin[r]) * kBlock + threadIdx.x;
+        if (p < b.r[r].n_points) forward_point(b.r[r], s_sph, s_light, p);
     }
-    if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+// L2 adjoint for every tile of every request in the batch.  Each tile's scene
+// sums go to its request's accumulator with atomics; the tile that completes a
+// request writes that request's outputs.
+__global__ void __launch_bounds__(kBlock, NB <= 4 ? 4 : 1)
+    backward_batch_kernel(const __grid_constant__ BwdBatch b) {
+    extern __shared__ __align__(16) float4 dyn[];
+    __shared__ __align__(16) float s_light[3 * KPAD];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ float s_dl[NWARP][3 * K + 1];
+    __shared__ bool s_last;
+    __shared__ long long s_tile;
+    float4* s_sph = dyn;                                        // [max N]
+    float* s_acc = reinterpret_cast<float*>(dyn + b.max_spheres);   // [NWARP][4 max N]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    mbar_init(&s_bar);
+    int staged = -1;
+    uint32_t parity = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = static_cast<long long>(atomicAdd(b.queue, 1u));
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= b.total_tiles) break;
+        const int r = find_request(b.tile_begin, b.n, tile);
+        const BwdArgs& a = b.r[r];
+        const int N = a.sc.n_spheres;
+        if (r != staged) {
+            if (!stage_copy(a.sc, s_sph, s_light, &s_bar, parity)) return;
+            parity ^= 1u;
+            staged = r;
+        }
+        for (int e = threadIdx.x; e < NWARP * 4 * N; e += kBlock) s_acc[e] = 0.f;
+        for (int e = threadIdx.x; e < NWARP * (3 * K + 1); e += kBlock) (&s_dl[0][0])[e] = 0.f;
+        __syncthreads();
+        backward_tile(a, s_sph, s_light, s_acc, s_dl, tile - b.tile_begin[r], lane, warp);
+        __syncthreads();
+        const int E = 3 * K + 1 + 4 * N;
+        for (int e = threadIdx.x; e < E; e += kBlock) {
+            float v = 0.f;
+            if (e <= 3 * K) {
+#pragma unroll
+                for (int w = 0; w < NWARP; ++w) v += s_dl[w][e];
+            } else {
+                const int q = e - (3 * K + 1);
+#pragma unroll
+                for (int w = 0; w < NWARP; ++w) v += s_acc[w * 4 * N + q];
+            }
+            atomicAdd(a.partials + e, v);
+        }
+        __threadfence();
+        __syncthreads();
+        const int64_t ntiles_r = b.tile_begin[r + 1] - b.tile_begin[r];
+        if (threadIdx.x == 0) s_last = atomicAdd(a.counter, 1u) == static_cast<unsigned>(ntiles_r - 1);
+        __syncthreads();
+        if (s_last) finish_scene_sums(a, E);
+    }
 }
 
 // Deterministic finish: out[e] = sum over blocks b (in order) of partials[b][e].
@@ -748,6 +876,41 @@ int backward_blocks_per_sm<NB>(int n_spheres) {
                                                       backward_dyn_smem(n_spheres)) != cudaSuccess || nb < 1)
         nb = 1;
     return nb;
+}
+
+template <>
+cudaError_t launch_forward_batch<NB>(const FwdBatch& b, cudaStream_t s) {
+    if (b.total_tiles <= 0) return cudaSuccess;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, forward_batch_kernel, kBlock, 0);
+    if (e != cudaSuccess) return e;
+    const int64_t cap = static_cast<int64_t>(sms) * (per_sm > 0 ? per_sm : 1);
+    const int grid = static_cast<int>(b.total_tiles < cap ? b.total_tiles : cap);
+    forward_batch_kernel<<<grid, kBlock, 0, s>>>(b);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_backward_batch<NB>(const BwdBatch& b, cudaStream_t s) {
+    if (b.total_tiles <= 0) return cudaSuccess;
+    const size_t smem = backward_dyn_smem(b.max_spheres);
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        backward_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        static_cast<int>(backward_dyn_smem(kMaxSpheres)));
+    if (attr != cudaSuccess) return attr;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backward_batch_kernel, kBlock, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t cap = static_cast<int64_t>(sms) * (per_sm > 0 ? per_sm : 1);
+    const int grid = static_cast<int>(b.total_tiles < cap ? b.total_tiles : cap);
+    backward_batch_kernel<<<grid, kBlock, smem, s>>>(b);
+    count_launch();
+    return cudaGetLastError();
 }
 
 template <>

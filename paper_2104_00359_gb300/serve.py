@@ -1,0 +1,299 @@
+"""Continuous-batching server for many concurrent analysis-by-synthesis jobs.
+
+Each job keeps its state resident on the device: its scene (spheres + SH
+lighting, Sec. 3.3), its G-buffer (points, normals, albedo), the target image
+of its L2 loss (Sec. 3.5, Eq. 15) and its output buffers.  Jobs are admitted
+only while their device bytes fit the HBM budget; the rest wait and are
+admitted as memory frees up.  Requests ("fwd": shade; "fwdbwd": shade + L2 loss
++ adjoint) queue per arrival; whenever one of the batch slots is free, the
+server packs up to ``max_batch`` ready requests of distinct jobs into one
+``shs_shade_batch`` call (one persistent launch per band count and pass) on
+that slot's stream.  Batches in different slots overlap on the device, and
+requests that arrive while batches run join the next free slot -- continuous
+batching, not a queue in front of one call at a time.
+
+The per-call baseline (``PerCallRunner``) serves the same stream of requests
+one at a time with ``shs_shade`` / ``shs_shade_backward_l2`` on one stream.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _lib
+from ._lib import ShsRequest, check, ptr
+from .shade import Config, Scene
+
+
+def _load():
+    return _lib.load()
+
+
+MAX_BATCH = 32
+
+
+class Job:
+    """A job's resident device state."""
+
+    def __init__(self, job_id, points, normals, albedo, centers, radii, light, config: Config, target=None,
+                 device="cuda"):
+        self.job_id = job_id
+        self.config = config
+        dev = torch.device(device)
+        f32 = lambda t: torch.as_tensor(t, dtype=torch.float32).to(dev).contiguous()
+        self.points, self.normals, self.albedo = f32(points), f32(normals), f32(albedo)
+        self.centers, self.radii, self.light = f32(centers), f32(radii), f32(light)
+        self.target = f32(target) if target is not None else None
+        self.P = int(self.points.shape[0])
+        self.N = int(self.centers.shape[0])
+        self.scene = Scene(self.centers if self.N else None, self.radii if self.N else None, self.light, config)
+        self.saved = self.scene.new_saved(self.P, dev)
+        self.radiance = torch.empty((self.P, 3), dtype=torch.float32, device=dev)
+        self.grads = self.scene._grad_buffers(self.P, dev, ("light", "albedo", "centers", "radii"))
+        self.loss = torch.zeros((), dtype=torch.float32, device=dev)
+        self.busy = False
+
+    @staticmethod
+    def device_bytes(P, N, n_bands, with_target=True):
+        """Bytes a job holds on the device (inputs, outputs, saved state, scene)."""
+        K = n_bands * n_bands
+        per_point = 4 * (9 + 3 + (3 if with_target else 0) + 3 + K + 1)
+        scene = 16 * N + 4 * (3 * K + 4) + 4 * 2 * (3 * K + 1 + 4 * N) + 4 * (3 * K + 4 * N)
+        return P * per_point + scene + 4096
+
+    def bytes(self):
+        return self.device_bytes(self.P, self.N, self.config.n_bands, self.target is not None)
+
+    def request_struct(self, op):
+        r = ShsRequest()
+        r.scene = self.scene.handle.value
+        r.n_points = self.P
+        r.points, r.normals, r.albedo = (t.data_ptr() for t in (self.points, self.normals, self.albedo))
+        r.radiance = self.radiance.data_ptr()
+        r.saved = self.saved.data_ptr()
+        if op == "fwdbwd":
+            r.target = self.target.data_ptr()
+            r.loss = self.loss.data_ptr()
+            for k in ("d_light", "d_albedo", "d_centers", "d_radii"):
+                v = self.grads[k]
+                setattr(r, k, v.data_ptr() if v is not None else None)
+        return r
+
+    def close(self):
+        self.scene.close()
+
+
+@dataclass
+class Request:
+    req_id: int
+    job_id: object
+    op: str                      # "fwd" or "fwdbwd"
+    arrival: float               # host time (perf_counter) the request became available
+    launched: float = 0.0
+    done: float = 0.0
+    batch: int = -1
+    pairs: int = 0
+    on_done: object = None
+
+    @property
+    def latency(self):
+        return self.done - self.arrival
+
+
+@dataclass
+class _Slot:
+    stream: torch.cuda.Stream
+    ctx: ctypes.c_void_p
+    event: torch.cuda.Event = None
+    requests: list = field(default_factory=list)
+
+
+class Server:
+    """Continuous-batching request loop (see module docstring)."""
+
+    def __init__(self, hbm_budget_bytes=80e9, n_slots=3, max_batch=MAX_BATCH, device="cuda"):
+        if not 1 <= max_batch <= MAX_BATCH:
+            raise ValueError(f"max_batch must be in 1..{MAX_BATCH}")
+        self.lib = _load()
+        self.device = device
+        self.budget = float(hbm_budget_bytes)
+        self.max_batch = max_batch
+        self.jobs = {}
+        self.waiting_jobs = deque()       # (job_id, kwargs) not yet admitted
+        self.used = 0
+        self.pending = deque()            # requests not yet launched
+        self.completed = []
+        self.batches = 0
+        self.max_inflight = 0
+        self._req_ids = 0
+        self.slots = []
+        for _ in range(n_slots):
+            h = ctypes.c_void_p()
+            check(self.lib.shs_batch_create(ctypes.byref(h)), "shs_batch_create")
+            self.slots.append(_Slot(torch.cuda.Stream(device=device), h))
+
+    # -- jobs ------------------------------------------------------------
+    def add_job(self, job_id, points, normals, albedo, centers, radii, light, config: Config, target=None):
+        """Admit the job if its device bytes fit the budget, else queue it.
+        Returns True when admitted now."""
+        kw = dict(points=points, normals=normals, albedo=albedo, centers=centers, radii=radii, light=light,
+                  config=config, target=target)
+        need = Job.device_bytes(len(points), len(centers), config.n_bands, target is not None)
+        if need > self.budget:
+            raise ValueError(f"job {job_id} needs {need} bytes, more than the whole budget")
+        if self.used + need <= self.budget and not self.waiting_jobs:
+            self._admit(job_id, kw)
+            return True
+        self.waiting_jobs.append((job_id, kw))
+        return False
+
+    def _admit(self, job_id, kw):
+        job = Job(job_id, device=self.device, **kw)
+        # the job's uploads and scene set-up ran on the current stream; the
+        # batch slots use their own streams
+        torch.cuda.current_stream().synchronize()
+        self.jobs[job_id] = job
+        self.used += job.bytes()
+
+    def remove_job(self, job_id):
+        job = self.jobs.pop(job_id)
+        if job.busy:
+            raise RuntimeError("job has a request in flight")
+        self.used -= job.bytes()
+        job.close()
+        self._admit_waiting()
+
+    def _admit_waiting(self):
+        while self.waiting_jobs:
+            job_id, kw = self.waiting_jobs[0]
+            need = Job.device_bytes(len(kw["points"]), len(kw["centers"]), kw["config"].n_bands,
+                                    kw["target"] is not None)
+            if self.used + need > self.budget:
+                break
+            self.waiting_jobs.popleft()
+            self._admit(job_id, kw)
+
+    def admitted(self, job_id):
+        return job_id in self.jobs
+
+    # -- requests ----------------------------------------------------------
+    def submit(self, job_id, op="fwd", arrival=None, on_done=None):
+        if op not in ("fwd", "fwdbwd"):
+            raise ValueError("op must be 'fwd' or 'fwdbwd'")
+        r = Request(self._req_ids, job_id, op, time.perf_counter() if arrival is None else arrival,
+                    on_done=on_done)
+        self._req_ids += 1
+        self.pending.append(r)
+        return r
+
+    def _retire(self, slot):
+        now = time.perf_counter()
+        for r in slot.requests:
+            r.done = now
+            job = self.jobs[r.job_id]
+            job.busy = False
+            if r.on_done is not None:
+                r.on_done(r, job)
+            self.completed.append(r)
+        slot.requests = []
+        slot.event = None
+
+    def poll(self):
+        """Retire finished batches, then launch ready requests into free
+        slots.  Returns the number of requests launched."""
+        for slot in self.slots:
+            if slot.event is not None and slot.event.query():
+                self._retire(slot)
+        launched = 0
+        for slot in self.slots:
+            if slot.event is not None:
+                continue
+            batch, keep = [], deque()
+            while self.pending and len(batch) < self.max_batch:
+                r = self.pending.popleft()
+                job = self.jobs.get(r.job_id)
+                if job is None or job.busy or any(b.job_id == r.job_id for b in batch):
+                    keep.append(r)
+                    continue
+                if r.op == "fwdbwd" and job.target is None:
+                    raise ValueError(f"job {r.job_id} has no target for a fwdbwd request")
+                batch.append(r)
+            keep.extend(self.pending)
+            self.pending = keep
+            if not batch:
+                break
+            arr = (ShsRequest * len(batch))()
+            now = time.perf_counter()
+            for i, r in enumerate(batch):
+                job = self.jobs[r.job_id]
+                job.busy = True
+                arr[i] = job.request_struct(r.op)
+                r.launched = now
+                r.batch = self.batches
+                r.pairs = job.P * job.N
+            check(self.lib.shs_shade_batch(slot.ctx, arr, len(batch), ctypes.c_void_p(slot.stream.cuda_stream)),
+                  "shs_shade_batch")
+            slot.event = torch.cuda.Event()
+            slot.event.record(slot.stream)
+            slot.requests = batch
+            self.batches += 1
+            launched += len(batch)
+        inflight = sum(1 for s in self.slots if s.event is not None)
+        self.max_inflight = max(self.max_inflight, inflight)
+        return launched
+
+    def idle(self):
+        return not self.pending and all(s.event is None for s in self.slots)
+
+    def drain(self, timeout_s=600.0):
+        t0 = time.perf_counter()
+        while not self.idle():
+            self.poll()
+            if time.perf_counter() - t0 > timeout_s:
+                raise TimeoutError("server did not drain")
+
+    def close(self):
+        torch.cuda.synchronize()
+        for slot in self.slots:
+            self.lib.shs_batch_destroy(slot.ctx)
+        for job in self.jobs.values():
+            job.close()
+        self.jobs.clear()
+
+
+class PerCallRunner:
+    """Baseline: each request as its own shs_shade (+ shs_shade_backward_l2)
+    call, one at a time in arrival order, on one stream."""
+
+    def __init__(self, server_jobs):
+        self.jobs = server_jobs
+        self.stream = torch.cuda.Stream()
+
+    def run(self, req: Request):
+        job = self.jobs[req.job_id]
+        with torch.cuda.stream(self.stream):
+            job.scene.shade(job.points, job.normals, job.albedo, saved=job.saved, out=job.radiance)
+            if req.op == "fwdbwd":
+                lib = job.scene.lib
+                g = job.grads
+                check(lib.shs_shade_backward_l2(job.scene.handle, job.P, ptr(job.points), ptr(job.normals),
+                                                ptr(job.albedo), ptr(job.saved), ptr(job.radiance),
+                                                ptr(job.target), ptr(job.loss), ptr(g["d_light"]),
+                                                ptr(g["d_albedo"]), ptr(g["d_centers"]), ptr(g["d_radii"]),
+                                                None, None, ctypes.c_void_p(self.stream.cuda_stream)),
+                      "shs_shade_backward_l2")
+        ev = torch.cuda.Event()
+        ev.record(self.stream)
+        return ev
+
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return float("nan")
+    return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))]

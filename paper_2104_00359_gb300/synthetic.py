@@ -33,6 +33,8 @@ __all__ = [
     "random_scene",
     "perturb_scene",
     "sh_lighting",
+    "serving_job",
+    "mesh_deformation_scene",
 ]
 
 
@@ -230,3 +232,104 @@ def perturb_scene(scene, seed, center_sigma=0.01, light_sigma=0.05,
     out["albedo"] = _f32(scene["albedo"].astype(np.float64)
                          * rng.uniform(*albedo_range, scene["albedo"].shape))
     return out
+
+
+def serving_job(seed, n_points, n_spheres, n_bands, n_bumps=4):
+    """A job of the serving mix: the first ``n_points`` samples of a square
+    height-field grid (``n_bumps`` Gaussian bumps over [-1,1]^2) with analytic
+    unit normals, albedo uniform in [0.2, 0.9], spheres hovering over the field
+    (height + U[0.05, 0.8], radii log-uniform in [0.01, 0.2]) and lighting
+    N(0,0.3)/(l+1) with l=0 term 1.0."""
+    rng = np.random.default_rng(seed)
+    res = int(np.ceil(np.sqrt(n_points)))
+    amp = rng.uniform(-0.25, 0.25, n_bumps)
+    mu = rng.uniform(-1.0, 1.0, (n_bumps, 2))
+    sig = rng.uniform(0.15, 0.4, n_bumps)
+    t = -1.0 + (2.0 * np.arange(res) + 1.0) / res
+    X, Y = np.meshgrid(t, t, indexing="xy")
+    X = X.ravel()[:n_points]
+    Y = Y.ravel()[:n_points]
+
+    def h_and_grad(x, y):
+        h = np.zeros_like(x)
+        hx = np.zeros_like(x)
+        hy = np.zeros_like(x)
+        for a, (mx, my), s in zip(amp, mu, sig):
+            g = a * np.exp(-((x - mx) ** 2 + (y - my) ** 2) / (2 * s * s))
+            h += g
+            hx -= g * (x - mx) / (s * s)
+            hy -= g * (y - my) / (s * s)
+        return h, hx, hy
+
+    H, HX, HY = h_and_grad(X, Y)
+    nrm = np.stack([-HX, -HY, np.ones_like(H)], axis=1)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    albedo = rng.uniform(0.2, 0.9, size=(n_points, 3))
+    cxy = rng.uniform(-1.0, 1.0, (n_spheres, 2))
+    ch, _, _ = h_and_grad(cxy[:, 0], cxy[:, 1])
+    centers = np.concatenate([cxy, (ch + rng.uniform(0.05, 0.8, n_spheres))[:, None]], axis=1)
+    radii = np.exp(rng.uniform(np.log(0.01), np.log(0.2), n_spheres))
+    light = sh_lighting(rng, n_bands, band_decay=True)
+    return dict(points=_f32(np.stack([X, Y, H], axis=1)), normals=_f32(nrm), albedo=_f32(albedo),
+                centers=_f32(centers), radii=_f32(radii), light=_f32(light), n_bands=n_bands)
+
+
+def mesh_deformation_scene(seed=2, n_theta=250, n_phi=200, n_spheres=200, n_params=60, n_views=16,
+                           n_bands=4):
+    """Mesh-deformation batch: a UV-sphere mesh of n_theta x n_phi vertices
+    (radius 1 with a random smooth radial deformation), per-vertex normals and
+    albedo; n_spheres occluder spheres inside the mesh (centres at radius
+    0.5-0.8, radii U[0.05, 0.15]); vertices, normals and centres affine in
+    n_params deformation parameters (basis entries N(0, 0.01)); n_views rigid
+    poses (axis-angle |w| <= pi, translation N(0, 0.1)).  Returns float32
+    arrays: v0, n0, A_v [M,3,D], A_n [M,3,D], c0, A_c [N,3,D], radii, albedo,
+    light, poses [V,6]."""
+    rng = np.random.default_rng(seed)
+    th = (np.arange(n_theta) + 0.5) / n_theta * np.pi
+    ph = np.arange(n_phi) / n_phi * 2 * np.pi
+    TH, PH = np.meshgrid(th, ph, indexing="ij")
+    TH = TH.ravel()
+    PH = PH.ravel()
+    coef = rng.normal(0.0, 0.03, (4, 4))
+
+    def radius(t, p):
+        r = np.ones_like(t)
+        dr_t = np.zeros_like(t)
+        dr_p = np.zeros_like(t)
+        for a in range(4):
+            for b in range(4):
+                c = coef[a, b]
+                r += c * np.cos((a + 1) * t) * np.cos(b * p)
+                dr_t += -c * (a + 1) * np.sin((a + 1) * t) * np.cos(b * p)
+                dr_p += -c * b * np.cos((a + 1) * t) * np.sin(b * p)
+        return r, dr_t, dr_p
+
+    r, r_t, r_p = radius(TH, PH)
+    u = np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)], axis=1)
+    u_t = np.stack([np.cos(TH) * np.cos(PH), np.cos(TH) * np.sin(PH), -np.sin(TH)], axis=1)
+    u_p = np.stack([-np.sin(TH) * np.sin(PH), np.sin(TH) * np.cos(PH), np.zeros_like(TH)], axis=1)
+    v0 = r[:, None] * u
+    e_t = r_t[:, None] * u + r[:, None] * u_t
+    e_p = r_p[:, None] * u + r[:, None] * u_p
+    n0 = np.cross(e_t, e_p)
+    bad = np.linalg.norm(n0, axis=1) < 1e-9
+    n0[bad] = u[bad]
+    n0 /= np.linalg.norm(n0, axis=1, keepdims=True)
+    n0 *= np.sign(np.sum(n0 * u, axis=1, keepdims=True))
+    M = v0.shape[0]
+    A_v = rng.normal(0.0, 0.01, (M, 3, n_params))
+    A_n = rng.normal(0.0, 0.01, (M, 3, n_params))
+    albedo = rng.uniform(0.2, 0.9, (M, 3))
+    d = rng.normal(size=(n_spheres, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    c0 = d * rng.uniform(0.5, 0.8, (n_spheres, 1))
+    A_c = rng.normal(0.0, 0.01, (n_spheres, 3, n_params))
+    radii = rng.uniform(0.05, 0.15, n_spheres)
+    light = sh_lighting(rng, n_bands)
+    axes = rng.normal(size=(n_views, 3))
+    axes /= np.linalg.norm(axes, axis=1, keepdims=True)
+    w = axes * rng.uniform(0.0, np.pi, (n_views, 1))
+    t = rng.normal(0.0, 0.1, (n_views, 3))
+    return dict(v0=_f32(v0), n0=_f32(n0), A_v=_f32(A_v), A_n=_f32(A_n), c0=_f32(c0), A_c=_f32(A_c),
+                radii=_f32(radii), albedo=_f32(albedo), light=_f32(light),
+                poses=_f32(np.concatenate([w, t], axis=1)), n_bands=n_bands)

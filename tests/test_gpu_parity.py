@@ -167,9 +167,12 @@ def test_autograd_function_matches_direct_backward():
     T = {k: torch.from_numpy(sc[k]).to(dev).requires_grad_(True) for k in FIELDS}
     scene = Scene(T["centers"].detach(), T["radii"].detach(), T["light"].detach(), Config())
     B = shade(T["points"], T["normals"], T["albedo"], T["centers"], T["radii"], T["light"], scene)
-    dB = torch.randn_like(B)
+    dB = torch.from_numpy(np.random.default_rng(16).normal(size=tuple(B.shape)).astype(np.float32)).to(dev)
     B.backward(dB)
-    ref = O.shade_backward(O.Config(n_bands=4), *[sc[x] for x in FIELDS], dB.cpu().numpy())
+    sv = scene.new_saved(B.shape[0], dev)
+    scene.shade(T["points"].detach(), T["normals"].detach(), T["albedo"].detach(), saved=sv)
+    k = scene.saved_views(sv, B.shape[0])[1].cpu().numpy().astype(np.int64)
+    ref = O.shade_backward(O.Config(n_bands=4), *[sc[x] for x in FIELDS], dB.cpu().numpy(), k=k)
     name_map = dict(points="d_points", normals="d_normals", albedo="d_albedo", centers="d_centers",
                     radii="d_radii", light="d_light")
     for k_, t in T.items():
