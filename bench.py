@@ -471,6 +471,57 @@ def bench_serving(args, world, rank, local):
                            "unit": "pairs/s"})
 
 
+def bench_heightfield(args, world, rank, local):
+    """The precision workload: 1,048,576 points of a 1024x1024 height field,
+    300 spheres (radii log-uniform [0.01, 0.2]), n_bands = 8 (64 SH coeffs):
+    forward and backward times per pass, and the forward's error against the
+    FP64 oracle on a random sample of points, per output."""
+    import torch
+    from oracle import shs_oracle as O
+    from paper_2104_00359_gb300 import Config, Scene, synthetic
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = synthetic.height_field_scene(seed=3)
+    T = {k: torch.from_numpy(sc[k]).to(dev) for k in ("points", "normals", "albedo", "centers", "radii", "light")}
+    P, N = sc["points"].shape[0], sc["centers"].shape[0]
+    out = {}
+    for prec_name, prec in (("fp32", 0),):
+        scene = Scene(T["centers"], T["radii"], T["light"], Config(n_bands=8, precision=prec))
+        saved = scene.new_saved(P, dev)
+        dB = torch.randn((P, 3), device=dev)
+        times_f, times_b = [], []
+        for it in range(args.warmup + args.steps):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            B = scene.shade(T["points"], T["normals"], T["albedo"], saved=saved)
+            e1.record()
+            scene.backward(T["points"], T["normals"], T["albedo"], dB, saved=saved,
+                           want=("light", "albedo", "centers", "radii"))
+            e2.record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                times_f.append(e0.elapsed_time(e1))
+                times_b.append(e1.elapsed_time(e2))
+        k = scene.saved_views(saved, P)[1].cpu().numpy().astype(np.int64)
+        sel = np.sort(np.random.default_rng(1).choice(P, 256, replace=False))
+        args_o = [sc[f][sel] if f in ("points", "normals", "albedo") else sc[f]
+                  for f in ("points", "normals", "albedo", "centers", "radii", "light")]
+        ref = O.shade_forward(O.Config(n_bands=8), *args_o, k=k[sel])["radiance"]
+        got = B.cpu().numpy()[sel]
+        err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+        out[prec_name] = {"fwd_ms": statistics.fmean(times_f), "bwd_ms": statistics.fmean(times_b),
+                          "pairs_per_s_fwd": P * N / (statistics.fmean(times_f) * 1e-3),
+                          "pairs_per_s_fwd_bwd": P * N / ((statistics.fmean(times_f) + statistics.fmean(times_b)) * 1e-3),
+                          "radiance_max_rel_err_vs_fp64": float(err.max()), "k_mean": float(k.mean())}
+        scene.close()
+    return dict(metric="height field 1024^2 x 300 spheres, n_bands=8: pairs/sec and error vs FP64 per precision",
+                value=out["fp32"]["pairs_per_s_fwd_bwd"], unit="pairs/s", n_gpus=world, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f32", data="synthetic", impl="ours",
+                config={"workload": "height field 1024x1024 points, 300 spheres, n_bands=8 (64 SH coeffs)",
+                        "points": P, "spheres": N, "error_sample_points": 256},
+                precisions=out)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -479,7 +530,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--atomic", action="store_true", help="unordered (atomic) scene-gradient reduction")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--workload", choices=("capsule", "serving"), default="capsule",
+    ap.add_argument("--workload", choices=("capsule", "serving", "heightfield"), default="capsule",
                     help="capsule: the 512x512 G-buffer step (default); serving: the mixed request stream")
     ap.add_argument("--serve-jobs", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -490,6 +541,8 @@ def main():
         res = bench_reference(args, world, rank)
     elif args.workload == "serving":
         res = bench_serving(args, world, rank, local)
+    elif args.workload == "heightfield":
+        res = bench_heightfield(args, world, rank, local)
     else:
         res = bench_ours(args, world, rank, local, dist)
     if rank == 0 and res is not None:

@@ -216,6 +216,18 @@ shs_status shs_batch_destroy(shs_batch_t batch);
  * Returns SHS_ERR_INVALID_ARG for more than 32 requests. */
 shs_status shs_shade_batch(shs_batch_t batch, const shs_request* reqs, int32_t n_reqs, void* stream);
 
+/* Diagnostic: one CTA computes D = A B^T with M = 128 rows, n columns and
+ * inner size k on the tensor cores (tcgen05, BF16 operands, FP32 accumulation
+ * in tensor memory); split != 0 uses split precision (each operand as the sum
+ * of two BF16 values, three MMAs per product).  This checks the tensor-core
+ * operand layouts and descriptors of the reduced-precision tail (the paper's
+ * triple product, Eq. 7, and shading contraction, Eq. 8).
+ *   A: [128,k], B: [n,k], D: [128,n] float32 device arrays; 16 <= n <= 256,
+ *   16 <= k <= 64, both multiples of 16.  *device_status (device int) is set
+ *   to SHS_ERR_TIMEOUT if the bounded wait for the MMAs gave up. */
+shs_status shs_tc_gemm_selftest(const float* A, const float* B, int32_t n, int32_t k, int32_t split,
+                                float* D, int32_t* device_status, void* stream);
+
 /* Synchronises `stream`, then reports and clears the scene's device-side
  * status word: 0 = no error, otherwise a shs_status a kernel raised (e.g.
  * SHS_ERR_TIMEOUT when a bounded wait for staged data gave up). */

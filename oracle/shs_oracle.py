@@ -340,9 +340,10 @@ def shade_backward(cfg, points, normals, albedo, centers, radii, light, d_radian
 
     Returns dict with d_light [3,K], d_albedo [P,3], d_centers [N,3],
     d_radii [N], d_points [P,3], d_normals [P,3] and the forward dict.  For the
-    three sums over points it also returns ``abs_<name>``: the sum over points
-    of the absolute per-point terms, the scale that bounds rounding error in
-    any evaluation order."""
+    outputs that are sums (lighting, centres and radii over points; point
+    positions over spheres) it also returns ``abs_<name>``: the same sum of the
+    absolute terms, the scale that bounds rounding error in any evaluation
+    order."""
     n = cfg.n_bands
     K = n * n
     C = gaunt_tensor(n)
@@ -400,6 +401,7 @@ def shade_backward(cfg, points, normals, albedo, centers, radii, light, d_radian
     d_radii = np.zeros_like(rad)
     abs_d_centers = np.zeros_like(ctr)
     abs_d_radii = np.zeros_like(rad)
+    abs_d_points = np.zeros_like(pts)
     for j in range(ctr.shape[0]):
         d, D, valid, s, ca = cap_cosine(pts, ctr[j], rad[j])
         sh = d / D[:, None]
@@ -428,7 +430,9 @@ def shade_backward(cfg, points, normals, albedo, centers, radii, light, d_radian
         d_radii[j] = dr.sum()
         abs_d_centers[j] = np.abs(dd).sum(axis=0)
         abs_d_radii[j] = np.abs(dr).sum()
+        abs_d_points += np.abs(dd)
         d_points -= dd
     return dict(d_light=d_light, d_albedo=d_albedo, d_centers=d_centers, d_radii=d_radii,
                 d_points=d_points, d_normals=d_normals, df=df, forward=fw,
-                abs_d_light=abs_d_light, abs_d_centers=abs_d_centers, abs_d_radii=abs_d_radii)
+                abs_d_light=abs_d_light, abs_d_centers=abs_d_centers, abs_d_radii=abs_d_radii,
+                abs_d_points=abs_d_points)

@@ -22,9 +22,9 @@ def rel_err(got, ref, floor_frac=1e-3):
 
 
 def grad_err(name, got, ref):
-    """Normalised error of a gradient output.  Per-point outputs use rel_err.
-    The scene-level sums over points (d_light, d_centers, d_radii) may cancel,
-    so their scale also includes 1e-2 x the sum of absolute per-point terms:
+    """Normalised error of a gradient output.  Outputs that are sums which may
+    cancel (d_light, d_centers, d_radii over points; d_points over spheres)
+    also include 1e-2 x the sum of absolute terms in their scale:
     float32 summation of P terms in any order is accurate to a few ulps of that
     sum, so 1e-4 of this scale (1e-6 of the absolute sum) is a rounding-level
     gate, not a loosened one."""
