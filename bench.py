@@ -485,7 +485,7 @@ def bench_heightfield(args, world, rank, local):
     T = {k: torch.from_numpy(sc[k]).to(dev) for k in ("points", "normals", "albedo", "centers", "radii", "light")}
     P, N = sc["points"].shape[0], sc["centers"].shape[0]
     out = {}
-    for prec_name, prec in (("fp32", 0),):
+    for prec_name, prec in (("fp32", 0), ("bf16_split_tc", 2), ("fp16_split_tc", 3)):
         scene = Scene(T["centers"], T["radii"], T["light"], Config(n_bands=8, precision=prec))
         saved = scene.new_saved(P, dev)
         dB = torch.randn((P, 3), device=dev)

@@ -62,9 +62,15 @@ typedef enum {
     SHS_ERR_BUSY = 6         /* resource in use                                   */
 } shs_status;
 
-/* Arithmetic of the SH contractions (the pair terms and the exponent's scaling
- * always run in float32). */
-enum { SHS_FP32 = 0, SHS_TF32 = 1, SHS_BF16 = 2 };
+/* Arithmetic of the SH contractions: the squarings of the exponential (Eq. 7)
+ * and the shading contraction (Eq. 8).  The pair terms, the exponent's
+ * scaling and optimal linear step, and the adjoint always run in float32.
+ *   SHS_FP32: float32 on the CUDA cores (all band counts).
+ *   SHS_BF16 / SHS_FP16: tensor cores (tcgen05) with split 16-bit operands
+ *     (each value as the sum of two bfloat16 / IEEE half values, three MMAs
+ *     per product) and float32 accumulation; n_bands = 8 only.
+ *   SHS_TF32: not implemented (SHS_ERR_UNSUPPORTED). */
+enum { SHS_FP32 = 0, SHS_TF32 = 1, SHS_BF16 = 2, SHS_FP16 = 3 };
 
 typedef struct {
     int32_t n_bands;       /* SH bands n, 1..8; K = n*n (paper uses 8, Sec. 3.2)          */

@@ -14,7 +14,7 @@ from ctypes import POINTER, c_char_p, c_float, c_int32, c_int64, c_size_t, c_voi
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libshshadow.so")
 
 SHS_OK = 0
-SHS_FP32, SHS_TF32, SHS_BF16 = 0, 1, 2
+SHS_FP32, SHS_TF32, SHS_BF16, SHS_FP16 = 0, 1, 2, 3
 STATUS_NAMES = {0: "SHS_OK", 1: "SHS_ERR_INVALID_ARG", 2: "SHS_ERR_UNSUPPORTED", 3: "SHS_ERR_OOM",
                 4: "SHS_ERR_CUDA", 5: "SHS_ERR_TIMEOUT", 6: "SHS_ERR_BUSY"}
 

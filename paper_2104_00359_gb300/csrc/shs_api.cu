@@ -2,7 +2,10 @@
 // validation, scene memory, and dispatch to the per-band-count kernels.
 
 #include <atomic>
+#include <cmath>
 #include <cstdarg>
+#include <mutex>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -75,6 +78,10 @@ struct shs_scene_s {
     unsigned int* counter;
     float* batch_acc;      // [partial_stride] accumulator for batched calls (kept zero)
     unsigned int* batch_counter;
+    void* b3h;             // tensor-core precisions: 2^4 M_c (lighting-dependent), split operands
+    void* b3l;
+    float* fwork;          // f storage when shs_shade gets no saved buffer (tensor-core path)
+    int64_t fwork_points;
 };
 
 struct shs_batch_s {
@@ -136,9 +143,12 @@ shs_status check_config(const shs_config* c) {
     if (!(c->exp_tau > 0.f) || !(c->exp_tau < 1e30f)) return fail(SHS_ERR_INVALID_ARG, "exp_tau must be finite and > 0");
     if (c->exp_kmax < 0 || c->exp_kmax > shs::kMaxK) return fail(SHS_ERR_INVALID_ARG, "exp_kmax not in 0..%d", shs::kMaxK);
     if (c->fixed_k > shs::kMaxK) return fail(SHS_ERR_INVALID_ARG, "fixed_k > %d", shs::kMaxK);
-    if (c->precision != SHS_FP32 && c->precision != SHS_TF32 && c->precision != SHS_BF16)
+    if (c->precision != SHS_FP32 && c->precision != SHS_TF32 && c->precision != SHS_BF16 &&
+        c->precision != SHS_FP16)
         return fail(SHS_ERR_INVALID_ARG, "unknown precision %d", c->precision);
-    if (c->precision != SHS_FP32) return fail(SHS_ERR_UNSUPPORTED, "only SHS_FP32 is implemented");
+    if (c->precision == SHS_TF32) return fail(SHS_ERR_UNSUPPORTED, "SHS_TF32 is not implemented");
+    if ((c->precision == SHS_BF16 || c->precision == SHS_FP16) && c->n_bands != 8)
+        return fail(SHS_ERR_UNSUPPORTED, "tensor-core precisions need n_bands = 8");
     if (c->deterministic != 0 && c->deterministic != 1) return fail(SHS_ERR_INVALID_ARG, "deterministic must be 0 or 1");
     if (c->reserved != 0) return fail(SHS_ERR_INVALID_ARG, "reserved must be 0");
     return SHS_OK;
@@ -158,10 +168,143 @@ SceneView view_of(const shs_scene_s* s) {
     return v;
 }
 
+bool tensor_core_precision(const shs_config& c) { return c.precision == SHS_BF16 || c.precision == SHS_FP16; }
+
+constexpr int kB2Shift = 8;   // power-of-two pre-scaling of w_q y_i(w_q) (keeps half-precision parts normal)
+constexpr int kB3Shift = 4;   // and of M_c
+
 shs_status set_light(shs_scene_s* s, const float* light, cudaStream_t st) {
     cudaError_t e = cudaMemcpy2DAsync(s->light, s->Kpad * sizeof(float), light, s->K * sizeof(float),
                                       s->K * sizeof(float), 3, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && tensor_core_precision(s->cfg))
+        e = shs::launch_build_mcat<8>(view_of(s), s->b3h, s->b3l, s->cfg.precision == SHS_FP16,
+                                      std::ldexp(1.0f, kB3Shift), st);
     return e == cudaSuccess ? SHS_OK : cuda_fail(e, "copy lighting");
+}
+
+// Real orthonormal SH (no Condon-Shortley phase) in double precision from the
+// recurrences the device code uses: (x + i y)^m and d^m P_l / dz^m.
+void real_sh_double(int n, double x, double y, double z, double* out) {
+    double C[8], S[8], Pb[8][8];
+    C[0] = 1.0;
+    S[0] = 0.0;
+    for (int m = 1; m < n; ++m) {
+        C[m] = x * C[m - 1] - y * S[m - 1];
+        S[m] = x * S[m - 1] + y * C[m - 1];
+    }
+    for (int m = 0; m < n; ++m) {
+        double df = 1.0;
+        for (int t = 1; t < 2 * m; t += 2) df *= t;
+        Pb[m][m] = df;
+        if (m + 1 < n) Pb[m + 1][m] = (2 * m + 1) * z * Pb[m][m];
+        for (int l = m + 2; l < n; ++l)
+            Pb[l][m] = ((2 * l - 1) * z * Pb[l - 1][m] - (l + m - 1) * Pb[l - 2][m]) / (l - m);
+    }
+    for (int l = 0; l < n; ++l) {
+        for (int m = 0; m <= l; ++m) {
+            double ratio = 1.0;   // (l-m)!/(l+m)!
+            for (int t = l - m + 1; t <= l + m; ++t) ratio /= t;
+            double N = std::sqrt((2 * l + 1) / (4.0 * M_PI) * ratio) * (m ? std::sqrt(2.0) : 1.0);
+            if (m == 0) {
+                out[l * l + l] = N * Pb[l][0];
+            } else {
+                out[l * l + l + m] = N * Pb[l][m] * C[m];
+                out[l * l + l - m] = N * Pb[l][m] * S[m];
+            }
+        }
+    }
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton's method.
+void gauss_legendre(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double t = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double dp = n * (t * p1 - p0) / (t * t - 1.0);
+            const double dt = p1 / dp;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = t;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        const double dp = n * (t * p1 - p0) / (t * t - 1.0);
+        x[i] = t;
+        w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
+// Per device and operand format: Y (rows q, 64 columns) and 2^8 w Y^T (rows i,
+// 256 columns) for the product quadrature 11 Gauss-Legendre nodes in z x 22
+// uniform nodes in phi (exact for the degree-21 integrand of an 8-band triple
+// product); directions 242..255 are zero padding.
+struct TcTables {
+    void* b1h = nullptr;
+    void* b1l = nullptr;
+    void* b2h = nullptr;
+    void* b2l = nullptr;
+};
+TcTables g_tc_tables[64][2];
+std::mutex g_tc_mutex;
+
+shs_status tc_tables(int fp16, cudaStream_t st, TcTables* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(SHS_ERR_UNSUPPORTED, "device ordinal %d", dev);
+    std::lock_guard<std::mutex> lock(g_tc_mutex);
+    TcTables& t = g_tc_tables[dev][fp16 ? 1 : 0];
+    if (!t.b1h) {
+        const int Q = shs::kTcQ, K = 64, NZ = 11, NP = 22;
+        std::vector<float> b1(static_cast<size_t>(Q) * K, 0.f), b2(static_cast<size_t>(K) * Q, 0.f);
+        double zx[NZ], zw[NZ], Y[64];
+        gauss_legendre(NZ, zx, zw);
+        for (int a = 0; a < NZ; ++a)
+            for (int b = 0; b < NP; ++b) {
+                const int q = a * NP + b;
+                const double phi = 2.0 * M_PI * (b + 0.5) / NP, st_ = std::sqrt(1.0 - zx[a] * zx[a]);
+                real_sh_double(8, st_ * std::cos(phi), st_ * std::sin(phi), zx[a], Y);
+                const double w = zw[a] * 2.0 * M_PI / NP;
+                for (int i = 0; i < K; ++i) {
+                    b1[static_cast<size_t>(q) * K + i] = static_cast<float>(Y[i]);
+                    b2[static_cast<size_t>(i) * Q + q] = static_cast<float>(std::ldexp(w * Y[i], kB2Shift));
+                }
+            }
+        float* staging = nullptr;
+        const size_t bytes = sizeof(float) * Q * K;
+        TcTables nt;
+        e = cudaMalloc(&staging, 2 * bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&nt.b1h, Q * K * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&nt.b1l, Q * K * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&nt.b2h, Q * K * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&nt.b2l, Q * K * 2);
+        if (e == cudaSuccess) e = cudaMemcpy(staging, b1.data(), bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(staging + Q * K, b2.data(), bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = shs::launch_pack_split(staging, Q, K, fp16, nt.b1h, nt.b1l, 0);
+        if (e == cudaSuccess) e = shs::launch_pack_split(staging + Q * K, K, Q, fp16, nt.b2h, nt.b2l, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(staging);
+        if (e != cudaSuccess) {
+            cudaFree(nt.b1h);
+            cudaFree(nt.b1l);
+            cudaFree(nt.b2h);
+            cudaFree(nt.b2l);
+            return cuda_fail(e, "tensor-core tables");
+        }
+        t = nt;
+    }
+    (void)st;
+    *out = t;
+    return SHS_OK;
 }
 
 void free_scene(shs_scene_s* s) {
@@ -173,6 +316,9 @@ void free_scene(shs_scene_s* s) {
     cudaFree(s->counter);
     cudaFree(s->batch_acc);
     cudaFree(s->batch_counter);
+    cudaFree(s->b3h);
+    cudaFree(s->b3l);
+    cudaFree(s->fwork);
     delete s;
 }
 
@@ -257,6 +403,14 @@ shs_status shs_scene_create(const shs_config* cfg, int32_t n_spheres, const floa
         free_scene(sc);
         return cuda_fail(e, "allocate scene");
     }
+    if (tensor_core_precision(*cfg)) {
+        e = cudaMalloc(&sc->b3h, 192 * 64 * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&sc->b3l, 192 * 64 * 2);
+        if (e != cudaSuccess) {
+            free_scene(sc);
+            return cuda_fail(e, "allocate tensor-core lighting table");
+        }
+    }
     e = shs::launch_pack_spheres(centers, radii, sc->spheres, n_spheres, true, true, s);
     if (e != cudaSuccess) {
         free_scene(sc);
@@ -330,7 +484,47 @@ shs_status shs_shade(shs_scene_t sc, int64_t n_points, const float* points, cons
     a.albedo = albedo;
     a.radiance = radiance;
     split_saved(sc, n_points, saved, &a.saved_f, &a.saved_k);
-    cudaError_t e = dispatch<Fwd>(sc->cfg.n_bands, a, static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (tensor_core_precision(sc->cfg)) {
+        // pair terms in float32, then the exponential and shading on the tensor cores
+        if (!a.saved_f) {
+            if (sc->fwork_points < n_points) {
+                cudaError_t e = cudaStreamSynchronize(st);
+                cudaFree(sc->fwork);
+                sc->fwork = nullptr;
+                sc->fwork_points = 0;
+                if (e == cudaSuccess) e = cudaMalloc(&sc->fwork, sizeof(float) * sc->K * n_points);
+                if (e != cudaSuccess) return cuda_fail(e, "allocate f workspace");
+                sc->fwork_points = n_points;
+            }
+            a.saved_f = sc->fwork;
+        }
+        TcTables tt;
+        shs_status ts = tc_tables(sc->cfg.precision == SHS_FP16, st, &tt);
+        if (ts != SHS_OK) return ts;
+        cudaError_t e = shs::launch_forward_pairs<8>(a, st);
+        if (e != cudaSuccess) return cuda_fail(e, "launch pair terms");
+        shs::TcArgs t;
+        t.sc = a.sc;
+        t.n_points = n_points;
+        t.normals = normals;
+        t.albedo = albedo;
+        t.radiance = radiance;
+        t.f = a.saved_f;
+        t.saved_k = a.saved_k;
+        t.b1h = tt.b1h;
+        t.b1l = tt.b1l;
+        t.b2h = tt.b2h;
+        t.b2l = tt.b2l;
+        t.b3h = sc->b3h;
+        t.b3l = sc->b3l;
+        t.b2_unscale = std::ldexp(1.0f, -kB2Shift);
+        t.b3_unscale = std::ldexp(1.0f, -kB3Shift);
+        t.fp16 = sc->cfg.precision == SHS_FP16;
+        e = shs::launch_tail_tc<8>(t, st);
+        return e == cudaSuccess ? SHS_OK : cuda_fail(e, "launch tensor-core tail");
+    }
+    cudaError_t e = dispatch<Fwd>(sc->cfg.n_bands, a, st);
     return e == cudaSuccess ? SHS_OK : cuda_fail(e, "launch forward");
 }
 

@@ -84,7 +84,38 @@ struct BwdBatch {
     BwdArgs r[kMaxBatch];                 // partials/counter: per-request accumulator
 };
 
+// Reduced-precision tail on the tensor cores (8 bands): inputs are the
+// log-visibility f saved by the pair pass; tables are in the canonical K-major
+// layout as split 16-bit operands (hi, lo).
+struct TcArgs {
+    SceneView sc;
+    int64_t n_points;
+    const float* normals;
+    const float* albedo;
+    float* radiance;
+    const float* f;          // [K][P]
+    int* saved_k;            // [P] out
+    const void* b1h;         // y_i(w_q), rows q (256) x 64
+    const void* b1l;
+    const void* b2h;         // 2^s2 w_q y_i(w_q), rows i (64) x 256
+    const void* b2l;
+    const void* b3h;         // 2^s3 M_c[j][k], rows c*64+k (192) x 64
+    const void* b3l;
+    float b2_unscale;        // 2^-s2
+    float b3_unscale;        // 2^-s3
+    int fp16;                // operand format: 1 = IEEE half, 0 = bfloat16
+};
+
+constexpr int kTcQ = 256;    // quadrature directions (242 used) for 8 bands
+
+template <int NB> cudaError_t launch_forward_pairs(const FwdArgs& a, cudaStream_t s);
+template <int NB> cudaError_t launch_tail_tc(const TcArgs& a, cudaStream_t s);
+template <int NB> cudaError_t launch_build_mcat(const SceneView& sc, void* b3h, void* b3l, int fp16, float scale,
+                                                cudaStream_t s);
 template <int NB> cudaError_t launch_forward_batch(const FwdBatch& b, cudaStream_t s);
+// Lay out a row-major float [rows x cols] table as split 16-bit operands in
+// the canonical K-major layout (defined in shs_tc.cu).
+cudaError_t launch_pack_split(const float* src, int rows, int cols, int fp16, void* hi, void* lo, cudaStream_t s);
 template <int NB> cudaError_t launch_backward_batch(const BwdBatch& b, cudaStream_t s);
 template <int NB> cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
 template <int NB> cudaError_t launch_backward(const BwdArgs& a, cudaStream_t s);

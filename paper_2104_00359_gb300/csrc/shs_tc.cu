@@ -87,7 +87,29 @@ __global__ void __launch_bounds__(128) tc_gemm_selftest_kernel(const float* A, c
     if (warp == 0) shs::tc::tmem_dealloc(tmem, ncols);
 }
 
+__global__ void pack_split_kernel(const float* src, int rows, int cols, int fp16, uint16_t* hi, uint16_t* lo) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows * cols) return;
+    const int r = e / cols, c = e % cols;
+    uint16_t h, l;
+    if (fp16) shs::tc::split_fp16(src[e], h, l);
+    else shs::tc::split_bf16(src[e], h, l);
+    const uint32_t o = shs::tc::kmajor_offset(r, c, cols) >> 1;
+    hi[o] = h;
+    lo[o] = l;
+}
+
 }  // namespace
+
+namespace shs {
+cudaError_t launch_pack_split(const float* src, int rows, int cols, int fp16, void* hi, void* lo, cudaStream_t s) {
+    const int n = rows * cols;
+    pack_split_kernel<<<(n + 255) / 256, 256, 0, s>>>(src, rows, cols, fp16, static_cast<uint16_t*>(hi),
+                                                      static_cast<uint16_t*>(lo));
+    count_launch();
+    return cudaGetLastError();
+}
+}  // namespace shs
 
 extern "C" shs_status shs_tc_gemm_selftest(const float* A, const float* B, int32_t n, int32_t k, int32_t split,
                                            float* D, int32_t* device_status, void* stream) {

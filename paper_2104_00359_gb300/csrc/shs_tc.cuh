@@ -16,6 +16,9 @@
 
 #include <cstdint>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 namespace shs {
 namespace tc {
 
@@ -39,14 +42,17 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t smem_addr, uint32_t sbo_b
     return d;                                      // base offset 0, no swizzle
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16 (fmt 1) or F16
+// (fmt 0), both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, uint32_t fmt) {
     return (1u << 4)                                // D format F32
-         | (1u << 7)                                // A format BF16
-         | (1u << 10)                               // B format BF16
+         | (fmt << 7)                               // A format
+         | (fmt << 10)                              // B format
          | (static_cast<uint32_t>(N >> 3) << 17)
          | (static_cast<uint32_t>(M >> 4) << 24);
 }
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) { return idesc_f16kind(M, N, 1u); }
+__host__ __device__ constexpr uint32_t idesc_fp16(int M, int N) { return idesc_f16kind(M, N, 0u); }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                          bool accumulate) {
@@ -147,6 +153,41 @@ __device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) 
     const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
     hi = __bfloat16_as_ushort(h);
     lo = __bfloat16_as_ushort(l);
+}
+
+// Same split with IEEE half precision (11 significant bits per part).
+__device__ __forceinline__ void split_fp16(float x, uint16_t& hi, uint16_t& lo) {
+    const __half h = __float2half_rn(x);
+    const __half l = __float2half_rn(x - __half2float(h));
+    hi = __half_as_ushort(h);
+    lo = __half_as_ushort(l);
+}
+
+template <bool FP16>
+__device__ __forceinline__ void split16(float x, uint16_t& hi, uint16_t& lo) {
+    if constexpr (FP16) split_fp16(x, hi, lo);
+    else split_bf16(x, hi, lo);
+}
+
+// Store 64 values of row r as split 16-bit operands in the canonical K-major
+// layout of a [rows x 64] operand (SBO = 1024 B).
+template <bool FP16>
+__device__ __forceinline__ void store_row64(unsigned char* hi_base, unsigned char* lo_base, int r, const float* v) {
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            uint16_t h0, l0, h1, l1;
+            split16<FP16>(v[8 * g + 2 * e], h0, l0);
+            split16<FP16>(v[8 * g + 2 * e + 1], h1, l1);
+            h[e] = static_cast<uint32_t>(h0) | (static_cast<uint32_t>(h1) << 16);
+            l[e] = static_cast<uint32_t>(l0) | (static_cast<uint32_t>(l1) << 16);
+        }
+        const uint32_t off = (r >> 3) * 1024 + g * 128 + (r & 7) * 16;
+        *reinterpret_cast<uint4*>(hi_base + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(lo_base + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
 }
 
 }  // namespace tc
