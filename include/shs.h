@@ -132,7 +132,9 @@ shs_status shs_shade(shs_scene_t scene, int64_t n_points, const float* points,
  * Any output pointer may be NULL to skip that gradient.  `saved` is the buffer
  * shs_shade filled for the same inputs, or NULL to recompute.  The number of
  * squarings k is piecewise constant, so no gradient flows through it; no
- * gradient flows through a clamped cap (point inside a sphere). */
+ * gradient flows through a clamped cap (point inside a sphere).
+ * With 6 or more bands the scene keeps a workspace of K floats per point for
+ * the adjoint, grown (cudaMalloc) on the first call that needs more. */
 shs_status shs_shade_backward(shs_scene_t scene, int64_t n_points, const float* points,
                               const float* normals, const float* albedo, const void* saved,
                               const float* d_radiance, float* d_light, float* d_albedo,

@@ -82,6 +82,8 @@ struct shs_scene_s {
     void* b3l;
     float* fwork;          // f storage when shs_shade gets no saved buffer (tensor-core path)
     int64_t fwork_points;
+    float* bwork;          // [K][P] adjoint coefficients of the split backward (>= 6 bands)
+    int64_t bwork_points;
 };
 
 struct shs_batch_s {
@@ -319,6 +321,7 @@ void free_scene(shs_scene_s* s) {
     cudaFree(s->b3h);
     cudaFree(s->b3l);
     cudaFree(s->fwork);
+    cudaFree(s->bwork);
     delete s;
 }
 
@@ -571,6 +574,20 @@ static shs_status backward_common(shs_scene_t sc, int64_t n_points, const float*
     a.partials = sc->partials;
     a.counter = sc->cfg.deterministic ? nullptr : sc->counter;
     a.partial_stride = sc->partial_stride;
+    a.dfp_ws = nullptr;
+    if (sc->cfg.n_bands >= 6) {
+        // split backward: per-point tail pass, then a sphere-per-lane pair pass
+        if (sc->bwork_points < n_points) {
+            cudaError_t e = cudaStreamSynchronize(s);
+            cudaFree(sc->bwork);
+            sc->bwork = nullptr;
+            sc->bwork_points = 0;
+            if (e == cudaSuccess) e = cudaMalloc(&sc->bwork, sizeof(float) * sc->K * n_points);
+            if (e != cudaSuccess) return cuda_fail(e, "allocate adjoint workspace");
+            sc->bwork_points = n_points;
+        }
+        a.dfp_ws = sc->bwork;
+    }
     const int64_t tiles = (n_points + shs::kBlock - 1) / shs::kBlock;
     a.grid = static_cast<int>(tiles < sc->max_grid ? tiles : sc->max_grid);
     cudaError_t e = dispatch<Bwd>(sc->cfg.n_bands, a, s);

@@ -57,6 +57,7 @@ struct BwdArgs {
     float* d_radii;
     float* d_points;
     float* d_normals;
+    float* dfp_ws;           // [K][P] pair-adjoint coefficients (split backward, >= 6 bands)
     float* partials;         // [grid][stride] scratch
     unsigned int* counter;   // scratch, zero between launches
     int partial_stride;

@@ -725,6 +725,7 @@ __device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v
 // Adjoint of one 128-point tile of one request: per-point outputs are written,
 // the scene-level sums are added to the block's shared accumulators
 // (s_dl: d_light and loss per warp, s_acc: per warp and sphere).
+template <bool PAIRS = true>
 __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_sph, const float* s_light,
                                               float* s_acc, float (*s_dl)[3 * K + 1], int64_t tile,
                                               int lane, int warp) {
@@ -872,6 +873,14 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_
 #pragma unroll
     for (int i = 0; i < K; ++i) dfp[i] *= a.sc.neg_2pi_eps * SH::norm(i);
 
+    if constexpr (!PAIRS) {
+        // split backward: the pair pass reads these coefficients
+        if (live) {
+#pragma unroll
+            for (int i = 0; i < K; ++i) a.dfp_ws[i * P + q] = dfp[i];
+        }
+        return;
+    }
     // ---- pair adjoints
     const bool want_sph = a.d_centers || a.d_radii;
     if (want_sph || a.d_points) {
@@ -957,7 +966,8 @@ __device__ void finish_scene_sums(const BwdArgs& a, int E) {
 //   [3K+1, 3K+1+4N)  per sphere (d cx, d cy, d cz, d r)
 // Up to 4 bands: four resident blocks per SM (<= 128 registers per thread) for
 // the pair loop; above that the tail state needs the registers.
-__global__ void __launch_bounds__(kBlock, NB <= 4 ? 4 : 1) backward_kernel(BwdArgs a) {
+template <bool PAIRS>
+__global__ void __launch_bounds__(kBlock, NB <= 4 ? 4 : 1) backward_kernel_t(BwdArgs a) {
     extern __shared__ __align__(16) float4 dyn[];
     __shared__ __align__(16) float s_light[3 * KPAD];
     __shared__ __align__(8) uint64_t s_bar;
@@ -975,11 +985,11 @@ __global__ void __launch_bounds__(kBlock, NB <= 4 ? 4 : 1) backward_kernel(BwdAr
 
     const int64_t ntiles = (a.n_points + kBlock - 1) / kBlock;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-        backward_tile(a, s_sph, s_light, s_acc, s_dl, tile, lane, warp);
+        backward_tile<PAIRS>(a, s_sph, s_light, s_acc, s_dl, tile, lane, warp);
 
     // ---- block reduction, then one scene-level reduction
     __syncthreads();
-    const int E = 3 * K + 1 + 4 * N;
+    const int E = PAIRS ? 3 * K + 1 + 4 * N : 3 * K + 1;   // tail-only: lighting and loss entries
     float* out = a.partials + static_cast<size_t>(blockIdx.x) * a.partial_stride;
     const bool det = a.counter == nullptr;
     for (int e = threadIdx.x; e < E; e += kBlock) {
@@ -995,10 +1005,141 @@ __global__ void __launch_bounds__(kBlock, NB <= 4 ? 4 : 1) backward_kernel(BwdAr
         if (det) out[e] = v;
         else atomicAdd(a.partials + e, v);
     }
-    if (det) return;
+    if (det || !PAIRS) return;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    finish_scene_sums(a, E);
+}
+
+// ---------------------------------------------------------------------------
+// split backward, pair pass (>= 6 bands): one sphere per lane
+// ---------------------------------------------------------------------------
+// Work unit: 32 points.  Their gradient-polynomial coefficients (from the
+// adjoint coefficients the tail pass stored) are staged in shared memory and
+// read as warp-wide broadcasts; each lane owns one sphere, so sphere sums stay
+// in registers and only the per-point gradient needs a cross-lane sum.
+constexpr int kPtTile = 32;
+// Up to 5 bands the pair pass uses the per-band gradient polynomials in
+// monomial form; above that their float32 evaluation loses accuracy (large
+// alternating coefficients at degree 6-7), so it uses the SH recurrences and
+// their reverse sweep, broadcasting the K adjoint coefficients instead.
+constexpr bool kMonoPairs = NB <= 5;
+constexpr int NGP = kMonoPairs ? (SH::NG + 3) / 4 * 4 : (K + 3) / 4 * 4;
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kBlock) bwd_pairs_t_kernel(BwdArgs a) {
+    extern __shared__ __align__(16) float4 dyn[];
+    __shared__ __align__(16) float s_light[3 * KPAD];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ __align__(16) float s_gq[kPtTile][NGP];
+    __shared__ __align__(16) float4 s_pt[kPtTile];        // x, y, z, Phi_0
+    __shared__ float s_dpt[kPtTile][3];
+    __shared__ bool s_last;
+    const int N = a.sc.n_spheres;
+    float4* s_sph = dyn;                                   // [N]
+    float4* s_sacc = dyn + N;                              // [N] block sphere sums
+    if (!stage_scene(a.sc, s_sph, s_light, &s_bar)) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int j = tid; j < N; j += kBlock) s_sacc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool want_pts = a.d_points != nullptr;
+    const int64_t P = a.n_points;
+    const int64_t nunits = (P + kPtTile - 1) / kPtTile;
+    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        __syncthreads();
+        if (tid < kPtTile) {
+            const int64_t p = u * kPtTile + tid;
+            const bool live = p < P;
+            float dfp[K];
+#pragma unroll
+            for (int i = 0; i < K; ++i) dfp[i] = live ? __ldg(a.dfp_ws + i * P + p) : 0.f;
+            if constexpr (kMonoPairs) {
+                float gq[SH::NG];
+                SH::grad_coeffs(dfp, gq);
+#pragma unroll
+                for (int o = 0; o < SH::NG; ++o) s_gq[tid][o] = gq[o];
+            } else {
+#pragma unroll
+                for (int o = 0; o < K; ++o) s_gq[tid][o] = dfp[o];
+            }
+            s_pt[tid] = live ? make_float4(__ldg(a.points + 3 * p), __ldg(a.points + 3 * p + 1),
+                                           __ldg(a.points + 3 * p + 2), dfp[0])
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+            s_dpt[tid][0] = s_dpt[tid][1] = s_dpt[tid][2] = 0.f;
+        }
+        __syncthreads();
+        for (int j0 = 0; j0 < N; j0 += kBlock) {
+            const int j = j0 + tid;
+            const bool has = j < N;
+            const float4 sp = has ? s_sph[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+            for (int t = 0; t < kPtTile; ++t) {
+                const float4 pt = s_pt[t];
+                float gcx, gcy, gcz, gr;
+                if constexpr (kMonoPairs)
+                    pair_backward_grad(pt.x, pt.y, pt.z, sp, &s_gq[t][0], pt.w, gcx, gcy, gcz, gr);
+                else
+                    pair_backward(pt.x, pt.y, pt.z, sp, &s_gq[t][0], gcx, gcy, gcz, gr);
+                if (!has) gcx = gcy = gcz = gr = 0.f;
+                acc.x += gcx;
+                acc.y += gcy;
+                acc.z += gcz;
+                acc.w += gr;
+                if (want_pts) {
+                    const float sx = warp_sum_f(gcx), sy = warp_sum_f(gcy), sz = warp_sum_f(gcz);
+                    if (lane == 0) {
+                        atomicAdd(&s_dpt[t][0], sx);
+                        atomicAdd(&s_dpt[t][1], sy);
+                        atomicAdd(&s_dpt[t][2], sz);
+                    }
+                }
+            }
+            if (has) {
+                float4 v = s_sacc[j];
+                v.x += acc.x;
+                v.y += acc.y;
+                v.z += acc.z;
+                v.w += acc.w;
+                s_sacc[j] = v;
+            }
+        }
+        if (want_pts) {
+            __syncthreads();
+            if (tid < kPtTile) {
+                const int64_t p = u * kPtTile + tid;
+                if (p < P) {
+                    a.d_points[3 * p] = -s_dpt[tid][0];
+                    a.d_points[3 * p + 1] = -s_dpt[tid][1];
+                    a.d_points[3 * p + 2] = -s_dpt[tid][2];
+                }
+            }
+        }
+    }
+    (void)warp;
+    __syncthreads();
+    // sphere entries of the block's partial row (the tail pass wrote the others)
+    const int E = 3 * K + 1 + 4 * N;
+    float* out = a.partials + static_cast<size_t>(blockIdx.x) * a.partial_stride;
+    const bool det = a.counter == nullptr;
+    for (int e = 3 * K + 1 + tid; e < E; e += kBlock) {
+        const int q = e - (3 * K + 1);
+        const float4 v = s_sacc[q >> 2];
+        const float x = (q & 3) == 0 ? v.x : (q & 3) == 1 ? v.y : (q & 3) == 2 ? v.z : v.w;
+        if (det) out[e] = x;
+        else atomicAdd(a.partials + e, x);
+    }
+    if (det) return;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!s_last) return;
     finish_scene_sums(a, E);
@@ -1140,10 +1281,10 @@ size_t backward_dyn_smem(int n_spheres) {
 
 template <>
 int backward_blocks_per_sm<NB>(int n_spheres) {
-    cudaFuncSetAttribute(backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(backward_kernel_t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(backward_dyn_smem(kMaxSpheres)));
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, backward_kernel, kBlock,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, backward_kernel_t<true>, kBlock,
                                                       backward_dyn_smem(n_spheres)) != cudaSuccess || nb < 1)
         nb = 1;
     return nb;
@@ -1253,14 +1394,37 @@ template <>
 cudaError_t launch_backward<NB>(const BwdArgs& a, cudaStream_t s) {
     if (a.n_points <= 0) return cudaSuccess;
     const size_t smem = backward_dyn_smem(a.sc.n_spheres);
-    static const cudaError_t attr = cudaFuncSetAttribute(
-        backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-        static_cast<int>(backward_dyn_smem(kMaxSpheres)));
+    static const cudaError_t attr = [] {
+        cudaError_t e = cudaFuncSetAttribute(backward_kernel_t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(backward_dyn_smem(kMaxSpheres)));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(backward_kernel_t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(backward_dyn_smem(kMaxSpheres)));
+        return e;
+    }();
     cudaError_t err = attr;
     if (err != cudaSuccess) return err;
-    backward_kernel<<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
-    count_launch();
-    err = cudaGetLastError();
+    if (a.dfp_ws) {
+        // split backward: tail pass (per point), then the pair pass (per sphere lane)
+        backward_kernel_t<false><<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
+        count_launch();
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        const bool need_pairs = a.d_centers || a.d_radii || a.d_points;
+        static const cudaError_t attr2 = cudaFuncSetAttribute(
+            bwd_pairs_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSpheres * 32);
+        if (attr2 != cudaSuccess) return attr2;
+        if (need_pairs || a.counter != nullptr) {
+            bwd_pairs_t_kernel<<<static_cast<unsigned>(a.grid), kBlock,
+                                 static_cast<size_t>(a.sc.n_spheres) * 32u, s>>>(a);
+            count_launch();
+            err = cudaGetLastError();
+        }
+    } else {
+        backward_kernel_t<true><<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
+        count_launch();
+        err = cudaGetLastError();
+    }
     if (err != cudaSuccess || a.counter != nullptr) return err;
     const int E = 3 * K + 1 + 4 * a.sc.n_spheres;
     reduce_partials_kernel<<<(E + 31) / 32, 256, 0, s>>>(a, a.grid);
