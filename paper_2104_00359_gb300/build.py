@@ -46,6 +46,13 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _tune_defines():
+    """Optional -D tuning flags from SHS_TUNE="NAME=V,NAME=V" (e.g. register
+    caps for launch-bound experiments)."""
+    spec = os.environ.get("SHS_TUNE", "").strip()
+    return [f"-D{kv.strip()}" for kv in spec.split(",") if kv.strip()]
+
+
 def _flags():
     # -ftz=true: float32 denormals flush to zero, so rsqrt/rcp map to single
     # MUFU instructions (no denormal fix-up code); the path never produces
@@ -55,7 +62,7 @@ def _flags():
 
 
 def _compile(src, obj, defines, log):
-    cmd = [nvcc()] + _flags() + ["-Xptxas", "-v"] + defines + ["-c", src, "-o", obj]
+    cmd = [nvcc()] + _flags() + ["-Xptxas", "-v"] + defines + _tune_defines() + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     with open(log, "w") as fh:
         fh.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)

