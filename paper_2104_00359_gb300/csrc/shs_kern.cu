@@ -377,7 +377,7 @@ __device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_
 #define SHS_FWD_MINB 1
 #endif
 #ifndef SHS_BWD_MINB
-#define SHS_BWD_MINB 4
+#define SHS_BWD_MINB 3
 #endif
 
 template <bool TAIL>
