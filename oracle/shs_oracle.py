@@ -341,7 +341,8 @@ def shade_backward(cfg, points, normals, albedo, centers, radii, light, d_radian
     Returns dict with d_light [3,K], d_albedo [P,3], d_centers [N,3],
     d_radii [N], d_points [P,3], d_normals [P,3] and the forward dict.  For the
     outputs that are sums (lighting, centres and radii over points; point
-    positions over spheres) it also returns ``abs_<name>``: the same sum of the
+    positions over spheres; normals over the K lobe coefficients) it also
+    returns ``abs_<name>``: the same sum of the
     absolute terms, the scale that bounds rounding error in any evaluation
     order."""
     n = cfg.n_bands
@@ -372,8 +373,12 @@ def shade_backward(cfg, points, normals, albedo, centers, radii, light, d_radian
     nlen = np.linalg.norm(nrm, axis=-1, keepdims=True)
     nh = nrm / nlen
     coef = zh_rotation_scale(n) * clamped_cosine_zh(n)[band_of(K)]
-    dnh = np.einsum("pk,pkc->pc", dH * coef, real_sh_grad(n, nh))
+    Yg = real_sh_grad(n, nh)                       # [P, K, 3]
+    dnh = np.einsum("pk,pkc->pc", dH * coef, Yg)
     d_normals = (dnh - nh * np.sum(nh * dnh, axis=-1, keepdims=True)) / nlen
+    # each component is a sum over the K coefficients of tangential terms
+    Yt = Yg - nh[:, None, :] * np.sum(nh[:, None, :] * Yg, axis=-1, keepdims=True)
+    abs_d_normals = np.einsum("pk,pkc->pc", np.abs(dH * coef), np.abs(Yt)) / nlen
 
     # V = e0 * S_k ;  S_{t+1} = S_t * S_t ;  S_0 = a (sqrt(4pi) e_0 + g)
     k_pt, e0, g, a, levels = ex["k"], ex["e0"], ex["g"], ex["a"], ex["levels"]
@@ -435,4 +440,4 @@ def shade_backward(cfg, points, normals, albedo, centers, radii, light, d_radian
     return dict(d_light=d_light, d_albedo=d_albedo, d_centers=d_centers, d_radii=d_radii,
                 d_points=d_points, d_normals=d_normals, df=df, forward=fw,
                 abs_d_light=abs_d_light, abs_d_centers=abs_d_centers, abs_d_radii=abs_d_radii,
-                abs_d_points=abs_d_points)
+                abs_d_points=abs_d_points, abs_d_normals=abs_d_normals)

@@ -539,10 +539,16 @@ def generate():
         parts.append("        (void)x; (void)y; (void)z; (void)gq; (void)gx; (void)gy; (void)gz;")
         parts.append(indent(ge_l))
         parts.append("    }")
-        parts.append("    __device__ __forceinline__ static void mul(const float* a, const float* b, float* o) {")
+        # From 7 bands on the products are tens of thousands of FMAs each:
+        # one out-of-line copy per translation unit instead of one per call
+        # site keeps compile time and the instruction footprint bounded (the
+        # operands of an out-of-line call live in local memory, a few hundred
+        # bytes against ~10^4 FMAs per call).
+        prod = "__noinline__" if n >= 7 else "__forceinline__"
+        parts.append(f"    __device__ {prod} static void mul(const float* a, const float* b, float* o) {{")
         parts.append(indent(mul_l))
         parts.append("    }")
-        parts.append("    __device__ __forceinline__ static void sqr(const float* a, float* o) {")
+        parts.append(f"    __device__ {prod} static void sqr(const float* a, float* o) {{")
         parts.append(indent(sqr_l))
         parts.append("    }")
         parts.append("};")
