@@ -27,7 +27,10 @@ Readings where the paper is silent (each is also a configuration field):
 * A shading point inside or on a sphere (D <= r) sees a hemisphere cap
   (sin(alpha) clamped to 1, cos(alpha) = 0); no gradient flows through the
   clamped cap angle.  A sphere whose centre coincides with the point (D = 0)
-  is skipped.  No horizon culling: every sphere contributes.
+  is skipped.  By default every sphere contributes (the paper sums all
+  blockers); with ``horizon_cull`` a sphere lying entirely below the tangent
+  plane at x, (c - x) . n_hat < -r, is dropped for that point (no gradient
+  flows through that selection).
 * SH exponential (the paper defers to Ren et al. 2006 "scaling, squaring and
   optimal linear approximation" without giving constants):
     1. DC isolation  e0 = exp(f_0 / sqrt(4 pi)),  fh = f with fh_0 = 0
@@ -64,6 +67,7 @@ class Config:
     exp_tau: float = 1.0
     exp_kmax: int = 16
     fixed_k: int = -1
+    horizon_cull: bool = False
 
 
 def sh_index(l, m):
@@ -246,7 +250,17 @@ def log_cap_zh(n_bands, epsilon, cos_a):
     return out
 
 
-def log_visibility(cfg, points, centers, radii):
+def horizon_keep(cfg, d, radius, normals):
+    """Pairs that contribute: all of them, or with horizon culling those whose
+    sphere reaches the upper half-space of the normal, (c - x) . n_hat >= -r."""
+    if not cfg.horizon_cull:
+        return np.ones(d.shape[0], dtype=bool)
+    nrm = np.asarray(normals, np.float64)
+    nh = nrm / np.linalg.norm(nrm, axis=-1, keepdims=True)
+    return np.sum(d * nh, axis=-1) >= -radius
+
+
+def log_visibility(cfg, points, centers, radii, normals=None):
     """f(x) = sum_j rotate(ZH of log V'_j, (c_j - x)/|c_j - x|)  [P, K]."""
     n = cfg.n_bands
     K = n * n
@@ -255,8 +269,11 @@ def log_visibility(cfg, points, centers, radii):
     f = np.zeros((P, K))
     lvec = band_of(K)
     R = zh_rotation_scale(n)
+    if cfg.horizon_cull and normals is None:
+        raise ValueError("horizon culling needs the normals")
     for j in range(np.shape(centers)[0]):
         d, D, valid, s, ca = cap_cosine(pts, np.asarray(centers[j], np.float64), float(radii[j]))
+        valid = valid & horizon_keep(cfg, d, float(radii[j]), normals)
         zh = log_cap_zh(n, cfg.epsilon, ca)
         sh = d / D[:, None]
         Fj = R[None, :] * zh[:, lvec] * real_sh(n, sh)
@@ -323,7 +340,7 @@ def shade_forward(cfg, points, normals, albedo, centers, radii, light, k=None):
     alb = np.asarray(albedo, np.float64)
     L = np.asarray(light, np.float64).reshape(3, n * n)
     f = log_visibility(cfg, pts, np.asarray(centers, np.float64).reshape(-1, 3),
-                       np.asarray(radii, np.float64).reshape(-1))
+                       np.asarray(radii, np.float64).reshape(-1), normals)
     V, ex = sh_exp(cfg, C, f, k)
     H = cosine_lobe(n, normals)
     W = sh_product(C, V, H)
@@ -409,6 +426,7 @@ def shade_backward(cfg, points, normals, albedo, centers, radii, light, d_radian
     abs_d_points = np.zeros_like(pts)
     for j in range(ctr.shape[0]):
         d, D, valid, s, ca = cap_cosine(pts, ctr[j], rad[j])
+        valid = valid & horizon_keep(cfg, d, rad[j], nrm)
         sh = d / D[:, None]
         Y = real_sh(n, sh)
         zh = log_cap_zh(n, cfg.epsilon, ca)

@@ -78,3 +78,31 @@ def test_adjoint_with_free_k_away_from_boundaries():
             assert np.array_equal(fp["k"], fw["k"]) and np.array_equal(fm["k"], fw["k"])
             fd = np.sum(dB * (fp["radiance"] - fm["radiance"])) / (2 * h)
             assert abs(fd - g["d_centers"][j, c]) < 2e-7 * max(1.0, abs(fd))
+
+
+def test_adjoint_with_horizon_cull():
+    """Horizon culling is a per-pair selection with no gradient: away from its
+    boundary the adjoint still matches central differences."""
+    sc = _scene(44, 10, 6, 4)
+    cfg = O.Config(n_bands=4, fixed_k=2, horizon_cull=True)
+    nh = sc["normals"] / np.linalg.norm(sc["normals"], axis=1, keepdims=True)
+    margin = np.einsum("pjc,pc->pj", sc["centers"][None] - sc["points"][:, None], nh) + sc["radii"][None]
+    assert (margin < 0).any() and (margin > 0).any()           # some pairs culled, some kept
+    keep = np.all(np.abs(margin) > 1e-3, axis=1)
+    for k in ("points", "normals", "albedo"):
+        sc[k] = sc[k][keep]
+    dB = np.random.default_rng(45).normal(size=sc["points"].shape)
+    g = O.shade_backward(cfg, *[sc[k] for k in ORDER], dB)
+    h = 1e-6
+    for name, grad in (("centers", g["d_centers"]), ("radii", g["d_radii"]), ("points", g["d_points"])):
+        base = sc[name]
+        it = np.nditer(base, flags=["multi_index"])
+        for _ in it:
+            idx = it.multi_index
+            p, m = dict(sc), dict(sc)
+            p[name], m[name] = base.copy(), base.copy()
+            p[name][idx] += h
+            m[name][idx] -= h
+            fd = np.sum(dB * (O.shade_forward(cfg, *[p[k] for k in ORDER])["radiance"]
+                              - O.shade_forward(cfg, *[m[k] for k in ORDER])["radiance"])) / (2 * h)
+            assert abs(fd - grad[idx]) < 2e-7 * max(1.0, abs(fd)), (name, idx, fd, grad[idx])

@@ -399,3 +399,48 @@ def test_monte_carlo_brute_force_report():
     # worst ~0.38 (a point inside a sphere, hemisphere cap at n = 4).
     print("MC relative errors:", np.round(errs, 3))
     assert np.mean(errs) < 0.2 and max(errs) < 0.5, errs
+
+
+def test_horizon_cull_below_horizon_is_unoccluded():
+    """A sphere entirely below the tangent plane cannot block the upper
+    hemisphere: with horizon culling the shading equals the unoccluded closed
+    form exactly; without it the band-limited SH method still sees it (the
+    lobe rings below the horizon, and exp mixes bands)."""
+    n = 4
+    sc = S.random_scene(23, 40, 0, n)
+    nrm = sc["normals"].astype(float)
+    nh = nrm / np.linalg.norm(nrm, axis=1, keepdims=True)
+    pts = sc["points"].astype(float)
+    Ahat = np.array([np.pi, 2 * np.pi / 3, np.pi / 4, 0.0])[O.band_of(16)]
+    ref = sc["albedo"].astype(float) * ((_scipy_real_sh(n, nh) * Ahat) @ sc["light"].astype(float).T)
+    for p in range(pts.shape[0]):
+        # one sphere per point, centred 0.5 below it along -n (r = 0.2 < 0.5)
+        ctr = (pts[p] - 0.5 * nh[p])[None]
+        args = (pts[p:p + 1], nrm[p:p + 1], sc["albedo"][p:p + 1], ctr, np.array([0.2]), sc["light"])
+        on = O.shade_forward(O.Config(n_bands=n, horizon_cull=True), *args)
+        off = O.shade_forward(O.Config(n_bands=n), *args)
+        np.testing.assert_allclose(on["radiance"][0], ref[p], rtol=1e-12, atol=1e-12)
+        assert np.abs(on["f"]).max() == 0.0
+        assert np.abs(off["f"]).max() > 1e-4
+
+
+def test_horizon_cull_boundary_and_upper_spheres():
+    """Spheres reaching the upper half-space are kept (the boundary
+    (c - x) . n_hat = -r included); culling changes nothing when every sphere
+    does."""
+    cfg_on = O.Config(n_bands=4, horizon_cull=True)
+    x = np.zeros((1, 3))
+    nz = np.array([[0.0, 0.0, 2.0]])            # unnormalised normal: the test uses n_hat
+    d = np.array([[0.5, 0.0, -0.25]])
+    keep = O.horizon_keep(cfg_on, d, 0.25, nz)
+    drop = O.horizon_keep(cfg_on, d - np.array([[0.0, 0.0, 1e-9]]), 0.25, nz)
+    assert keep[0] and not drop[0]
+    # the 32 x 32 plane: normals +z, sphere centres at z >= 0.1 (every sphere
+    # reaches the upper half-space of every point)
+    sc = S.plane_grid_scene(seed=0, grid=12)
+    ctr = sc["centers"].astype(float)
+    assert np.all(ctr[:, 2] + sc["radii"] >= 0.0)
+    args = (sc["points"], sc["normals"], sc["albedo"], ctr, sc["radii"], sc["light"])
+    on = O.shade_forward(cfg_on, *args)["radiance"]
+    off = O.shade_forward(O.Config(n_bands=4), *args)["radiance"]
+    np.testing.assert_array_equal(on, off)
