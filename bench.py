@@ -70,6 +70,36 @@ def flop_model(n, n_spheres, k_mean):
     return dict(fwd=n_spheres * pf + tf, bwd=n_spheres * pb + tb)
 
 
+KERNEL_SOURCES = ("paper_2104_00359_gb300/csrc/shs_kern.cu", "paper_2104_00359_gb300/csrc/shs_internal.h",
+                  "paper_2104_00359_gb300/csrc/generated/shs_sh_gen.cuh")
+
+
+def kernel_source_hash():
+    """Short hash of the sources the shading kernels are compiled from."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, workload_tag):
+    """DRAM bytes per launch (read + write) of ``kernel`` from the committed
+    ncu summary, or None when the kernels changed since it was taken.  The
+    summary carries lines 'traffic <kernel> <workload> <bytes> <source hash>'."""
+    import glob
+    want = kernel_source_hash()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as fh:
+            for line in fh:
+                parts = line.strip().strip("`").split()
+                if len(parts) == 5 and parts[0] == "traffic" and parts[1] == kernel and parts[2] == workload_tag:
+                    if parts[4] == want:
+                        return float(parts[3])
+    return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -270,7 +300,11 @@ def bench_ours(args, world, rank, local, dist):
         latency_ms={"p50": p50, "p99": p99, "fwd_mean": fwd_mean, "bwd_mean": bwd_mean},
         roofline={"bound": "alu", "kernel": "backward (pair adjoints + tail adjoint)",
                   "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                  "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                  "traffic": profiled_traffic("backward_kernel_t", "capsule512_n4"),
+                  "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (profiles/), "
+                                    "null when the kernel sources changed since",
+                  "kernel_source_hash": kernel_source_hash(),
+                  "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                   "flops_per_point": fm["bwd"], "k_mean": k_mean,
                   "forward": {"achieved": achieved_fwd, "frac": achieved_fwd / peak,
                               "flops_per_point": fm["fwd"]}},

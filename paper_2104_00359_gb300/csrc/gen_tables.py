@@ -423,12 +423,25 @@ def emit_monomial_route(n):
     for l in range(n):
         offs.append(na)
         na += len(monomials(l))
-    ml, name = _mono_lines(n - 1)
+    # Monomials are built up to degree n-2; the top band's terms are
+    # G_{n-1} x^a y^b z^c = (G_{n-1} v) m' with v the first variable of the
+    # monomial and m' of degree n-2, so its monomials are never formed.
+    top = n - 1
+    ml, name = _mono_lines(max(top - 1, 1) if top >= 1 else 0)
+    if top >= 2:
+        ml += [f"const float gt{v} = G[{top}] * {v};" for v in "xyz"]
     acc = []
     for l in range(n):
         for ai, mono in enumerate(monomials(l)):
-            m = "1.0f" if mono == (0, 0, 0) else name[mono]
-            acc.append(f"acc[{offs[l] + ai}] = fmaf(G[{l}], {m}, acc[{offs[l] + ai}]);")
+            o = offs[l] + ai
+            if l == top and l >= 2:
+                v = next(i for i in range(3) if mono[i] > 0)
+                low = list(mono)
+                low[v] -= 1
+                acc.append(f"acc[{o}] = fmaf(gt{'xyz'[v]}, {name[tuple(low)]}, acc[{o}]);")
+            else:
+                m = "1.0f" if mono == (0, 0, 0) else name[mono]
+                acc.append(f"acc[{o}] = fmaf(G[{l}], {m}, acc[{o}]);")
     m2f = []
     for i in range(n * n):
         l = int(math.isqrt(i))
@@ -543,12 +556,14 @@ def generate():
         # one out-of-line copy per translation unit instead of one per call
         # site keeps compile time and the instruction footprint bounded (the
         # operands of an out-of-line call live in local memory, a few hundred
-        # bytes against ~10^4 FMAs per call).
+        # bytes against ~10^4 FMAs per call; the operands never alias, which
+        # lets every input stay in a register while the outputs are stored).
         prod = "__noinline__" if n >= 7 else "__forceinline__"
-        parts.append(f"    __device__ {prod} static void mul(const float* a, const float* b, float* o) {{")
+        parts.append(f"    __device__ {prod} static void mul(const float* __restrict__ a, const float* __restrict__ b,")
+        parts.append("                                      float* __restrict__ o) {")
         parts.append(indent(mul_l))
         parts.append("    }")
-        parts.append(f"    __device__ {prod} static void sqr(const float* a, float* o) {{")
+        parts.append(f"    __device__ {prod} static void sqr(const float* __restrict__ a, float* __restrict__ o) {{")
         parts.append(indent(sqr_l))
         parts.append("    }")
         parts.append("};")

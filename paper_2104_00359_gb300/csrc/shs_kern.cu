@@ -141,6 +141,44 @@ __device__ __forceinline__ void cap_integrals(float c, float s2, const float* dP
     for (int l = 1; l < NB; ++l) G[l] = s2 * dP[l] * (1.f / float(l * (l + 1)));
 }
 
+// Up to 5 bands, G_l and P_l in closed form in s2 = sin^2 alpha and
+// c = cos alpha, with c^2 = 1 - s2 substituted (fewer operations than the
+// recurrences, and s2 = r^2 / D^2 is the accurately known quantity):
+//   G_0 = 1 - c, G_1 = s2/2, G_2 = c s2/2, G_3 = s2 (1/2 - 5 s2/8),
+//   G_4 = c s2 (1/2 - 7 s2/8);
+//   P_1 = c, P_2 = 1 - 3 s2/2, P_3 = c (1 - 5 s2/2), P_4 = 1 - 5 s2 + 35 s2^2/8.
+__device__ __forceinline__ void cap_closed(float c, float s2, float* G, float* P) {   // NB <= 5 only
+    G[0] = 1.f - c;
+    P[0] = 1.f;
+    if constexpr (NB > 1) {
+        G[1] = 0.5f * s2;
+        P[1] = c;
+    }
+    if constexpr (NB > 2) {
+        G[2] = G[1] * c;
+        P[2] = fmaf(-1.5f, s2, 1.f);
+    }
+    if constexpr (NB > 3) {
+        G[3] = s2 * fmaf(-0.625f, s2, 0.5f);
+        P[3] = c * fmaf(-2.5f, s2, 1.f);
+    }
+    if constexpr (NB > 4) {
+        G[4] = G[2] * fmaf(-1.75f, s2, 1.f);
+        P[4] = fmaf(s2, fmaf(4.375f, s2, -5.f), 1.f);
+    }
+}
+
+// G_l (and P_l) of one pair.
+__device__ __forceinline__ void cap_terms(float c, float s2, float* G, float* P) {
+    if constexpr (NB <= 5) {
+        cap_closed(c, s2, G, P);
+    } else {
+        float dP[NB];
+        legendre(c, P, dP);
+        cap_integrals(c, s2, dP, G);
+    }
+}
+
 struct PairGeom {
     float dx, dy, dz, invD, invD2, s2, c;
     bool open;
@@ -172,9 +210,8 @@ constexpr int NACC = kMono ? SH::NA : K;
 // One pair's un-normalised log-visibility terms, added to acc.
 __device__ __forceinline__ void pair_forward(float px, float py, float pz, float4 sp, float* acc) {
     const PairGeom g = pair_geometry(px, py, pz, sp);
-    float P[NB], dP[NB], G[NB];
-    legendre(g.c, P, dP);
-    cap_integrals(g.c, g.s2, dP, G);
+    float P[NB], G[NB];
+    cap_terms(g.c, g.s2, G, P);
     const float sx = g.dx * g.invD, sy = g.dy * g.invD, sz = g.dz * g.invD;
     if constexpr (kMono) {
         SH::accumulate(G, sx, sy, sz, acc);
@@ -193,9 +230,8 @@ __device__ __forceinline__ void pair_backward(float px, float py, float pz, floa
                                               const float* dfp, float& gcx, float& gcy,
                                               float& gcz, float& gr) {
     const PairGeom g = pair_geometry(px, py, pz, sp);
-    float P[NB], dP[NB], G[NB];
-    legendre(g.c, P, dP);
-    cap_integrals(g.c, g.s2, dP, G);
+    float P[NB], G[NB];
+    cap_terms(g.c, g.s2, G, P);
     const float sx = g.dx * g.invD, sy = g.dy * g.invD, sz = g.dz * g.invD;
     float Y[K];
     SH::ybar(sx, sy, sz, Y);
@@ -235,9 +271,8 @@ __device__ __forceinline__ void pair_backward_grad(float px, float py, float pz,
                                                    const float* gq, float q0, float& gcx,
                                                    float& gcy, float& gcz, float& gr) {
     const PairGeom g = pair_geometry(px, py, pz, sp);
-    float P[NB], dP[NB], G[NB];
-    legendre(g.c, P, dP);
-    cap_integrals(g.c, g.s2, dP, G);
+    float P[NB], G[NB];
+    cap_terms(g.c, g.s2, G, P);
     const float sx = g.dx * g.invD, sy = g.dy * g.invD, sz = g.dz * g.invD;
     float gx[NB], gy[NB], gz[NB];
     SH::grad_eval(sx, sy, sz, gq, gx, gy, gz);
@@ -374,7 +409,7 @@ __device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_
 }
 
 #ifndef SHS_FWD_MINB
-#define SHS_FWD_MINB 1
+#define SHS_FWD_MINB 4
 #endif
 #ifndef SHS_BWD_MINB
 #define SHS_BWD_MINB 3
