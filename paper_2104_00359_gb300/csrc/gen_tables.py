@@ -29,6 +29,7 @@ checks that the committed header is current.
 from __future__ import annotations
 
 import math
+import re
 import os
 import sys
 from fractions import Fraction
@@ -482,6 +483,31 @@ def emit_monomial_route(n):
     return na, ng, ml, acc, m2f, gc, ge
 
 
+def packed_lines(lines):
+    """The float2 form of straight-line scalar code made of 'const float a =
+    b;', 'const float a = b * c;' and 'acc[i] = fmaf(b, c, acc[i]);' lines,
+    with the packed sm_100 float32x2 intrinsics."""
+    out = []
+    for ln in lines:
+        m = re.fullmatch(r"const float (\w+) = (\S+) \* (\S+);", ln)
+        if m:
+            out.append(f"const float2 {m[1]} = __fmul2_rn({m[2]}, {m[3]});")
+            continue
+        m = re.fullmatch(r"const float (\w+) = (\w+);", ln)
+        if m:
+            out.append(f"const float2 {m[1]} = {m[2]};")
+            continue
+        m = re.fullmatch(r"(acc\[\d+\]) = fmaf\((\S+), (\S+), (acc\[\d+\])\);", ln)
+        if m and m[1] == m[4]:
+            if m[3] == "1.0f":
+                out.append(f"{m[1]} = __fadd2_rn({m[2]}, {m[1]});")
+            else:
+                out.append(f"{m[1]} = __ffma2_rn({m[2]}, {m[3]}, {m[1]});")
+            continue
+        raise ValueError(f"cannot pack: {ln}")
+    return out
+
+
 def indent(lines, k=8):
     return "\n".join(" " * k + ln for ln in lines)
 
@@ -539,6 +565,12 @@ def generate():
         parts.append("    __device__ __forceinline__ static void accumulate(const float* G, float x, float y, float z, float* acc) {")
         parts.append("        (void)x; (void)y; (void)z;")
         parts.append(indent(ml + acc_l))
+        parts.append("    }")
+        parts.append("    // the same for two pairs at once, one per half of each float2")
+        parts.append("    __device__ __forceinline__ static void accumulate2(const float2* G, float2 x, float2 y, float2 z,")
+        parts.append("                                                       float2* acc) {")
+        parts.append("        (void)x; (void)y; (void)z;")
+        parts.append(indent(packed_lines(ml + acc_l)))
         parts.append("    }")
         parts.append("    __device__ __forceinline__ static void mono_to_f(const float* acc, float* f) {")
         parts.append(indent(m2f_l))

@@ -223,6 +223,42 @@ __device__ __forceinline__ void pair_forward(float px, float py, float pz, float
     }
 }
 
+// Two pairs at once in the packed float32x2 instructions of sm_100+, one
+// sphere per half of every float2 (same arithmetic as pair_forward).  The
+// spheres come interleaved: qa = (x0, x1, y0, y1), qb = (z0, z1, r0, r1).
+__device__ __forceinline__ void pair_forward2(float2 npx, float2 npy, float2 npz, float4 qa, float4 qb,
+                                              float2* acc) {
+    const float2 one = make_float2(1.f, 1.f), mone = make_float2(-1.f, -1.f);
+    const float2 dx = __fadd2_rn(make_float2(qa.x, qa.y), npx);
+    const float2 dy = __fadd2_rn(make_float2(qa.z, qa.w), npy);
+    const float2 dz = __fadd2_rn(make_float2(qb.x, qb.y), npz);
+    const float2 D2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    const float2 invD = make_float2(D2.x > 0.f ? rsqrtf(D2.x) : 0.f, D2.y > 0.f ? rsqrtf(D2.y) : 0.f);
+    const float2 r = make_float2(qb.z, qb.w);
+    const float2 r2i = __fmul2_rn(__fmul2_rn(r, r), __fmul2_rn(invD, invD));
+    const float2 s2 = make_float2(fminf(r2i.x, 1.f), fminf(r2i.y, 1.f));
+    const float2 om = __ffma2_rn(s2, mone, one);
+    const float2 c = __fmul2_rn(om, make_float2(rsqrtf(fmaxf(om.x, 1e-30f)), rsqrtf(fmaxf(om.y, 1e-30f))));
+    float2 G[NB];
+    G[0] = __ffma2_rn(c, mone, one);
+    if constexpr (NB > 1) G[1] = __fmul2_rn(make_float2(0.5f, 0.5f), s2);
+    if constexpr (NB > 2) G[2] = __fmul2_rn(G[1], c);
+    if constexpr (NB > 3) G[3] = __fmul2_rn(s2, __ffma2_rn(make_float2(-0.625f, -0.625f), s2, make_float2(0.5f, 0.5f)));
+    if constexpr (NB > 4) G[4] = __fmul2_rn(G[2], __ffma2_rn(make_float2(-1.75f, -1.75f), s2, one));
+    SH::accumulate2(G, __fmul2_rn(dx, invD), __fmul2_rn(dy, invD), __fmul2_rn(dz, invD), acc);
+}
+
+// Interleave the staged spheres in place for pair_forward2: entries 2q and
+// 2q+1 become (x, x', y, y') and (z, z', r, r'); an odd last sphere stays as
+// it is.  The caller synchronises the block before and after.
+__device__ __forceinline__ void interleave_sphere_pairs(float4* s_sph, int N) {
+    for (int q = threadIdx.x; q < (N >> 1); q += blockDim.x) {
+        const float4 a = s_sph[2 * q], b = s_sph[2 * q + 1];
+        s_sph[2 * q] = make_float4(a.x, b.x, a.y, b.y);
+        s_sph[2 * q + 1] = make_float4(a.z, b.z, a.w, b.w);
+    }
+}
+
 // Adjoint of one pair given dfp_i = dLoss/df_i * (-2 pi eps) * NORM_i.
 // Returns the gradient with respect to the sphere centre (the point gets the
 // negative) and the radius.
@@ -355,11 +391,24 @@ __device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_
                 pz = __ldg(a.points + 3 * p + 2);
 
     float acc[NACC];
-#pragma unroll
-    for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
     const int N = a.sc.n_spheres;
+    if constexpr (kMono) {
+        // spheres interleaved in pairs (interleave_sphere_pairs)
+        float2 acc2[NACC];
+#pragma unroll
+        for (int i = 0; i < NACC; ++i) acc2[i] = make_float2(0.f, 0.f);
+        const float2 npx = make_float2(-px, -px), npy = make_float2(-py, -py), npz = make_float2(-pz, -pz);
+#pragma unroll 1
+        for (int q = 0; q < (N >> 1); ++q) pair_forward2(npx, npy, npz, s_sph[2 * q], s_sph[2 * q + 1], acc2);
+#pragma unroll
+        for (int i = 0; i < NACC; ++i) acc[i] = acc2[i].x + acc2[i].y;
+        if (N & 1) pair_forward(px, py, pz, s_sph[N - 1], acc);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
 #pragma unroll 2
-    for (int j = 0; j < N; ++j) pair_forward(px, py, pz, s_sph[j], acc);
+        for (int j = 0; j < N; ++j) pair_forward(px, py, pz, s_sph[j], acc);
+    }
 
     float f[K];
     finish_f(a.sc, acc, f);
@@ -421,6 +470,10 @@ __global__ void __launch_bounds__(kBlock, NB <= 4 ? SHS_FWD_MINB : 1) forward_ke
     __shared__ __align__(16) float s_light[3 * KPAD];
     __shared__ __align__(8) uint64_t s_bar;
     if (!stage_scene(a.sc, s_sph, s_light, &s_bar)) return;
+    if constexpr (kMono) {
+        interleave_sphere_pairs(s_sph, a.sc.n_spheres);
+        __syncthreads();
+    }
     const int64_t p = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x;
     if (p >= a.n_points) return;
     forward_point<TAIL>(a, s_sph, s_light, p);
@@ -1219,6 +1272,10 @@ __global__ void __launch_bounds__(kBlock) forward_batch_kernel(const __grid_cons
             if (!stage_copy(b.r[r].sc, s_sph, s_light, &s_bar, parity)) return;
             parity ^= 1u;
             staged = r;
+            if constexpr (kMono) {
+                interleave_sphere_pairs(s_sph, b.r[r].sc.n_spheres);
+                __syncthreads();
+            }
         }
         const int64_t p = (tile - b.tile_begin[r]) * kBlock + threadIdx.x;
         if (p < b.r[r].n_points) forward_point(b.r[r], s_sph, s_light, p);
