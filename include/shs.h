@@ -80,11 +80,14 @@ typedef struct {
     int32_t fixed_k;       /* >= 0: use this k for every point; < 0: per-point k          */
     int32_t precision;     /* SHS_FP32 (SHS_TF32 / SHS_BF16: tensor-core contractions)    */
     int32_t deterministic; /* 1: scene gradients reduced in a fixed order                  */
-    int32_t reserved;      /* must be 0                                                   */
+    int32_t horizon_cull;  /* 0: every sphere blocks every point (Sec. 3.3.2 sums all      */
+                           /*    blockers); 1: per point, skip a sphere lying entirely     */
+                           /*    below the tangent plane, (c - x) . n_hat < -r (no         */
+                           /*    gradient through that selection)                          */
 } shs_config;
 
 /* Fills *cfg with n_bands=4, epsilon=3, exp_tau=1, exp_kmax=16, fixed_k=-1,
- * precision=SHS_FP32, deterministic=1. */
+ * precision=SHS_FP32, deterministic=1, horizon_cull=0. */
 shs_status shs_config_default(shs_config* cfg);
 
 /* Creates a resident scene of n_spheres occluder spheres (Sec. 3.3.1: the

@@ -29,7 +29,7 @@ class ShsConfig(ctypes.Structure):
         ("fixed_k", c_int32),
         ("precision", c_int32),
         ("deterministic", c_int32),
-        ("reserved", c_int32),
+        ("horizon_cull", c_int32),
     ]
 
 

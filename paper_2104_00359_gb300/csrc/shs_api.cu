@@ -152,7 +152,7 @@ shs_status check_config(const shs_config* c) {
     if ((c->precision == SHS_BF16 || c->precision == SHS_FP16) && c->n_bands != 8)
         return fail(SHS_ERR_UNSUPPORTED, "tensor-core precisions need n_bands = 8");
     if (c->deterministic != 0 && c->deterministic != 1) return fail(SHS_ERR_INVALID_ARG, "deterministic must be 0 or 1");
-    if (c->reserved != 0) return fail(SHS_ERR_INVALID_ARG, "reserved must be 0");
+    if (c->horizon_cull != 0 && c->horizon_cull != 1) return fail(SHS_ERR_INVALID_ARG, "horizon_cull must be 0 or 1");
     return SHS_OK;
 }
 
@@ -166,6 +166,7 @@ SceneView view_of(const shs_scene_s* s) {
     v.tau2 = s->cfg.exp_tau * s->cfg.exp_tau;
     v.kmax = s->cfg.exp_kmax;
     v.fixed_k = s->cfg.fixed_k;
+    v.horizon_cull = s->cfg.horizon_cull;
     v.status = s->status;
     return v;
 }
@@ -356,7 +357,7 @@ shs_status shs_config_default(shs_config* cfg) {
     cfg->fixed_k = -1;
     cfg->precision = SHS_FP32;
     cfg->deterministic = 1;
-    cfg->reserved = 0;
+    cfg->horizon_cull = 0;
     return SHS_OK;
 }
 

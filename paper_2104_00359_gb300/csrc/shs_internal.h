@@ -25,6 +25,7 @@ struct SceneView {
     float tau2;              // exp_tau^2
     int kmax;
     int fixed_k;
+    int horizon_cull;        // 1: drop spheres below the tangent plane, per point
     int* status;             // device status word
 };
 

@@ -17,6 +17,7 @@
 //   int_c^1 P_0 = 1 - c,   int_c^1 P_l = (1 - c^2) P_l'(c) / (l (l + 1))  (l >= 1),
 // both from Legendre's equation; d/dc int_c^1 P_l = -P_l(c).
 
+#include <type_traits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -184,7 +185,22 @@ struct PairGeom {
     bool open;
 };
 
-__device__ __forceinline__ PairGeom pair_geometry(float px, float py, float pz, float4 sp) {
+// Unit normal of the shading point, used by horizon culling.
+struct Normal {
+    float x = 0.f, y = 0.f, z = 0.f;
+};
+
+__device__ __forceinline__ Normal unit_normal(float nx, float ny, float nz) {
+    const float n2 = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+    const float il = n2 > 0.f ? rsqrtf(n2) : 0.f;
+    return Normal{nx * il, ny * il, nz * il};
+}
+
+// With CULL (the optional horizon-culling reading), a sphere entirely below
+// the tangent plane at x, (c - x) . n_hat < -r, becomes an empty cap: s2 = 0
+// and c = 1 make every G_l zero, and a closed cap carries no gradient.
+template <bool CULL = false>
+__device__ __forceinline__ PairGeom pair_geometry(float px, float py, float pz, float4 sp, Normal u = {}) {
     PairGeom g;
     g.dx = sp.x - px;
     g.dy = sp.y - py;
@@ -196,6 +212,13 @@ __device__ __forceinline__ PairGeom pair_geometry(float px, float py, float pz, 
     g.open = r2i < 1.f;
     g.s2 = fminf(r2i, 1.f);                   // point inside the sphere: hemisphere cap
     g.c = fast_sqrt(1.f - g.s2);
+    if constexpr (CULL) {
+        if (fmaf(g.dx, u.x, fmaf(g.dy, u.y, g.dz * u.z)) < -sp.w) {
+            g.s2 = 0.f;
+            g.c = 1.f;
+            g.open = false;
+        }
+    }
     return g;
 }
 
@@ -208,8 +231,9 @@ constexpr bool kMono = NB <= 5;
 constexpr int NACC = kMono ? SH::NA : K;
 
 // One pair's un-normalised log-visibility terms, added to acc.
-__device__ __forceinline__ void pair_forward(float px, float py, float pz, float4 sp, float* acc) {
-    const PairGeom g = pair_geometry(px, py, pz, sp);
+template <bool CULL = false>
+__device__ __forceinline__ void pair_forward(float px, float py, float pz, float4 sp, float* acc, Normal u = {}) {
+    const PairGeom g = pair_geometry<CULL>(px, py, pz, sp, u);
     float P[NB], G[NB];
     cap_terms(g.c, g.s2, G, P);
     const float sx = g.dx * g.invD, sy = g.dy * g.invD, sz = g.dz * g.invD;
@@ -226,8 +250,9 @@ __device__ __forceinline__ void pair_forward(float px, float py, float pz, float
 // Two pairs at once in the packed float32x2 instructions of sm_100+, one
 // sphere per half of every float2 (same arithmetic as pair_forward).  The
 // spheres come interleaved: qa = (x0, x1, y0, y1), qb = (z0, z1, r0, r1).
+template <bool CULL = false>
 __device__ __forceinline__ void pair_forward2(float2 npx, float2 npy, float2 npz, float4 qa, float4 qb,
-                                              float2* acc) {
+                                              float2* acc, Normal u = {}) {
     const float2 one = make_float2(1.f, 1.f), mone = make_float2(-1.f, -1.f);
     const float2 dx = __fadd2_rn(make_float2(qa.x, qa.y), npx);
     const float2 dy = __fadd2_rn(make_float2(qa.z, qa.w), npy);
@@ -236,9 +261,21 @@ __device__ __forceinline__ void pair_forward2(float2 npx, float2 npy, float2 npz
     const float2 invD = make_float2(D2.x > 0.f ? rsqrtf(D2.x) : 0.f, D2.y > 0.f ? rsqrtf(D2.y) : 0.f);
     const float2 r = make_float2(qb.z, qb.w);
     const float2 r2i = __fmul2_rn(__fmul2_rn(r, r), __fmul2_rn(invD, invD));
-    const float2 s2 = make_float2(fminf(r2i.x, 1.f), fminf(r2i.y, 1.f));
+    float2 s2 = make_float2(fminf(r2i.x, 1.f), fminf(r2i.y, 1.f));
     const float2 om = __ffma2_rn(s2, mone, one);
-    const float2 c = __fmul2_rn(om, make_float2(rsqrtf(fmaxf(om.x, 1e-30f)), rsqrtf(fmaxf(om.y, 1e-30f))));
+    float2 c = __fmul2_rn(om, make_float2(rsqrtf(fmaxf(om.x, 1e-30f)), rsqrtf(fmaxf(om.y, 1e-30f))));
+    if constexpr (CULL) {   // as in pair_geometry
+        const float2 h = __ffma2_rn(dx, make_float2(u.x, u.x),
+                                    __ffma2_rn(dy, make_float2(u.y, u.y), __fmul2_rn(dz, make_float2(u.z, u.z))));
+        if (h.x < -qb.z) {
+            s2.x = 0.f;
+            c.x = 1.f;
+        }
+        if (h.y < -qb.w) {
+            s2.y = 0.f;
+            c.y = 1.f;
+        }
+    }
     float2 G[NB];
     G[0] = __ffma2_rn(c, mone, one);
     if constexpr (NB > 1) G[1] = __fmul2_rn(make_float2(0.5f, 0.5f), s2);
@@ -262,10 +299,11 @@ __device__ __forceinline__ void interleave_sphere_pairs(float4* s_sph, int N) {
 // Adjoint of one pair given dfp_i = dLoss/df_i * (-2 pi eps) * NORM_i.
 // Returns the gradient with respect to the sphere centre (the point gets the
 // negative) and the radius.
+template <bool CULL = false>
 __device__ __forceinline__ void pair_backward(float px, float py, float pz, float4 sp,
                                               const float* dfp, float& gcx, float& gcy,
-                                              float& gcz, float& gr) {
-    const PairGeom g = pair_geometry(px, py, pz, sp);
+                                              float& gcz, float& gr, Normal u = {}) {
+    const PairGeom g = pair_geometry<CULL>(px, py, pz, sp, u);
     float P[NB], G[NB];
     cap_terms(g.c, g.s2, G, P);
     const float sx = g.dx * g.invD, sy = g.dy * g.invD, sz = g.dz * g.invD;
@@ -303,10 +341,11 @@ __device__ __forceinline__ void pair_backward(float px, float py, float pz, floa
 //   dPsi/dc = -sum_l P_l Phi_l = -(s_hat . b) - Phi_0
 //   dPsi/dd = (a - (s_hat . a) s_hat) / D + 2 (dPsi/dD^2) d
 // so only the gradient polynomials (degree l-1) are evaluated per pair.
+template <bool CULL = false>
 __device__ __forceinline__ void pair_backward_grad(float px, float py, float pz, float4 sp,
                                                    const float* gq, float q0, float& gcx,
-                                                   float& gcy, float& gcz, float& gr) {
-    const PairGeom g = pair_geometry(px, py, pz, sp);
+                                                   float& gcy, float& gcz, float& gr, Normal u = {}) {
+    const PairGeom g = pair_geometry<CULL>(px, py, pz, sp, u);
     float P[NB], G[NB];
     cap_terms(g.c, g.s2, G, P);
     const float sx = g.dx * g.invD, sy = g.dy * g.invD, sz = g.dz * g.invD;
@@ -398,16 +437,34 @@ __device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_
 #pragma unroll
         for (int i = 0; i < NACC; ++i) acc2[i] = make_float2(0.f, 0.f);
         const float2 npx = make_float2(-px, -px), npy = make_float2(-py, -py), npz = make_float2(-pz, -pz);
+        if (a.sc.horizon_cull) {
+            const Normal u = unit_normal(__ldg(a.normals + 3 * p), __ldg(a.normals + 3 * p + 1),
+                                         __ldg(a.normals + 3 * p + 2));
 #pragma unroll 1
-        for (int q = 0; q < (N >> 1); ++q) pair_forward2(npx, npy, npz, s_sph[2 * q], s_sph[2 * q + 1], acc2);
+            for (int q = 0; q < (N >> 1); ++q)
+                pair_forward2<true>(npx, npy, npz, s_sph[2 * q], s_sph[2 * q + 1], acc2, u);
 #pragma unroll
-        for (int i = 0; i < NACC; ++i) acc[i] = acc2[i].x + acc2[i].y;
-        if (N & 1) pair_forward(px, py, pz, s_sph[N - 1], acc);
+            for (int i = 0; i < NACC; ++i) acc[i] = acc2[i].x + acc2[i].y;
+            if (N & 1) pair_forward<true>(px, py, pz, s_sph[N - 1], acc, u);
+        } else {
+#pragma unroll 1
+            for (int q = 0; q < (N >> 1); ++q) pair_forward2(npx, npy, npz, s_sph[2 * q], s_sph[2 * q + 1], acc2);
+#pragma unroll
+            for (int i = 0; i < NACC; ++i) acc[i] = acc2[i].x + acc2[i].y;
+            if (N & 1) pair_forward(px, py, pz, s_sph[N - 1], acc);
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
+        if (a.sc.horizon_cull) {
+            const Normal u = unit_normal(__ldg(a.normals + 3 * p), __ldg(a.normals + 3 * p + 1),
+                                         __ldg(a.normals + 3 * p + 2));
 #pragma unroll 2
-        for (int j = 0; j < N; ++j) pair_forward(px, py, pz, s_sph[j], acc);
+            for (int j = 0; j < N; ++j) pair_forward<true>(px, py, pz, s_sph[j], acc, u);
+        } else {
+#pragma unroll 2
+            for (int j = 0; j < N; ++j) pair_forward(px, py, pz, s_sph[j], acc);
+        }
     }
 
     float f[K];
@@ -820,7 +877,8 @@ __device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v
 // Adjoint of one 128-point tile of one request: per-point outputs are written,
 // the scene-level sums are added to the block's shared accumulators
 // (s_dl: d_light and loss per warp, s_acc: per warp and sphere).
-template <bool PAIRS = true>
+// CULLM: horizon culling off (0), on (1), or read from the scene per call (2).
+template <bool PAIRS = true, int CULLM = 2>
 __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_sph, const float* s_light,
                                               float* s_acc, float (*s_dl)[3 * K + 1], int64_t tile,
                                               int lane, int warp) {
@@ -843,8 +901,15 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_
         float acc[NACC];
 #pragma unroll
         for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
+        if (CULLM == 1 || (CULLM == 2 && a.sc.horizon_cull)) {
+            const Normal u = unit_normal(load_or(a.normals, 3 * q, live), load_or(a.normals, 3 * q + 1, live),
+                                         load_or(a.normals, 3 * q + 2, live));
 #pragma unroll 2
-        for (int j = 0; j < N; ++j) pair_forward(px, py, pz, s_sph[j], acc);
+            for (int j = 0; j < N; ++j) pair_forward<true>(px, py, pz, s_sph[j], acc, u);
+        } else {
+#pragma unroll 2
+            for (int j = 0; j < N; ++j) pair_forward(px, py, pz, s_sph[j], acc);
+        }
         finish_f(a.sc, acc, f);
         k = -1;
     }
@@ -982,47 +1047,59 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_
         float gq[kMono ? SH::NG : 1];
         if constexpr (kMono) SH::grad_coeffs(dfp, gq);
         const float q0 = dfp[0];
-        auto pair = [&](float4 sp, float& gcx, float& gcy, float& gcz, float& gr) {
-            if constexpr (kMono) pair_backward_grad(px, py, pz, sp, gq, q0, gcx, gcy, gcz, gr);
-            else pair_backward(px, py, pz, sp, dfp, gcx, gcy, gcz, gr);
-        };
+        const Normal u{ux, uy, uz};
         float gpx = 0.f, gpy = 0.f, gpz = 0.f;
         float* my_acc = s_acc + warp * 4 * N;
-        if (want_sph && N >= 32) {
-            // Skewed order: at step t lane l handles sphere (l + t) mod N, so the
-            // 32 lanes update 32 distinct slots of the warp's accumulator row
-            // with plain shared-memory read-modify-writes (no cross-lane sums).
-            float4* row = reinterpret_cast<float4*>(my_acc);
-            int j = lane;
+        // the pair loops, instantiated with and without horizon culling so the
+        // selection costs nothing per pair when it is off
+        auto loops = [&](auto cull_tag) {
+            constexpr bool CULL = decltype(cull_tag)::value;
+            auto pair = [&](float4 sp, float& gcx, float& gcy, float& gcz, float& gr) {
+                if constexpr (kMono) pair_backward_grad<CULL>(px, py, pz, sp, gq, q0, gcx, gcy, gcz, gr, u);
+                else pair_backward<CULL>(px, py, pz, sp, dfp, gcx, gcy, gcz, gr, u);
+            };
+            if (want_sph && N >= 32) {
+                // Skewed order: at step t lane l handles sphere (l + t) mod N, so the
+                // 32 lanes update 32 distinct slots of the warp's accumulator row
+                // with plain shared-memory read-modify-writes (no cross-lane sums).
+                float4* row = reinterpret_cast<float4*>(my_acc);
+                int j = lane;
 #pragma unroll 1
-            for (int t = 0; t < N; ++t) {
-                float gcx, gcy, gcz, gr;
-                pair(s_sph[j], gcx, gcy, gcz, gr);
-                gpx -= gcx;
-                gpy -= gcy;
-                gpz -= gcz;
-                float4 acc = row[j];
-                acc.x += gcx;
-                acc.y += gcy;
-                acc.z += gcz;
-                acc.w += gr;
-                row[j] = acc;
-                __syncwarp();
-                j = (j + 1 == N) ? 0 : j + 1;
-            }
-        } else {
+                for (int t = 0; t < N; ++t) {
+                    float gcx, gcy, gcz, gr;
+                    pair(s_sph[j], gcx, gcy, gcz, gr);
+                    gpx -= gcx;
+                    gpy -= gcy;
+                    gpz -= gcz;
+                    float4 acc = row[j];
+                    acc.x += gcx;
+                    acc.y += gcy;
+                    acc.z += gcz;
+                    acc.w += gr;
+                    row[j] = acc;
+                    __syncwarp();
+                    j = (j + 1 == N) ? 0 : j + 1;
+                }
+            } else {
 #pragma unroll 1
-            for (int j = 0; j < N; ++j) {
-                float gcx, gcy, gcz, gr;
-                pair(s_sph[j], gcx, gcy, gcz, gr);
-                gpx -= gcx;
-                gpy -= gcy;
-                gpz -= gcz;
-                if (want_sph) {
-                    const float v = warp_sum4(gcx, gcy, gcz, gr, lane);
-                    if ((lane & 7) == 0) my_acc[4 * j + (lane >> 3)] += v;
+                for (int j = 0; j < N; ++j) {
+                    float gcx, gcy, gcz, gr;
+                    pair(s_sph[j], gcx, gcy, gcz, gr);
+                    gpx -= gcx;
+                    gpy -= gcy;
+                    gpz -= gcz;
+                    if (want_sph) {
+                        const float v = warp_sum4(gcx, gcy, gcz, gr, lane);
+                        if ((lane & 7) == 0) my_acc[4 * j + (lane >> 3)] += v;
+                    }
                 }
             }
+        };
+        if constexpr (CULLM == 2) {
+            if (a.sc.horizon_cull) loops(std::true_type{});
+            else loops(std::false_type{});
+        } else {
+            loops(std::integral_constant<bool, CULLM == 1>{});
         }
         if (live && a.d_points) {
             a.d_points[3 * q] = gpx;
@@ -1061,7 +1138,7 @@ __device__ void finish_scene_sums(const BwdArgs& a, int E) {
 //   [3K+1, 3K+1+4N)  per sphere (d cx, d cy, d cz, d r)
 // Up to 4 bands: four resident blocks per SM (<= 128 registers per thread) for
 // the pair loop; above that the tail state needs the registers.
-template <bool PAIRS>
+template <bool PAIRS, int CULLM>
 __global__ void __launch_bounds__(kBlock, NB <= 4 ? SHS_BWD_MINB : 1) backward_kernel_t(BwdArgs a) {
     extern __shared__ __align__(16) float4 dyn[];
     __shared__ __align__(16) float s_light[3 * KPAD];
@@ -1080,7 +1157,7 @@ __global__ void __launch_bounds__(kBlock, NB <= 4 ? SHS_BWD_MINB : 1) backward_k
 
     const int64_t ntiles = (a.n_points + kBlock - 1) / kBlock;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-        backward_tile<PAIRS>(a, s_sph, s_light, s_acc, s_dl, tile, lane, warp);
+        backward_tile<PAIRS, CULLM>(a, s_sph, s_light, s_acc, s_dl, tile, lane, warp);
 
     // ---- block reduction, then one scene-level reduction
     __syncthreads();
@@ -1136,6 +1213,7 @@ __global__ void __launch_bounds__(kBlock) bwd_pairs_t_kernel(BwdArgs a) {
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ __align__(16) float s_gq[kPtTile][NGP];
     __shared__ __align__(16) float4 s_pt[kPtTile];        // x, y, z, Phi_0
+    __shared__ __align__(16) float4 s_nrm[kPtTile];       // unit normal (horizon culling)
     __shared__ float s_dpt[kPtTile][3];
     __shared__ bool s_last;
     const int N = a.sc.n_spheres;
@@ -1145,6 +1223,7 @@ __global__ void __launch_bounds__(kBlock) bwd_pairs_t_kernel(BwdArgs a) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int j = tid; j < N; j += kBlock) s_sacc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
     const bool want_pts = a.d_points != nullptr;
+    const bool cull = a.sc.horizon_cull != 0;
     const int64_t P = a.n_points;
     const int64_t nunits = (P + kPtTile - 1) / kPtTile;
     for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
@@ -1167,6 +1246,11 @@ __global__ void __launch_bounds__(kBlock) bwd_pairs_t_kernel(BwdArgs a) {
             s_pt[tid] = live ? make_float4(__ldg(a.points + 3 * p), __ldg(a.points + 3 * p + 1),
                                            __ldg(a.points + 3 * p + 2), dfp[0])
                              : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a.sc.horizon_cull) {
+                const Normal un = unit_normal(load_or(a.normals, 3 * p, live), load_or(a.normals, 3 * p + 1, live),
+                                              load_or(a.normals, 3 * p + 2, live));
+                s_nrm[tid] = make_float4(un.x, un.y, un.z, 0.f);
+            }
             s_dpt[tid][0] = s_dpt[tid][1] = s_dpt[tid][2] = 0.f;
         }
         __syncthreads();
@@ -1179,10 +1263,19 @@ __global__ void __launch_bounds__(kBlock) bwd_pairs_t_kernel(BwdArgs a) {
             for (int t = 0; t < kPtTile; ++t) {
                 const float4 pt = s_pt[t];
                 float gcx, gcy, gcz, gr;
-                if constexpr (kMonoPairs)
-                    pair_backward_grad(pt.x, pt.y, pt.z, sp, &s_gq[t][0], pt.w, gcx, gcy, gcz, gr);
-                else
-                    pair_backward(pt.x, pt.y, pt.z, sp, &s_gq[t][0], gcx, gcy, gcz, gr);
+                if (cull) {
+                    const float4 un = s_nrm[t];
+                    const Normal u{un.x, un.y, un.z};
+                    if constexpr (kMonoPairs)
+                        pair_backward_grad<true>(pt.x, pt.y, pt.z, sp, &s_gq[t][0], pt.w, gcx, gcy, gcz, gr, u);
+                    else
+                        pair_backward<true>(pt.x, pt.y, pt.z, sp, &s_gq[t][0], gcx, gcy, gcz, gr, u);
+                } else {
+                    if constexpr (kMonoPairs)
+                        pair_backward_grad(pt.x, pt.y, pt.z, sp, &s_gq[t][0], pt.w, gcx, gcy, gcz, gr);
+                    else
+                        pair_backward(pt.x, pt.y, pt.z, sp, &s_gq[t][0], gcx, gcy, gcz, gr);
+                }
                 if (!has) gcx = gcy = gcz = gr = 0.f;
                 acc.x += gcx;
                 acc.y += gcy;
@@ -1343,21 +1436,36 @@ __global__ void __launch_bounds__(kBlock, NB <= 4 ? 4 : 1)
 // Deterministic finish: out[e] = sum over blocks b (in order) of partials[b][e].
 // One warp per 32 consecutive elements and per slice of blocks; the slices are
 // then added in fixed order.
-__global__ void __launch_bounds__(256) reduce_partials_kernel(BwdArgs a, int nblk) {
-    __shared__ float s[8][33];
+// Fixed-order sum of the blocks' partial rows.  One block per 32 entries;
+// its 32 warps stride over the rows with four independent loads in flight
+// each (the sum is latency-bound: ~450 rows of 32 floats per block).
+constexpr int kReduceWarps = 32;
+
+__global__ void __launch_bounds__(32 * kReduceWarps) reduce_partials_kernel(BwdArgs a, int nblk) {
+    __shared__ float s[kReduceWarps][33];
     const int N = a.sc.n_spheres;
     const int E = 3 * K + 1 + 4 * N;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int e = blockIdx.x * 32 + lane;
-    float v = 0.f;
-    if (e < E)
-        for (int b = warp; b < nblk; b += 8) v += __ldcg(a.partials + static_cast<size_t>(b) * a.partial_stride + e);
-    s[warp][lane] = v;
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+    if (e < E) {
+        const float* col = a.partials + e;
+        const size_t st = static_cast<size_t>(a.partial_stride);
+        int b = warp;
+        for (; b + 3 * kReduceWarps < nblk; b += 4 * kReduceWarps) {
+            v0 += __ldcg(col + b * st);
+            v1 += __ldcg(col + (b + kReduceWarps) * st);
+            v2 += __ldcg(col + (b + 2 * kReduceWarps) * st);
+            v3 += __ldcg(col + (b + 3 * kReduceWarps) * st);
+        }
+        for (; b < nblk; b += kReduceWarps) v0 += __ldcg(col + b * st);
+    }
+    s[warp][lane] = (v0 + v1) + (v2 + v3);
     __syncthreads();
     if (warp != 0 || e >= E) return;
     float t = 0.f;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) t += s[w][lane];
+    for (int w = 0; w < kReduceWarps; ++w) t += s[w][lane];
     if (e < 3 * K) {
         if (a.d_light) a.d_light[e] = t;
     } else if (e == 3 * K) {
@@ -1380,10 +1488,10 @@ size_t backward_dyn_smem(int n_spheres) {
 
 template <>
 int backward_blocks_per_sm<NB>(int n_spheres) {
-    cudaFuncSetAttribute(backward_kernel_t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(backward_kernel_t<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(backward_dyn_smem(kMaxSpheres)));
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, backward_kernel_t<true>, kBlock,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, backward_kernel_t<true, 0>, kBlock,
                                                       backward_dyn_smem(n_spheres)) != cudaSuccess || nb < 1)
         nb = 1;
     return nb;
@@ -1494,18 +1602,20 @@ cudaError_t launch_backward<NB>(const BwdArgs& a, cudaStream_t s) {
     if (a.n_points <= 0) return cudaSuccess;
     const size_t smem = backward_dyn_smem(a.sc.n_spheres);
     static const cudaError_t attr = [] {
-        cudaError_t e = cudaFuncSetAttribute(backward_kernel_t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(backward_dyn_smem(kMaxSpheres)));
+        const int bytes = static_cast<int>(backward_dyn_smem(kMaxSpheres));
+        cudaError_t e = cudaFuncSetAttribute(backward_kernel_t<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             bytes);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(backward_kernel_t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(backward_dyn_smem(kMaxSpheres)));
+            e = cudaFuncSetAttribute(backward_kernel_t<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(backward_kernel_t<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         return e;
     }();
     cudaError_t err = attr;
     if (err != cudaSuccess) return err;
     if (a.dfp_ws) {
         // split backward: tail pass (per point), then the pair pass (per sphere lane)
-        backward_kernel_t<false><<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
+        backward_kernel_t<false, 2><<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
         count_launch();
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
@@ -1520,13 +1630,16 @@ cudaError_t launch_backward<NB>(const BwdArgs& a, cudaStream_t s) {
             err = cudaGetLastError();
         }
     } else {
-        backward_kernel_t<true><<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
+        if (a.sc.horizon_cull)
+            backward_kernel_t<true, 1><<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
+        else
+            backward_kernel_t<true, 0><<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
         count_launch();
         err = cudaGetLastError();
     }
     if (err != cudaSuccess || a.counter != nullptr) return err;
     const int E = 3 * K + 1 + 4 * a.sc.n_spheres;
-    reduce_partials_kernel<<<(E + 31) / 32, 256, 0, s>>>(a, a.grid);
+    reduce_partials_kernel<<<(E + 31) / 32, 32 * kReduceWarps, 0, s>>>(a, a.grid);
     count_launch();
     return cudaGetLastError();
 }

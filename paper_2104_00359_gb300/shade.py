@@ -29,10 +29,12 @@ class Config:
     fixed_k: int = -1
     precision: int = _lib.SHS_FP32
     deterministic: bool = True
+    horizon_cull: bool = False
 
     def to_c(self):
         return ShsConfig(int(self.n_bands), float(self.epsilon), float(self.exp_tau), int(self.exp_kmax),
-                         int(self.fixed_k), int(self.precision), int(bool(self.deterministic)), 0)
+                         int(self.fixed_k), int(self.precision), int(bool(self.deterministic)),
+                         int(bool(self.horizon_cull)))
 
 
 def _stream():

@@ -54,7 +54,8 @@ def gpu_run(sc, cfg, dB=None, want=None, saved=True, l2_target=None):
     scene = Scene(T["centers"] if N else None, T["radii"] if N else None, T["light"],
                   Config(n_bands=cfg.n_bands, epsilon=cfg.epsilon, exp_tau=cfg.exp_tau,
                          exp_kmax=cfg.exp_kmax, fixed_k=cfg.fixed_k,
-                         deterministic=getattr(cfg, "deterministic", True)))
+                         deterministic=getattr(cfg, "deterministic", True),
+                         horizon_cull=getattr(cfg, "horizon_cull", False)))
     P = sc["points"].shape[0]
     K = cfg.n_bands ** 2
     sv = scene.new_saved(P, dev)
