@@ -585,6 +585,94 @@ def bench_heightfield(args, world, rank, local):
                 precisions=out)
 
 
+def bench_envmap(args, world, rank, local):
+    """Eq. 9 projection of an equirectangular HDR map (default 4096 x 8192,
+    402 MB, larger than L2) onto SH lighting, n = 8 and n = 4.  The kernel
+    streams the map once: bytes/s against the measured HBM copy bandwidth."""
+    import ctypes
+    import torch
+    from paper_2104_00359_gb300 import _lib, synthetic
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = _lib.load()
+    H, W = args.env_res, 2 * args.env_res
+    env_np = synthetic.environment_map(seed=5 + rank, height=H, width=W)
+    env = torch.from_numpy(env_np).to(dev)
+    nbytes = env.numel() * 4
+    sptr = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    stream = torch.cuda.current_stream()
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs")
+    out = {}
+    for n in (8, 4):
+        light = torch.empty((3, n * n), device=dev)
+        need = int(lib.shs_envmap_workspace_bytes(H, W, n))
+        ws = torch.empty(need // 4, device=dev)
+
+        def step():
+            _lib.check(lib.shs_project_envmap(_lib.ptr(env), H, W, n, _lib.ptr(light), _lib.ptr(ws), need, sptr),
+                       "shs_project_envmap")
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        K = max(3, min(args.steps, 200))
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        launches0 = lib.shs_launch_count()
+        with ClockSampler(local) as clk:
+            for e0, e1 in evs:
+                e0.record(stream)
+                step()
+                e1.record(stream)
+            torch.cuda.synchronize()
+        ms = statistics.fmean(a.elapsed_time(b) for a, b in evs)
+        out[f"n{n}"] = {"ms": ms, "bytes_per_s": nbytes / (ms * 1e-3), "gpu_launches": lib.shs_launch_count() - launches0,
+                        "clocks": clk.summary()}
+    # end to end: pinned host map -> device -> light back to the host
+    host = torch.from_numpy(env_np).pin_memory()
+    light_h = torch.empty((3, 64)).pin_memory()
+    light = torch.empty((3, 64), device=dev)
+    need = int(lib.shs_envmap_workspace_bytes(H, W, 8))
+    ws = torch.empty(need // 4, device=dev)
+    KE = 10
+    for i in range(KE + 2):
+        if i == 2:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        env.copy_(host, non_blocking=True)
+        _lib.check(lib.shs_project_envmap(_lib.ptr(env), H, W, 8, _lib.ptr(light), _lib.ptr(ws), need, sptr),
+                   "shs_project_envmap")
+        light_h.copy_(light, non_blocking=True)
+        stream.synchronize()
+    e2e_s = (time.perf_counter() - t0) / KE
+    main = out["n8"]
+    achieved = main["bytes_per_s"] / 1e9
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        from oracle import shs_oracle as O
+        rows = max(1, min(H, int(4e6 // W)))
+        t = time.perf_counter()
+        O.project_envmap(8, env_np[:rows])
+        dt = time.perf_counter() - t
+        cpu = {"value": rows * W * 12 / dt, "unit": "bytes/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {rows} rows of the {H}x{W} map, n_bands=8, float64 numpy, 1 thread, {dt:.1f} s"}
+    return dict(
+        metric="equirectangular HDR map -> SH lighting (Eq. 9), map bytes/s", value=main["bytes_per_s"],
+        unit="bytes/s", n_gpus=world, steps=K, warmup=args.warmup, ms_per_step=main["ms"], higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="f32", data="synthetic", impl="ours",
+        config={"workload": f"environment map {H}x{W}x3 float32 ({nbytes / 1e6:.0f} MB, larger than L2), n_bands=8",
+                "height": H, "width": W},
+        per_band_count=out,
+        roofline={"bound": "hbm", "kernel": "envmap_rows_kernel<8> + envmap_reduce_kernel",
+                  "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                  "frac": (achieved / hbm) if hbm else None, "traffic": None,
+                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth, read + write bytes)",
+                  "bytes_per_launch": nbytes},
+        e2e={"value": nbytes / e2e_s, "unit": "bytes/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 3 * 64 * 4,
+             "ms_per_step": e2e_s * 1e3},
+        gpu_launches=main["gpu_launches"], clocks=main["clocks"], cpu_baseline=cpu)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -593,11 +681,12 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--atomic", action="store_true", help="unordered (atomic) scene-gradient reduction")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--workload", choices=("capsule", "serving", "heightfield"), default="capsule",
+    ap.add_argument("--workload", choices=("capsule", "serving", "heightfield", "envmap"), default="capsule",
                     help="capsule: the 512x512 G-buffer step (default); serving: the mixed request stream")
     ap.add_argument("--hf-res", type=int, default=1024, help="height-field grid side (heightfield workload)")
     ap.add_argument("--precisions", default="fp32,bf16_split_tc,fp16_split_tc",
                     help="heightfield workload: comma list of fp32, bf16_split_tc, fp16_split_tc")
+    ap.add_argument("--env-res", type=int, default=4096, help="environment map rows (width = 2 x rows)")
     ap.add_argument("--serve-jobs", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=2000)
     args = ap.parse_args()
@@ -609,6 +698,8 @@ def main():
         res = bench_serving(args, world, rank, local)
     elif args.workload == "heightfield":
         res = bench_heightfield(args, world, rank, local)
+    elif args.workload == "envmap":
+        res = bench_envmap(args, world, rank, local)
     else:
         res = bench_ours(args, world, rank, local, dist)
     if rank == 0 and res is not None:

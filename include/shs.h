@@ -227,6 +227,26 @@ shs_status shs_batch_destroy(shs_batch_t batch);
  * Returns SHS_ERR_INVALID_ARG for more than 32 requests. */
 shs_status shs_shade_batch(shs_batch_t batch, const shs_request* reqs, int32_t n_reqs, void* stream);
 
+/* Lighting from an environment map (Eq. 9: L_c,i = int L_c(w) y_i(w) dw),
+ * for building a scene's `light` from an HDR map.
+ *   env: [height][width][3] float32 device array, an equirectangular radiance
+ *     map: row r covers polar angles [r, r+1] pi / height measured from +z,
+ *     column c covers azimuths [c, c+1] 2 pi / width from +x toward +y
+ *     (direction (sin t cos p, sin t sin p, cos t)).
+ *   light: [3][K] float32 device output, K = n_bands^2, overwritten.
+ *   workspace: 16-byte aligned device scratch of at least
+ *     shs_envmap_workspace_bytes(height, width, n_bands) bytes (0 for invalid
+ *     sizes), owned by the caller; a call uses it until it completes on
+ *     `stream`, so calls that may overlap need separate workspaces.
+ * Each pixel contributes its value times y_i at the pixel centre times its
+ * exact solid angle (cos t_r - cos t_{r+1}) 2 pi / width.  The sum runs in a
+ * fixed order (same result on every run).  1 <= height, width <= 65536 and
+ * 1 <= n_bands <= 8, else SHS_ERR_INVALID_ARG, as for NULL pointers or a
+ * short workspace.  Asynchronous on `stream`. */
+size_t shs_envmap_workspace_bytes(int32_t height, int32_t width, int32_t n_bands);
+shs_status shs_project_envmap(const float* env, int32_t height, int32_t width, int32_t n_bands, float* light,
+                              void* workspace, size_t workspace_bytes, void* stream);
+
 /* Diagnostic: one CTA computes D = A B^T with M = 128 rows, n columns and
  * inner size k on the tensor cores (tcgen05, BF16 operands, FP32 accumulation
  * in tensor memory); split != 0 uses split precision (each operand as the sum

@@ -16,6 +16,7 @@ order so it can be read against the paper:
   projected along z (ZH) and rotated toward the sphere centre
 * log-visibility = sum over spheres, then SH exponential      (Sec. 3.3.2, Eq. 12)
 * shading B = a * (L . (V * H))                               (Sec. 3.2, Eq. 8)
+* lighting projected from an equirectangular map              (Sec. 3.3, Eq. 9)
 * reverse-mode adjoint of all of the above (for d/d lighting, albedo, sphere
   centres and radii, point positions and normals; Sec. 3.5)
 
@@ -346,6 +347,44 @@ def shade_forward(cfg, points, normals, albedo, centers, radii, light, k=None):
     W = sh_product(C, V, H)
     B = alb * (W @ L.T)
     return dict(radiance=B, f=f, V=V, H=H, W=W, k=ex["k"], _exp=ex)
+
+
+# ----------------------------------------------------------------------------
+# Lighting from an environment map (Eq. 9)
+# ----------------------------------------------------------------------------
+
+def envmap_directions(height, width):
+    """Pixel-centre directions and exact pixel solid angles of an
+    equirectangular map: row r spans polar angles [r, r+1] pi / H from +z,
+    column c spans azimuths [c, c+1] 2 pi / W; the pixel's solid angle is
+    (cos theta_r - cos theta_{r+1}) 2 pi / W.  Returns dirs [H, W, 3] and
+    d_omega [H]."""
+    H, W = int(height), int(width)
+    theta = (np.arange(H) + 0.5) * math.pi / H
+    phi = (np.arange(W) + 0.5) * 2.0 * math.pi / W
+    edges = np.cos(np.arange(H + 1) * math.pi / H)
+    d_omega = (edges[:-1] - edges[1:]) * 2.0 * math.pi / W
+    st, ct = np.sin(theta)[:, None], np.cos(theta)[:, None]
+    dirs = np.stack([st * np.cos(phi)[None, :], st * np.sin(phi)[None, :],
+                     np.broadcast_to(ct, (H, W))], axis=-1)
+    return dirs, d_omega
+
+
+def project_envmap(n_bands, env):
+    """L_c,i = int L_c(omega) y_i(omega) d omega (Eq. 9) for an
+    equirectangular radiance map env [H, W, 3]: the sum over pixels of the
+    pixel value times y_i at the pixel centre times the pixel's solid angle.
+    Returns [3, K].  Processed a band of rows at a time."""
+    env = np.asarray(env, np.float64)
+    H, W = env.shape[:2]
+    dirs, d_omega = envmap_directions(H, W)
+    out = np.zeros((3, n_bands * n_bands))
+    step = max(1, 65536 // max(W, 1))
+    for r0 in range(0, H, step):
+        Y = real_sh(n_bands, dirs[r0:r0 + step])                 # [h, W, K]
+        w = env[r0:r0 + step] * d_omega[r0:r0 + step, None, None]  # [h, W, 3]
+        out += np.einsum("hwc,hwk->ck", w, Y)
+    return out
 
 
 # ----------------------------------------------------------------------------

@@ -1,0 +1,294 @@
+// Lighting from an environment map (Eq. 9): L_c,lm = int L_c(w) y_lm(w) dw for
+// an equirectangular radiance map, evaluated as the sum over pixels of the
+// pixel value times y_lm at the pixel centre times the pixel's exact solid
+// angle.
+//
+// The real SH factor as y_lm(theta, phi) = N'_lm P_l^|m|(cos theta) T_m(phi)
+// with T_0 = 1, T_m = cos(m phi), T_-m = sin(m phi) and N'_lm = N_lm (m = 0),
+// sqrt(2) N_lm (m != 0).  So each row r of the map first reduces to its 2n-1
+// azimuthal moments F_r,c,m = sum_col L_c(r, col) T_m(phi_col) (3 (2n-1)
+// multiply-adds per pixel: the pass streams the map once and is bound by HBM),
+// and the row then adds dOmega_r N'_lm P_l^|m|(cos theta_r) F_r,c,m to every
+// coefficient.  Row sums are per block; a fixed-order pass adds the blocks'
+// partial rows, so the result does not depend on scheduling.
+
+#include <cmath>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "shs.h"
+#include "shs_internal.h"
+
+namespace {
+
+constexpr int kEnvBlock = 128;
+constexpr int kEnvMaxBlocks = 152 * 8;
+constexpr int kEnvMaxSide = 65536;
+constexpr int kEnvReduceWarps = 32;
+
+struct EnvArgs {
+    const float* env;        // [H][W][3]
+    int H, W;
+    const float2* trig;      // [W] (cos, sin) of the column-centre azimuths
+    float domega_scale;      // dOmega_r = domega_scale * sin(theta_r)
+    float norm[64];          // N'_lm by linear index
+    float* partials;         // [gridDim.x][3K]
+    int vec4;                // 16-byte aligned map and width % 4 == 0: rows read as float4
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// P_l^m(x) without the Condon-Shortley phase, s = sqrt(1 - x^2) >= 0:
+// P_m^m = (2m-1)!! s^m, P_{m+1}^m = (2m+1) x P_m^m,
+// (l - m) P_l^m = (2l-1) x P_{l-1}^m - (l+m-1) P_{l-2}^m.
+__device__ float assoc_legendre(int l, int m, float x, float s) {
+    float pmm = 1.f;
+    for (int k = 1; k <= m; ++k) pmm *= (2.f * k - 1.f) * s;
+    if (l == m) return pmm;
+    float p1 = (2.f * m + 1.f) * x * pmm;
+    if (l == m + 1) return p1;
+    float p0 = pmm;
+    for (int ll = m + 2; ll <= l; ++ll) {
+        const float p2 = ((2.f * ll - 1.f) * x * p1 - (ll + m - 1.f) * p0) / (ll - m);
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+// One pixel's contribution to the 3 (2n-1) azimuthal moments, given
+// (cos phi, sin phi).  cos(m phi), sin(m phi) come from repeated rotation by
+// phi (complex multiplication: rounding grows about linearly in m, where the
+// three-term Chebyshev recurrence amplifies it near phi = 0 and pi); each
+// (cos, sin) pair accumulates with one packed float32x2 FMA per channel.
+template <int NB>
+__device__ __forceinline__ void add_pixel(float v0, float v1, float v2, float c1, float s1, float* acc,
+                                          float2* acc2) {
+    acc[0] += v0;
+    acc[1] += v1;
+    acc[2] += v2;
+    if constexpr (NB > 1) {
+        const float2 w0 = make_float2(v0, v0), w1 = make_float2(v1, v1), w2 = make_float2(v2, v2);
+        float cm = c1, sm = s1;
+#pragma unroll
+        for (int mm = 1; mm < NB; ++mm) {
+            const float2 t = make_float2(cm, sm);
+            acc2[3 * (mm - 1)] = __ffma2_rn(w0, t, acc2[3 * (mm - 1)]);
+            acc2[3 * (mm - 1) + 1] = __ffma2_rn(w1, t, acc2[3 * (mm - 1) + 1]);
+            acc2[3 * (mm - 1) + 2] = __ffma2_rn(w2, t, acc2[3 * (mm - 1) + 2]);
+            if (mm + 1 < NB) {
+                const float cn = fmaf(cm, c1, -sm * s1), sn = fmaf(sm, c1, cm * s1);
+                cm = cn;
+                sm = sn;
+            }
+        }
+    }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kEnvBlock) envmap_rows_kernel(const __grid_constant__ EnvArgs a) {
+    constexpr int K = NB * NB, NF = 2 * NB - 1, NV = 3 * NF, NOWN = (3 * K + kEnvBlock - 1) / kEnvBlock;
+    __shared__ float s_red[kEnvBlock / 32][NV];
+    __shared__ float s_row[NV];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // thread t owns coefficients e = t + j kEnvBlock < 3K (channel e / K, index e % K)
+    float coef[NOWN];
+#pragma unroll
+    for (int j = 0; j < NOWN; ++j) coef[j] = 0.f;
+    const bool vec = a.vec4 != 0;
+
+    for (int r = blockIdx.x; r < a.H; r += gridDim.x) {
+        // moments: acc = channel sums (m = 0), acc2[3 (m-1) + ch] = (cos, sin) moments
+        float acc[3] = {0.f, 0.f, 0.f};
+        float2 acc2[NB > 1 ? 3 * (NB - 1) : 1];
+#pragma unroll
+        for (int v = 0; v < (NB > 1 ? 3 * (NB - 1) : 1); ++v) acc2[v] = make_float2(0.f, 0.f);
+        const float* row = a.env + static_cast<size_t>(r) * a.W * 3;
+        if (vec) {
+            // 4 pixels (3 float4 of the map, 2 float4 of the azimuth table) per
+            // thread and step, two steps in flight
+            const float4* row4 = reinterpret_cast<const float4*>(row);
+            const float4* trig4 = reinterpret_cast<const float4*>(a.trig);
+            const int groups = a.W >> 2;
+#pragma unroll 2
+            for (int g = tid; g < groups; g += kEnvBlock) {
+                const float4 q0 = __ldcs(row4 + 3 * g), q1 = __ldcs(row4 + 3 * g + 1), q2 = __ldcs(row4 + 3 * g + 2);
+                const float4 t0 = __ldg(trig4 + 2 * g), t1 = __ldg(trig4 + 2 * g + 1);
+                add_pixel<NB>(q0.x, q0.y, q0.z, t0.x, t0.y, acc, acc2);
+                add_pixel<NB>(q0.w, q1.x, q1.y, t0.z, t0.w, acc, acc2);
+                add_pixel<NB>(q1.z, q1.w, q2.x, t1.x, t1.y, acc, acc2);
+                add_pixel<NB>(q2.y, q2.z, q2.w, t1.z, t1.w, acc, acc2);
+            }
+        } else {
+#pragma unroll 4
+            for (int col = tid; col < a.W; col += kEnvBlock) {
+                const float2 t = __ldg(a.trig + col);
+                add_pixel<NB>(__ldcs(row + 3 * col), __ldcs(row + 3 * col + 1), __ldcs(row + 3 * col + 2), t.x, t.y,
+                              acc, acc2);
+            }
+        }
+        // moment v in the kernel's order: channel ch, T index f -> ch * NF + f
+        float mom[NV];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            mom[ch * NF] = acc[ch];
+#pragma unroll
+            for (int mm = 1; mm < NB; ++mm) {
+                mom[ch * NF + 2 * mm - 1] = acc2[3 * (mm - 1) + ch].x;
+                mom[ch * NF + 2 * mm] = acc2[3 * (mm - 1) + ch].y;
+            }
+        }
+        float* acc_all = mom;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc_all[v] = warp_sum(acc_all[v]);
+        if (lane == 0) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) s_red[warp][v] = acc_all[v];
+        }
+        __syncthreads();
+        if (tid < NV) {
+            float t = 0.f;
+#pragma unroll
+            for (int w = 0; w < kEnvBlock / 32; ++w) t += s_red[w][tid];
+            s_row[tid] = t;
+        }
+        __syncthreads();
+        float st, ct;
+        sincospif((r + 0.5f) / a.H, &st, &ct);
+        const float w_row = a.domega_scale * st;
+#pragma unroll
+        for (int j = 0; j < NOWN; ++j) {
+            const int e = tid + j * kEnvBlock;
+            if (e < 3 * K) {
+                const int ch = e / K, idx = e % K;
+                int l = 0;
+                while ((l + 1) * (l + 1) <= idx) ++l;
+                const int m = idx - l * l - l, am = m < 0 ? -m : m;
+                const int f = m == 0 ? 0 : (m > 0 ? 2 * m - 1 : 2 * am);   // moment index of T_m
+                coef[j] = fmaf(w_row * a.norm[idx] * assoc_legendre(l, am, ct, st), s_row[ch * NF + f], coef[j]);
+            }
+        }
+        __syncthreads();   // s_red / s_row are rewritten by the next row
+    }
+#pragma unroll
+    for (int j = 0; j < NOWN; ++j) {
+        const int e = tid + j * kEnvBlock;
+        if (e < 3 * K) a.partials[static_cast<size_t>(blockIdx.x) * (3 * K) + e] = coef[j];
+    }
+}
+
+// (cos, sin) of each column's centre azimuth (c + 1/2) 2 pi / W, evaluated in
+// double precision and rounded once.
+__global__ void envmap_trig_kernel(int W, float2* trig) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= W) return;
+    double s, co;
+    sincospi((2.0 * c + 1.0) / W, &s, &co);
+    trig[c] = make_float2(static_cast<float>(co), static_cast<float>(s));
+}
+
+// light[e] = sum over the nblk partial rows in a fixed order; one block per
+// 32 entries, 32 warps striding over the rows.
+__global__ void __launch_bounds__(32 * kEnvReduceWarps) envmap_reduce_kernel(const float* partials, int nblk, int E,
+                                                                         float* light) {
+    __shared__ float s[kEnvReduceWarps][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    float v = 0.f;
+    if (e < E)
+        for (int b = warp; b < nblk; b += kEnvReduceWarps) v += partials[static_cast<size_t>(b) * E + e];
+    s[warp][lane] = v;
+    __syncthreads();
+    if (warp != 0 || e >= E) return;
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < kEnvReduceWarps; ++w) t += s[w][lane];
+    light[e] = t;
+}
+
+template <int NB>
+cudaError_t launch_env(EnvArgs& a, int grid, float* light, cudaStream_t s) {
+    envmap_trig_kernel<<<(a.W + 255) / 256, 256, 0, s>>>(a.W, const_cast<float2*>(a.trig));
+    shs::count_launch();
+    cudaError_t e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return e0;
+    envmap_rows_kernel<NB><<<grid, kEnvBlock, 0, s>>>(a);
+    shs::count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int E = 3 * NB * NB;
+    envmap_reduce_kernel<<<(E + 31) / 32, 32 * kEnvReduceWarps, 0, s>>>(a.partials, grid, E, light);
+    shs::count_launch();
+    return cudaGetLastError();
+}
+
+int env_grid(int height) { return height < kEnvMaxBlocks ? height : kEnvMaxBlocks; }
+
+double factorial_ratio(int l, int m) {   // (l - m)! / (l + m)!
+    double r = 1.0;
+    for (int k = l - m + 1; k <= l + m; ++k) r /= k;
+    return r;
+}
+
+}  // namespace
+
+// Workspace: the azimuth table [W] float2 (16-byte aligned length), then the
+// blocks' partial rows [grid][3K].
+size_t trig_bytes(int width) { return (sizeof(float2) * static_cast<size_t>(width) + 255) / 256 * 256; }
+
+extern "C" size_t shs_envmap_workspace_bytes(int32_t height, int32_t width, int32_t n_bands) {
+    if (height < 1 || width < 1 || n_bands < 1 || n_bands > 8 || height > kEnvMaxSide || width > kEnvMaxSide)
+        return 0;
+    return trig_bytes(width) + sizeof(float) * static_cast<size_t>(env_grid(height)) * 3 * n_bands * n_bands;
+}
+
+extern "C" shs_status shs_project_envmap(const float* env, int32_t height, int32_t width, int32_t n_bands,
+                                         float* light, void* workspace, size_t workspace_bytes, void* stream) {
+    if (!env || !light || !workspace)
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL env, light or workspace"));
+    if (n_bands < 1 || n_bands > 8)
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "n_bands %d not in 1..8", n_bands));
+    if (height < 1 || width < 1 || height > kEnvMaxSide || width > kEnvMaxSide)
+        return static_cast<shs_status>(
+            shs::report_error(SHS_ERR_INVALID_ARG, "map %d x %d outside 1..%d per side", height, width, kEnvMaxSide));
+    if (workspace_bytes < shs_envmap_workspace_bytes(height, width, n_bands))
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "workspace of %zu bytes < %zu needed",
+                                                         workspace_bytes,
+                                                         shs_envmap_workspace_bytes(height, width, n_bands)));
+    if (reinterpret_cast<uintptr_t>(workspace) & 15u)
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "workspace not 16-byte aligned"));
+    EnvArgs a{};
+    a.env = env;
+    a.H = height;
+    a.W = width;
+    a.trig = static_cast<const float2*>(workspace);
+    // cos theta_r - cos theta_{r+1} = 2 sin(theta_r) sin(pi / 2H)
+    a.domega_scale = static_cast<float>(2.0 * std::sin(M_PI / (2.0 * height)) * 2.0 * M_PI / width);
+    for (int l = 0; l < n_bands; ++l)
+        for (int m = -l; m <= l; ++m) {
+            const int am = m < 0 ? -m : m;
+            const double N = std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * factorial_ratio(l, am));
+            a.norm[l * l + l + m] = static_cast<float>(m == 0 ? N : std::sqrt(2.0) * N);
+        }
+    a.partials = reinterpret_cast<float*>(static_cast<unsigned char*>(workspace) + trig_bytes(width));
+    // rows of 4k pixels are 48k bytes, so an aligned map keeps every row aligned
+    a.vec4 = (width % 4 == 0 && (reinterpret_cast<uintptr_t>(env) & 15u) == 0) ? 1 : 0;
+    const int grid = env_grid(height);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    switch (n_bands) {
+        case 1: e = launch_env<1>(a, grid, light, s); break;
+        case 2: e = launch_env<2>(a, grid, light, s); break;
+        case 3: e = launch_env<3>(a, grid, light, s); break;
+        case 4: e = launch_env<4>(a, grid, light, s); break;
+        case 5: e = launch_env<5>(a, grid, light, s); break;
+        case 6: e = launch_env<6>(a, grid, light, s); break;
+        case 7: e = launch_env<7>(a, grid, light, s); break;
+        default: e = launch_env<8>(a, grid, light, s); break;
+    }
+    return e == cudaSuccess ? SHS_OK : static_cast<shs_status>(shs::report_cuda(e, "project envmap"));
+}

@@ -35,6 +35,7 @@ __all__ = [
     "sh_lighting",
     "serving_job",
     "mesh_deformation_scene",
+    "environment_map",
 ]
 
 
@@ -333,3 +334,32 @@ def mesh_deformation_scene(seed=2, n_theta=250, n_phi=200, n_spheres=200, n_para
     return dict(v0=_f32(v0), n0=_f32(n0), A_v=_f32(A_v), A_n=_f32(A_n), c0=_f32(c0), A_c=_f32(A_c),
                 radii=_f32(radii), albedo=_f32(albedo), light=_f32(light),
                 poses=_f32(np.concatenate([w, t], axis=1)), n_bands=n_bands)
+
+
+def environment_map(seed=5, height=1024, width=2048, n_suns=2):
+    """Equirectangular HDR radiance map [height, width, 3] (row r: polar
+    angles [r, r+1] pi / height from +z; column c: azimuths [c, c+1] 2 pi /
+    width), standing in for the paper's HDR environment maps: a sky whose
+    colour varies with elevation, a darker ground below the horizon, ``n_suns``
+    small bright discs (radiance 20-60, angular radius 2-5 degrees) and
+    multiplicative 5 % noise.  All values are positive."""
+    rng = np.random.default_rng(seed)
+    theta = (np.arange(height) + 0.5) * np.pi / height
+    phi = (np.arange(width) + 0.5) * 2.0 * np.pi / width
+    st, ct = np.sin(theta)[:, None], np.cos(theta)[:, None]
+    d = np.stack([st * np.cos(phi)[None, :], st * np.sin(phi)[None, :], np.broadcast_to(ct, (height, width))], -1)
+    zenith = rng.uniform(0.3, 0.6, 3)
+    horizon = rng.uniform(0.7, 1.0, 3)
+    ground = rng.uniform(0.1, 0.3, 3)
+    up = np.clip(d[..., 2:3], 0.0, 1.0)
+    sky = horizon[None, None] + (zenith - horizon)[None, None] * up
+    env = np.where(d[..., 2:3] >= 0.0, sky, ground[None, None])
+    for _ in range(n_suns):
+        el = rng.uniform(0.1, 1.3)
+        az = rng.uniform(0.0, 2.0 * np.pi)
+        s = np.array([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)])
+        radius = np.deg2rad(rng.uniform(2.0, 5.0))
+        disc = (d @ s) >= np.cos(radius)
+        env = env + disc[..., None] * rng.uniform(20.0, 60.0) * rng.uniform(0.8, 1.0, 3)[None, None]
+    env = env * rng.uniform(0.95, 1.05, size=env.shape)
+    return _f32(env)

@@ -103,3 +103,23 @@ def test_device_gaunt_route_agrees_with_oracle(n):
     ybar = [sum(float(c) * d[0, 0] ** a * d[0, 1] ** b * d[0, 2] ** e for (a, b, e), c in p.items())
             for p in gen_tables.ybar_polys(n)]
     np.testing.assert_allclose(np.array(N) * np.array(ybar), O.real_sh(n, d)[0], atol=1e-12)
+
+
+def test_envmap_projection_argument_checks_without_gpu(lib):
+    """Size query and argument validation of shs_project_envmap run on the host
+    (no device call for a rejected request)."""
+    assert lib.shs_envmap_workspace_bytes(0, 32, 4) == 0
+    assert lib.shs_envmap_workspace_bytes(16, 0, 4) == 0
+    assert lib.shs_envmap_workspace_bytes(16, 32, 9) == 0
+    assert lib.shs_envmap_workspace_bytes(16, 32, 4) == 256 + 4 * 16 * 3 * 16
+    assert lib.shs_envmap_workspace_bytes(100000, 32, 8) == 0
+    assert lib.shs_envmap_workspace_bytes(4096, 8192, 8) == 8 * 8192 + 4 * 1216 * 3 * 64
+    one = ctypes.c_void_p(16)
+    need = lib.shs_envmap_workspace_bytes(16, 32, 4)
+    for args in ((None, 16, 32, 4, one, one, need), (one, 16, 32, 4, None, one, need),
+                 (one, 16, 32, 4, one, None, need), (one, 16, 32, 0, one, one, need),
+                 (one, 16, 32, 9, one, one, need), (one, 0, 32, 4, one, one, need),
+                 (one, 16, 0, 4, one, one, need), (one, 16, 65537, 4, one, one, need),
+                 (one, 16, 32, 4, one, one, need - 4), (one, 16, 32, 4, one, ctypes.c_void_p(20), need)):
+        assert lib.shs_project_envmap(*args, None) == 1, args
+        assert lib.shs_last_error()

@@ -444,3 +444,67 @@ def test_horizon_cull_boundary_and_upper_spheres():
     on = O.shade_forward(cfg_on, *args)["radiance"]
     off = O.shade_forward(O.Config(n_bands=4), *args)["radiance"]
     np.testing.assert_array_equal(on, off)
+
+
+# --------------------------------------------------------------------------- Eq. 9: map -> SH lighting
+
+def test_envmap_constant_map():
+    """A constant map c: L_0 = c sqrt(4 pi) exactly (the pixel solid angles
+    tile the sphere); coefficients with m != 0 vanish by symmetry in phi; the
+    m = 0 ones of l > 0 vanish as the midpoint rule in theta converges (1/H^2)."""
+    errs = []
+    for H in (24, 48):
+        L = O.project_envmap(4, np.full((H, 2 * H, 3), 2.0))
+        np.testing.assert_allclose(L[:, 0], 2.0 * math.sqrt(4 * np.pi), rtol=1e-13)
+        m = np.array([mm for l in range(4) for mm in range(-l, l + 1)])
+        assert np.abs(L[:, m != 0]).max() < 1e-12
+        errs.append(np.abs(L[:, 1:]).max())
+    assert 3.6 < errs[0] / errs[1] < 4.4, errs
+
+
+def test_envmap_basis_function_converges_to_unit_vector():
+    """The map y_j (all channels) projects to e_j up to the quadrature error,
+    which falls as 1/H^2 (second-order rule)."""
+    for j in (0, 2, 6, 8, 13):
+        errs = []
+        for H in (32, 64):
+            dirs, _ = O.envmap_directions(H, 2 * H)
+            Y = O.real_sh(4, dirs)
+            L = O.project_envmap(4, np.repeat(Y[..., j:j + 1], 3, axis=-1))
+            e = L - np.eye(16)[j][None]
+            errs.append(np.abs(e).max())
+        assert errs[1] < 5e-4 and 3.5 < errs[0] / errs[1] < 4.5, (j, errs)
+
+
+def test_envmap_clamped_cosine_map():
+    """The map max(n . omega, 0) projects to the clamped-cosine lobe
+    A_hat_l y_lm(n) (closed form), within the quadrature error of a map with
+    a kink."""
+    n = np.array([0.3, -0.5, 0.81])
+    n = n / np.linalg.norm(n)
+    dirs, _ = O.envmap_directions(256, 512)
+    env = np.repeat(np.maximum(dirs @ n, 0.0)[..., None], 3, axis=-1)
+    L = O.project_envmap(4, env)
+    Ahat = np.array([np.pi, 2 * np.pi / 3, np.pi / 4, 0.0])[O.band_of(16)]
+    ref = Ahat * _scipy_real_sh(4, n[None])[0]
+    np.testing.assert_allclose(L[0], ref, atol=2e-4)
+
+
+def test_envmap_column_shift_rotates_coefficients():
+    """Shifting the map by s columns rotates it about z by a = 2 pi s / W;
+    the coefficients of each band rotate exactly:
+    L'_{l,m} = cos(m a) L_{l,m} - sin(m a) L_{l,-m},
+    L'_{l,-m} = sin(m a) L_{l,m} + cos(m a) L_{l,-m}."""
+    rng = np.random.default_rng(3)
+    H, W, s = 20, 36, 5
+    env = rng.uniform(0, 1, size=(H, W, 3))
+    L = O.project_envmap(5, env)
+    Ls = O.project_envmap(5, np.roll(env, s, axis=1))
+    a = 2 * math.pi * s / W
+    ref = L.copy()
+    for l in range(5):
+        for m in range(1, l + 1):
+            p, q = O.sh_index(l, m), O.sh_index(l, -m)
+            ref[:, p] = math.cos(m * a) * L[:, p] - math.sin(m * a) * L[:, q]
+            ref[:, q] = math.sin(m * a) * L[:, p] + math.cos(m * a) * L[:, q]
+    np.testing.assert_allclose(Ls, ref, atol=1e-12)
