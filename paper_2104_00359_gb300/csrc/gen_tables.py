@@ -508,6 +508,79 @@ def packed_lines(lines):
     return out
 
 
+QUAD_FROM = 7   # band counts from which the triple product runs by quadrature
+
+
+def quadrature_tables(n):
+    """Separable quadrature for the truncated triple product at n bands.
+
+    y_i(theta, phi) = Leg_i(theta) T_f(i)(phi) with T_0 = 1, T_{2m-1} =
+    cos(m phi), T_{2m} = sin(m phi).  The product of three SH of degree < n is
+    a polynomial of degree <= 3(n-1) on the sphere, so NZ = 3(n-1)/2 + 1
+    Gauss-Legendre nodes in z = cos(theta) and NP = 3(n-1) + 1 uniform azimuths
+    integrate it exactly:  (a * b)_i = sum_{za, pb} w_za A B y_i.
+    Returns (leg [NZ][K], trig [NP][2n-1], w [NZ]) in float64 and checks the
+    factorisation and the exactness against the Gaunt tensor."""
+    K = n * n
+    D = 3 * (n - 1)
+    NZ, NP = D // 2 + 1, D + 1
+    z, wz = np.polynomial.legendre.leggauss(NZ)
+    H = homogeneous_polys(n)
+    N = norms(n)
+
+    def ysh(i, x, y, zz):
+        return N[i] * sum(float(v) * x ** a * y ** b * zz ** c for (a, b, c), v in H[i].items())
+
+    def f_of(m):
+        return 0 if m == 0 else (2 * m - 1 if m > 0 else 2 * (-m))
+
+    leg = np.zeros((NZ, K))
+    for za in range(NZ):
+        st = math.sqrt(1.0 - z[za] ** 2)
+        for i in range(K):
+            l = int(math.isqrt(i))
+            m = i - l * l - l
+            ph = 0.0 if m >= 0 else math.pi / (2 * (-m))
+            leg[za, i] = ysh(i, st * math.cos(ph), st * math.sin(ph), z[za])
+    phis = 2.0 * math.pi * (np.arange(NP) + 0.5) / NP
+    trig = np.zeros((NP, 2 * n - 1))
+    trig[:, 0] = 1.0
+    for m in range(1, n):
+        trig[:, 2 * m - 1] = np.cos(m * phis)
+        trig[:, 2 * m] = np.sin(m * phis)
+    w = wz * 2.0 * math.pi / NP
+    # checks: separation at an arbitrary azimuth, exactness against C_ijk
+    rng = np.random.default_rng(0)
+    for za in range(NZ):
+        st = math.sqrt(1.0 - z[za] ** 2)
+        ph = 0.731
+        for i in range(K):
+            l = int(math.isqrt(i))
+            m = i - l * l - l
+            t = 1.0 if m == 0 else (math.cos(m * ph) if m > 0 else math.sin(-m * ph))
+            assert abs(ysh(i, st * math.cos(ph), st * math.sin(ph), z[za]) - leg[za, i] * t) < 1e-12
+    fidx = [f_of(i - int(math.isqrt(i)) ** 2 - int(math.isqrt(i))) for i in range(K)]
+    Y = np.einsum("ai,bi->abi", leg, trig[:, fidx])          # [NZ, NP, K]
+    a, bb = rng.normal(size=K), rng.normal(size=K)
+    prod = np.einsum("ab,ab,abi->i", w[:, None] * (Y @ a), Y @ bb, Y)
+    ref = np.zeros(K)
+    for (i, j, k), v in gaunt_monomial(n).items():
+        ref[i] += float(v) * (a[j] * bb[k] + (a[k] * bb[j] if j != k else 0.0))
+    assert np.abs(prod - ref).max() < 1e-10 * max(1.0, np.abs(ref).max()), np.abs(prod - ref).max()
+    return leg, trig, w
+
+
+def emit_quadrature(n):
+    leg, trig, w = quadrature_tables(n)
+
+    def arr(name, a):
+        vals = ", ".join(fmt(("c", float(v))) for v in np.asarray(a).ravel())
+        return f"static __constant__ float {name}[{np.asarray(a).size}] = {{{vals}}};"
+    return [f"#if defined(SHS_NB) && SHS_NB == {n}",
+            arr(f"kQuadLeg{n}", leg), arr(f"kQuadTrig{n}", trig), arr(f"kQuadW{n}", w),
+            "#endif"], leg.shape[0], trig.shape[0]
+
+
 def indent(lines, k=8):
     return "\n".join(" " * k + ln for ln in lines)
 
@@ -516,7 +589,8 @@ def generate():
     parts = [
         "// Generated by gen_tables.py -- do not edit.",
         "// Real SH polynomials, their reverse-mode gradients, and the truncated",
-        "// SH triple product (Sec. 3.2, Eq. 3 and Eq. 6-7), unrolled per band count.",
+        "// SH triple product (Sec. 3.2, Eq. 3 and Eq. 6-7), unrolled per band count",
+        "// (from 7 bands, quadrature tables for the triple product instead).",
         "#pragma once",
         "",
         "namespace shsgen {",
@@ -530,9 +604,11 @@ def generate():
         code, outs = build_ybar(n)
         fwd = emit_forward(code, outs, "Y")
         vjp = emit_forward(code, [], "Y") + emit_vjp(code, outs)
-        mul_l, sqr_l = emit_gaunt(n, C)
+        mul_l, sqr_l = emit_gaunt(n, C) if n < QUAD_FROM else ([], [])
         N = norms(n)
         A = ahat(n)
+        if n >= QUAD_FROM:
+            parts.extend(emit_quadrature(n)[0])
         parts.append(f"template <> struct SH<{n}> {{")
         parts.append(f"    static constexpr int K = {K};")
         parts.append(f"    static constexpr int NNZ_SYM = {len(C)};   // entries (i, j <= k)")
@@ -590,14 +666,27 @@ def generate():
         # operands of an out-of-line call live in local memory, a few hundred
         # bytes against ~10^4 FMAs per call; the operands never alias, which
         # lets every input stay in a register while the outputs are stored).
-        prod = "__noinline__" if n >= 7 else "__forceinline__"
-        parts.append(f"    __device__ {prod} static void mul(const float* __restrict__ a, const float* __restrict__ b,")
-        parts.append("                                      float* __restrict__ o) {")
-        parts.append(indent(mul_l))
-        parts.append("    }")
-        parts.append(f"    __device__ {prod} static void sqr(const float* __restrict__ a, float* __restrict__ o) {{")
-        parts.append(indent(sqr_l))
-        parts.append("    }")
+        if n < QUAD_FROM:
+            parts.append("    __device__ __forceinline__ static void mul(const float* __restrict__ a, const float* __restrict__ b,")
+            parts.append("                                               float* __restrict__ o) {")
+            parts.append(indent(mul_l))
+            parts.append("    }")
+            parts.append("    __device__ __forceinline__ static void sqr(const float* __restrict__ a, float* __restrict__ o) {")
+            parts.append(indent(sqr_l))
+            parts.append("    }")
+        else:
+            # The unrolled products would be 10^4 FMAs of straight-line code
+            # each (instruction-fetch bound); these band counts use the
+            # separable quadrature of quadrature_tables() instead.
+            _, nz, npp = emit_quadrature(n)
+            parts.append(f"    static constexpr int QZ = {nz};    // Gauss-Legendre nodes in cos(theta)")
+            parts.append(f"    static constexpr int QP = {npp};    // uniform azimuths")
+            parts.append(f"    static constexpr int QF = {2 * n - 1};    // azimuthal harmonics 1, cos m phi, sin m phi")
+            parts.append("#if defined(SHS_NB) && SHS_NB == " + str(n))
+            parts.append(f"    __device__ __forceinline__ static const float* qleg() {{ return kQuadLeg{n}; }}")
+            parts.append(f"    __device__ __forceinline__ static const float* qtrig() {{ return kQuadTrig{n}; }}")
+            parts.append(f"    __device__ __forceinline__ static const float* qw() {{ return kQuadW{n}; }}")
+            parts.append("#endif")
         parts.append("};")
         parts.append("")
     parts.append("}  // namespace shsgen")

@@ -385,6 +385,105 @@ __device__ __forceinline__ int scaling_k(const SceneView& sc, float nrm2) {
     return k;
 }
 
+// Truncated SH triple product o = a * b (Eq. 7) and square o = a * a.
+// Up to 6 bands: the unrolled Gaunt contraction of the generated header.
+// From 7 bands: a separable quadrature that is exact for these degrees
+// (Gauss-Legendre in cos(theta) x uniform azimuths, tables in the generated
+// header): per latitude, the operands' azimuthal coefficients
+// c_f = sum_i a_i Leg_i (f the harmonic of i), their values at each azimuth,
+// the pointwise product accumulated against the harmonics, then projected
+// back with the latitude's weight.  Loop code keeps the instruction footprint
+// small (the unrolled contraction is ~10^4 instructions per call).  The
+// constant (l = 0) parts go separately: with a = a_0 y_0 + a~ and
+// y_0 = 1/sqrt(4 pi), a * b = a~ * b~ + y_0 (a_0 b~ + b_0 a~) + y_0 a_0 b_0 e_0
+// exactly, so only a~ * b~ runs through the quadrature; the exponential's
+// operands are dominated by their constant part, and this keeps the rounding
+// of the quadrature sums relative to the small remainder.
+__host__ __device__ constexpr int harm_of(int i) {   // 0: 1, 2m-1: cos m phi, 2m: sin m phi
+    return (i - band_of(i) * band_of(i) - band_of(i)) == 0
+               ? 0
+               : ((i - band_of(i) * band_of(i) - band_of(i)) > 0
+                      ? 2 * (i - band_of(i) * band_of(i) - band_of(i)) - 1
+                      : -2 * (i - band_of(i) * band_of(i) - band_of(i)));
+}
+
+#if SHS_NB >= 7
+template <bool SQR>
+__device__ __noinline__ void quad_product(const float* __restrict__ a, const float* __restrict__ b,
+                                          float* __restrict__ o) {
+    constexpr int QZ = SH::QZ, QP = SH::QP, QF = SH::QF;
+    const float* leg = SH::qleg();
+    const float* trig = SH::qtrig();
+    const float* qw = SH::qw();
+    float A[K], B[SQR ? 1 : K], O[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        A[i] = a[i];
+        if constexpr (!SQR) B[i] = b[i];
+        O[i] = 0.f;
+    }
+    const float a0 = A[0], b0 = SQR ? A[0] : B[0];
+    A[0] = 0.f;
+    if constexpr (!SQR) B[0] = 0.f;
+#pragma unroll 1
+    for (int za = 0; za < QZ; ++za) {
+        float ca[QF], cb[SQR ? 1 : QF], d[QF];
+#pragma unroll
+        for (int f = 0; f < QF; ++f) {
+            ca[f] = 0.f;
+            if constexpr (!SQR) cb[f] = 0.f;
+            d[f] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const float L = leg[za * K + i];
+            ca[harm_of(i)] = fmaf(A[i], L, ca[harm_of(i)]);
+            if constexpr (!SQR) cb[harm_of(i)] = fmaf(B[i], L, cb[harm_of(i)]);
+        }
+#pragma unroll 1
+        for (int pb = 0; pb < QP; ++pb) {
+            const float* T = trig + pb * QF;
+            float va = 0.f, vb = 0.f;
+#pragma unroll
+            for (int f = 0; f < QF; ++f) {
+                va = fmaf(ca[f], T[f], va);
+                if constexpr (!SQR) vb = fmaf(cb[f], T[f], vb);
+            }
+            const float p = SQR ? va * va : va * vb;
+#pragma unroll
+            for (int f = 0; f < QF; ++f) d[f] = fmaf(p, T[f], d[f]);
+        }
+        const float w = qw[za];
+#pragma unroll
+        for (int i = 0; i < K; ++i) O[i] = fmaf(w * leg[za * K + i], d[harm_of(i)], O[i]);
+    }
+    O[0] = fmaf(kInvSqrt4Pi * a0, b0, O[0]);
+#pragma unroll
+    for (int i = 1; i < K; ++i) {
+        if constexpr (SQR) O[i] = fmaf(2.f * kInvSqrt4Pi * a0, A[i], O[i]);
+        else O[i] = fmaf(kInvSqrt4Pi * a0, B[i], fmaf(kInvSqrt4Pi * b0, A[i], O[i]));
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) o[i] = O[i];
+}
+#endif
+
+__device__ __forceinline__ void sh_mul(const float* a, const float* b, float* o) {
+#if SHS_NB >= 7
+    quad_product<false>(a, b, o);
+#else
+    SH::mul(a, b, o);
+#endif
+}
+
+__device__ __forceinline__ void sh_sqr(const float* a, float* o) {
+#if SHS_NB >= 7
+    quad_product<true>(a, nullptr, o);
+#else
+    SH::sqr(a, o);
+#endif
+}
+
 // Clamped-cosine SH for a (not necessarily unit) normal; also returns the unit
 // normal and 1/|n| for the adjoint.
 __device__ __forceinline__ void cosine_lobe(float nx, float ny, float nz, float* H, float& ux,
@@ -486,7 +585,7 @@ __device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_
     for (int i = 1; i < K; ++i) S[i] = a0 * (f[i] * scale);
     for (int t = 0; t < k; ++t) {
         float T[K];
-        SH::sqr(S, T);
+        sh_sqr(S, T);
 #pragma unroll
         for (int i = 0; i < K; ++i) S[i] = T[i];
     }
@@ -499,7 +598,7 @@ __device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_
     cosine_lobe(__ldg(a.normals + 3 * p), __ldg(a.normals + 3 * p + 1), __ldg(a.normals + 3 * p + 2),
                 H, ux, uy, uz, il);
     float W[K];
-    SH::mul(V, H, W);
+    sh_mul(V, H, W);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         float d = 0.f;
@@ -786,7 +885,7 @@ __global__ void build_mcat_kernel(SceneView sc, unsigned char* b3h, unsigned cha
         Lc[i] = sc.light[c * KPAD + i];
         e[i] = i == j ? 1.f : 0.f;
     }
-    SH::mul(Lc, e, T);
+    sh_mul(Lc, e, T);
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) {
         uint16_t h, l;
@@ -932,7 +1031,7 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_
     float hist[kMaxK][K];
     for (int t = 0; t < k; ++t) {
         float T[K];
-        SH::sqr(S, T);
+        sh_sqr(S, T);
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             hist[t][i] = S[i];
@@ -947,7 +1046,7 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_
     cosine_lobe(load_or(a.normals, 3 * q, live), load_or(a.normals, 3 * q + 1, live),
                 load_or(a.normals, 3 * q + 2, live), H, ux, uy, uz, il);
     float W[K];
-    SH::mul(V, H, W);
+    sh_mul(V, H, W);
 
     // ---- shading adjoint: B_c = a_c L_c . W
     float dB[3], alb[3], loss = 0.f;
@@ -992,8 +1091,8 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_
         if (lane == 0) s_dl[warp][3 * K] += v;
     }
     float dV[K], dH[K];
-    SH::mul(dW, H, dV);                     // C is symmetric: adjoint of a*b is d*b
-    SH::mul(dW, V, dH);
+    sh_mul(dW, H, dV);                     // C is symmetric: adjoint of a*b is d*b
+    sh_mul(dW, V, dH);
 
     // ---- normal adjoint through H = A_hat_l NORM_i Ybar_i(n / |n|)
     if (live && a.d_normals) {
@@ -1019,7 +1118,7 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_
         float Ht[K], T[K];
 #pragma unroll
         for (int i = 0; i < K; ++i) Ht[i] = hist[t][i];
-        SH::mul(dS, Ht, T);
+        sh_mul(dS, Ht, T);
 #pragma unroll
         for (int i = 0; i < K; ++i) dS[i] = 2.f * T[i];
     }
