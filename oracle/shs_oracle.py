@@ -69,6 +69,7 @@ class Config:
     exp_kmax: int = 16
     fixed_k: int = -1
     horizon_cull: bool = False
+    exp_mode: int = 0          # 0: scaling + optimal linear + squarings; 1: projected exponential
 
 
 def sh_index(l, m):
@@ -325,6 +326,32 @@ def sh_exp(cfg, C, f, k=None):
     return V, dict(k=k, e0=e0, g=g, a=a, levels=levels)
 
 
+def projected_exp_rule(n_bands):
+    """Quadrature of the projected-exponential variant: 2n Gauss-Legendre nodes
+    in cos(theta) x 4n uniform azimuths (exact for polynomial integrands of
+    degree < 4n; exp of the log-visibility is not one, so the rule is part of
+    the variant's definition)."""
+    return sphere_quadrature(2 * n_bands, 4 * n_bands)
+
+
+def sh_exp_projected(n_bands, f, rule=None):
+    """Variant of the SH exponential (the next-step alternative to Ren et
+    al.'s scaling and squaring): the projection onto n bands of the pointwise
+    exponential of the band-limited log-visibility,
+        V_i = sum_q w_q exp(f~(w_q)) y_i(w_q),   f~ = sum_j f_j y_j,
+    with the constant term isolated (exp(f~) = e0 exp(f^), e0 = exp(f_0 y_0)).
+    Returns V and the intermediates of its adjoint."""
+    dirs, w = rule if rule is not None else projected_exp_rule(n_bands)
+    Y = real_sh(n_bands, dirs)                     # [Q, K]
+    e0 = np.exp(f[:, 0] / SQRT_FOUR_PI)
+    fh = f.copy()
+    fh[:, 0] = 0.0
+    E = np.exp(fh @ Y.T)                           # [P, Q]
+    U = (E * w[None, :]) @ Y
+    V = e0[:, None] * U
+    return V, dict(k=np.zeros(f.shape[0], dtype=np.int64), e0=e0, E=E, Y=Y, w=w, U=U)
+
+
 # ----------------------------------------------------------------------------
 # Forward shading (Eq. 8)
 # ----------------------------------------------------------------------------
@@ -342,7 +369,10 @@ def shade_forward(cfg, points, normals, albedo, centers, radii, light, k=None):
     L = np.asarray(light, np.float64).reshape(3, n * n)
     f = log_visibility(cfg, pts, np.asarray(centers, np.float64).reshape(-1, 3),
                        np.asarray(radii, np.float64).reshape(-1), normals)
-    V, ex = sh_exp(cfg, C, f, k)
+    if cfg.exp_mode == 1:
+        V, ex = sh_exp_projected(n, f)
+    else:
+        V, ex = sh_exp(cfg, C, f, k)
     H = cosine_lobe(n, normals)
     W = sh_product(C, V, H)
     B = alb * (W @ L.T)
@@ -391,6 +421,38 @@ def project_envmap(n_bands, env):
 # Reverse-mode adjoint (Sec. 3.5: B is differentiable w.r.t. theta, L and a)
 # ----------------------------------------------------------------------------
 
+def _sh_exp_adjoint(C, ex, dV):
+    """df from dV through the scaling, optimal linear step and squarings."""
+    # V = e0 * S_k ;  S_{t+1} = S_t * S_t ;  S_0 = a (sqrt(4pi) e_0 + g)
+    k_pt, e0, g, a, levels = ex["k"], ex["e0"], ex["g"], ex["a"], ex["levels"]
+    Sk = levels[-1]
+    de0 = np.sum(dV * Sk, axis=-1)
+    dS = e0[:, None] * dV
+    for t in reversed(range(len(levels) - 1)):
+        act = (k_pt > t)[:, None]
+        back = 2.0 * np.einsum("ijk,pi,pk->pj", C, dS, levels[t], optimize=True)
+        dS = np.where(act, back, dS)
+    base = g.copy()
+    base[:, 0] = SQRT_FOUR_PI
+    da = np.sum(dS * base, axis=-1)
+    dg = a[:, None] * dS
+    dg += (da * a / FOUR_PI)[:, None] * g          # d a / d g = a g / (4 pi)
+    dg[:, 0] = 0.0
+    df = dg / (2.0 ** k_pt)[:, None]
+    df[:, 0] = de0 * e0 / SQRT_FOUR_PI
+    return df
+
+
+def _sh_exp_projected_adjoint(ex, dV):
+    """df from dV through V = e0 (E w) Y, E = exp(f^ Y^T), e0 = exp(f_0 y_0)."""
+    e0, E, Y, w, U = ex["e0"], ex["E"], ex["Y"], ex["w"], ex["U"]
+    de0 = np.sum(dV * U, axis=-1)
+    dE = (e0[:, None] * dV) @ Y.T * w[None, :]        # [P, Q]
+    df = (dE * E) @ Y
+    df[:, 0] = de0 * e0 / SQRT_FOUR_PI
+    return df
+
+
 def shade_backward(cfg, points, normals, albedo, centers, radii, light, d_radiance, k=None):
     """Gradients of sum(d_radiance * B) w.r.t. every input, in float64.
 
@@ -436,23 +498,10 @@ def shade_backward(cfg, points, normals, albedo, centers, radii, light, d_radian
     Yt = Yg - nh[:, None, :] * np.sum(nh[:, None, :] * Yg, axis=-1, keepdims=True)
     abs_d_normals = np.einsum("pk,pkc->pc", np.abs(dH * coef), np.abs(Yt)) / nlen
 
-    # V = e0 * S_k ;  S_{t+1} = S_t * S_t ;  S_0 = a (sqrt(4pi) e_0 + g)
-    k_pt, e0, g, a, levels = ex["k"], ex["e0"], ex["g"], ex["a"], ex["levels"]
-    Sk = levels[-1]
-    de0 = np.sum(dV * Sk, axis=-1)
-    dS = e0[:, None] * dV
-    for t in reversed(range(len(levels) - 1)):
-        act = (k_pt > t)[:, None]
-        back = 2.0 * np.einsum("ijk,pi,pk->pj", C, dS, levels[t], optimize=True)
-        dS = np.where(act, back, dS)
-    base = g.copy()
-    base[:, 0] = SQRT_FOUR_PI
-    da = np.sum(dS * base, axis=-1)
-    dg = a[:, None] * dS
-    dg += (da * a / FOUR_PI)[:, None] * g          # d a / d g = a g / (4 pi)
-    dg[:, 0] = 0.0
-    df = dg / (2.0 ** k_pt)[:, None]
-    df[:, 0] = de0 * e0 / SQRT_FOUR_PI
+    if cfg.exp_mode == 1:
+        df = _sh_exp_projected_adjoint(ex, dV)
+    else:
+        df = _sh_exp_adjoint(C, ex, dV)
 
     # f = sum_j R_l zh_l(cos a_j) y(s_j),  s_j = d_j / D_j,  d_j = c_j - x
     lvec = band_of(K)

@@ -106,3 +106,28 @@ def test_adjoint_with_horizon_cull():
             fd = np.sum(dB * (O.shade_forward(cfg, *[p[k] for k in ORDER])["radiance"]
                               - O.shade_forward(cfg, *[m[k] for k in ORDER])["radiance"])) / (2 * h)
             assert abs(fd - grad[idx]) < 2e-7 * max(1.0, abs(fd)), (name, idx, fd, grad[idx])
+
+
+def test_adjoint_of_projected_exponential():
+    """The projected-exponential variant's adjoint against central differences."""
+    sc = _scene(46, 8, 5, 4)
+    cfg = O.Config(n_bands=4, exp_mode=1)
+    dB = np.random.default_rng(47).normal(size=sc["points"].shape)
+    g = O.shade_backward(cfg, *[sc[k] for k in ORDER], dB)
+    grads = dict(points=g["d_points"], normals=g["d_normals"], albedo=g["d_albedo"],
+                 centers=g["d_centers"], radii=g["d_radii"], light=g["d_light"])
+    h = 1e-6
+    for name in ("centers", "radii", "points", "normals", "light"):
+        base = sc[name]
+        fd = np.zeros_like(base)
+        it = np.nditer(base, flags=["multi_index"])
+        for _ in it:
+            idx = it.multi_index
+            p, m = dict(sc), dict(sc)
+            p[name], m[name] = base.copy(), base.copy()
+            p[name][idx] += h
+            m[name][idx] -= h
+            fd[idx] = np.sum(dB * (O.shade_forward(cfg, *[p[k] for k in ORDER])["radiance"]
+                                   - O.shade_forward(cfg, *[m[k] for k in ORDER])["radiance"])) / (2 * h)
+        scale = max(np.abs(fd).max(), 1e-3)
+        np.testing.assert_allclose(grads[name], fd, atol=2e-7 * scale + 1e-9, err_msg=name)

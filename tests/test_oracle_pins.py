@@ -508,3 +508,45 @@ def test_envmap_column_shift_rotates_coefficients():
             ref[:, p] = math.cos(m * a) * L[:, p] - math.sin(m * a) * L[:, q]
             ref[:, q] = math.sin(m * a) * L[:, p] + math.cos(m * a) * L[:, q]
     np.testing.assert_allclose(Ls, ref, atol=1e-12)
+
+
+# --------------------------------------------------------------------------- projected exponential variant
+
+def test_projected_exp_constant_and_first_order():
+    """exp of a constant is exact (V = e^{f_0 y_0} sqrt(4 pi) e_0: the rule
+    integrates y_0 y_i exactly); for a tiny f^ the projection is
+    e0 (sqrt(4 pi) e_0 + f^) to second order."""
+    n = 4
+    f = np.zeros((2, 16))
+    f[:, 0] = [0.7, -2.0]
+    V, _ = O.sh_exp_projected(n, f)
+    ref = np.zeros((2, 16))
+    ref[:, 0] = np.exp(f[:, 0] / math.sqrt(4 * np.pi)) * math.sqrt(4 * np.pi)
+    np.testing.assert_allclose(V, ref, rtol=1e-13, atol=1e-14)
+    rng = np.random.default_rng(1)
+    for eps in (1e-3, 1e-4):
+        g = rng.normal(size=(1, 16)) * eps
+        g[:, 0] = 0.0
+        V, _ = O.sh_exp_projected(n, g)
+        lin = g.copy()
+        lin[:, 0] = math.sqrt(4 * np.pi)
+        assert np.abs(V - lin).max() < 2 * eps * eps * 16
+
+
+def test_projected_exp_rule_converges_to_the_projection():
+    """The variant's rule (2n x 4n nodes) against a much finer rule: the
+    difference is the rule's aliasing error, small for moderate
+    log-visibility and shrinking as the rule is refined."""
+    n = 4
+    rng = np.random.default_rng(2)
+    f = rng.normal(0.0, 0.6, size=(20, 16))
+    fine = O.sphere_quadrature(64, 128)
+    Vf, _ = O.sh_exp_projected(n, f, rule=fine)
+    V1, _ = O.sh_exp_projected(n, f)
+    V2, _ = O.sh_exp_projected(n, f, rule=O.sphere_quadrature(4 * n, 8 * n))
+    e1 = np.abs(V1 - Vf).max() / np.abs(Vf).max()
+    e2 = np.abs(V2 - Vf).max() / np.abs(Vf).max()
+    assert e1 < 5e-3 and e2 < 1e-2 * e1, (e1, e2)
+    # the fine rule is itself converged: it agrees with a finer one
+    Vff, _ = O.sh_exp_projected(n, f, rule=O.sphere_quadrature(96, 192))
+    assert np.abs(Vff - Vf).max() < 1e-12 * np.abs(Vf).max()
