@@ -546,9 +546,10 @@ def bench_heightfield(args, world, rank, local):
     T = {k: torch.from_numpy(sc[k]).to(dev) for k in ("points", "normals", "albedo", "centers", "radii", "light")}
     P, N = sc["points"].shape[0], sc["centers"].shape[0]
     out = {}
-    all_precs = (("fp32", 0), ("bf16_split_tc", 2), ("fp16_split_tc", 3))
-    for prec_name, prec in [x for x in all_precs if x[0] in args.precisions.split(",")]:
-        scene = Scene(T["centers"], T["radii"], T["light"], Config(n_bands=8, precision=prec))
+    # (name, precision, exp_mode): exp_mode 1 is the projected-exponential variant
+    all_precs = (("fp32", 0, 0), ("bf16_split_tc", 2, 0), ("fp16_split_tc", 3, 0), ("fp32_projexp", 0, 1))
+    for prec_name, prec, mode in [x for x in all_precs if x[0] in args.precisions.split(",")]:
+        scene = Scene(T["centers"], T["radii"], T["light"], Config(n_bands=8, precision=prec, exp_mode=mode))
         saved = scene.new_saved(P, dev)
         dB = torch.randn((P, 3), device=dev)
         times_f, times_b = [], []
@@ -568,13 +569,24 @@ def bench_heightfield(args, world, rank, local):
         sel = np.sort(np.random.default_rng(1).choice(P, 256, replace=False))
         args_o = [sc[f][sel] if f in ("points", "normals", "albedo") else sc[f]
                   for f in ("points", "normals", "albedo", "centers", "radii", "light")]
-        ref = O.shade_forward(O.Config(n_bands=8), *args_o, k=k[sel])["radiance"]
+        ref = O.shade_forward(O.Config(n_bands=8, exp_mode=mode), *args_o, k=k[sel])["radiance"]
         got = B.cpu().numpy()[sel]
         err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
         out[prec_name] = {"fwd_ms": statistics.fmean(times_f), "bwd_ms": statistics.fmean(times_b),
                           "pairs_per_s_fwd": P * N / (statistics.fmean(times_f) * 1e-3),
                           "pairs_per_s_fwd_bwd": P * N / ((statistics.fmean(times_f) + statistics.fmean(times_b)) * 1e-3),
                           "radiance_max_rel_err_vs_fp64": float(err.max()), "k_mean": float(k.mean())}
+        if mode == 1:
+            # accuracy of both exponential methods (FP64) against the projection of
+            # exp(f) by a fine rule (64 x 128 nodes) on the same sample
+            fine = O.shade_forward(O.Config(n_bands=8, exp_mode=1, exp_rule=(64, 128)), *args_o)["radiance"]
+            sq = O.shade_forward(O.Config(n_bands=8), *args_o)["radiance"]
+
+            def rel(x):
+                d = np.abs(x - fine) / np.maximum(np.abs(fine), 1e-3 * np.abs(fine).max())
+                return {"max": float(d.max()), "median": float(np.median(d))}
+            out[prec_name]["vs_fine_projection_fp64"] = {"projected_2n_x_4n": rel(ref),
+                                                         "scaling_squaring": rel(sq)}
         scene.close()
     first = next(iter(out.values()))
     return dict(metric="height field 1024^2 x 300 spheres, n_bands=8: pairs/sec and error vs FP64 per precision",
@@ -684,8 +696,8 @@ def main():
     ap.add_argument("--workload", choices=("capsule", "serving", "heightfield", "envmap"), default="capsule",
                     help="capsule: the 512x512 G-buffer step (default); serving: the mixed request stream")
     ap.add_argument("--hf-res", type=int, default=1024, help="height-field grid side (heightfield workload)")
-    ap.add_argument("--precisions", default="fp32,bf16_split_tc,fp16_split_tc",
-                    help="heightfield workload: comma list of fp32, bf16_split_tc, fp16_split_tc")
+    ap.add_argument("--precisions", default="fp32,bf16_split_tc,fp16_split_tc,fp32_projexp",
+                    help="heightfield workload: comma list of fp32, bf16_split_tc, fp16_split_tc, fp32_projexp")
     ap.add_argument("--env-res", type=int, default=4096, help="environment map rows (width = 2 x rows)")
     ap.add_argument("--serve-jobs", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=2000)

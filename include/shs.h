@@ -84,10 +84,13 @@ typedef struct {
                            /*    blockers); 1: per point, skip a sphere lying entirely     */
                            /*    below the tangent plane, (c - x) . n_hat < -r (no         */
                            /*    gradient through that selection)                          */
+    int32_t exp_mode;      /* 0: the SH exponential by scaling, optimal linear step and    */
+                           /*    squarings (Sec. 3.3.2);  1: projected exponential         */
+                           /*    P_n[exp(f)] by a 2n x 4n quadrature (FP32 precision only) */
 } shs_config;
 
 /* Fills *cfg with n_bands=4, epsilon=3, exp_tau=1, exp_kmax=16, fixed_k=-1,
- * precision=SHS_FP32, deterministic=1, horizon_cull=0. */
+ * precision=SHS_FP32, deterministic=1, horizon_cull=0, exp_mode=0. */
 shs_status shs_config_default(shs_config* cfg);
 
 /* Creates a resident scene of n_spheres occluder spheres (Sec. 3.3.1: the

@@ -70,6 +70,7 @@ class Config:
     fixed_k: int = -1
     horizon_cull: bool = False
     exp_mode: int = 0          # 0: scaling + optimal linear + squarings; 1: projected exponential
+    exp_rule: tuple | None = None   # (n_theta, n_phi) of the projected exponential; None: (2n, 4n)
 
 
 def sh_index(l, m):
@@ -370,7 +371,7 @@ def shade_forward(cfg, points, normals, albedo, centers, radii, light, k=None):
     f = log_visibility(cfg, pts, np.asarray(centers, np.float64).reshape(-1, 3),
                        np.asarray(radii, np.float64).reshape(-1), normals)
     if cfg.exp_mode == 1:
-        V, ex = sh_exp_projected(n, f)
+        V, ex = sh_exp_projected(n, f, None if cfg.exp_rule is None else sphere_quadrature(*cfg.exp_rule))
     else:
         V, ex = sh_exp(cfg, C, f, k)
     H = cosine_lobe(n, normals)

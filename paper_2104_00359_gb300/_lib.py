@@ -30,6 +30,7 @@ class ShsConfig(ctypes.Structure):
         ("precision", c_int32),
         ("deterministic", c_int32),
         ("horizon_cull", c_int32),
+        ("exp_mode", c_int32),
     ]
 
 

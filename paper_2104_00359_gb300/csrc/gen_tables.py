@@ -570,6 +570,64 @@ def quadrature_tables(n):
     return leg, trig, w
 
 
+def exp_rule_tables(n):
+    """Rule of the projected-exponential variant: 2n Gauss-Legendre nodes in
+    cos(theta) x 4n uniform azimuths, in the separable form of
+    quadrature_tables (leg [2n][K], trig [4n][2n-1], w [2n]).  Checked:
+    the factorisation, and sum_q w y_i y_j = delta_ij (exact at this degree)."""
+    K = n * n
+    NZ, NP = 2 * n, 4 * n
+    z, wz = np.polynomial.legendre.leggauss(NZ)
+    H = homogeneous_polys(n)
+    N = norms(n)
+
+    def ysh(i, x, y, zz):
+        return N[i] * sum(float(v) * x ** a * y ** b * zz ** c for (a, b, c), v in H[i].items())
+
+    leg = np.zeros((NZ, K))
+    for za in range(NZ):
+        st = math.sqrt(1.0 - z[za] ** 2)
+        for i in range(K):
+            l = int(math.isqrt(i))
+            m = i - l * l - l
+            ph = 0.0 if m >= 0 else math.pi / (2 * (-m))
+            leg[za, i] = ysh(i, st * math.cos(ph), st * math.sin(ph), z[za])
+    phis = 2.0 * math.pi * (np.arange(NP) + 0.5) / NP
+    trig = np.zeros((NP, 2 * n - 1))
+    trig[:, 0] = 1.0
+    for m in range(1, n):
+        trig[:, 2 * m - 1] = np.cos(m * phis)
+        trig[:, 2 * m] = np.sin(m * phis)
+    w = wz * 2.0 * math.pi / NP
+
+    def f_of(i):
+        l = int(math.isqrt(i))
+        m = i - l * l - l
+        return 0 if m == 0 else (2 * m - 1 if m > 0 else 2 * (-m))
+    Y = np.einsum("ai,bi->abi", leg, trig[:, [f_of(i) for i in range(K)]])
+    gram = np.einsum("a,abi,abj->ij", w, Y, Y)
+    assert np.abs(gram - np.eye(K)).max() < 1e-12
+    for za in range(NZ):
+        st = math.sqrt(1.0 - z[za] ** 2)
+        for i in range(K):
+            l = int(math.isqrt(i))
+            m = i - l * l - l
+            t = 1.0 if m == 0 else (math.cos(m * 0.4) if m > 0 else math.sin(-m * 0.4))
+            assert abs(ysh(i, st * math.cos(0.4), st * math.sin(0.4), z[za]) - leg[za, i] * t) < 1e-12
+    return leg, trig, w
+
+
+def emit_exp_rule(n):
+    leg, trig, w = exp_rule_tables(n)
+
+    def arr(name, a):
+        vals = ", ".join(fmt(("c", float(v))) for v in np.asarray(a).ravel())
+        return f"static __constant__ float {name}[{np.asarray(a).size}] = {{{vals}}};"
+    return [f"#if defined(SHS_NB) && SHS_NB == {n}",
+            arr(f"kExpLeg{n}", leg), arr(f"kExpTrig{n}", trig), arr(f"kExpW{n}", w),
+            "#endif"]
+
+
 def emit_quadrature(n):
     leg, trig, w = quadrature_tables(n)
 
@@ -609,9 +667,17 @@ def generate():
         A = ahat(n)
         if n >= QUAD_FROM:
             parts.extend(emit_quadrature(n)[0])
+        parts.extend(emit_exp_rule(n))
         parts.append(f"template <> struct SH<{n}> {{")
         parts.append(f"    static constexpr int K = {K};")
         parts.append(f"    static constexpr int NNZ_SYM = {len(C)};   // entries (i, j <= k)")
+        parts.append(f"    static constexpr int EZ = {2 * n};    // projected-exponential rule: Gauss-Legendre nodes")
+        parts.append(f"    static constexpr int EP = {4 * n};    // projected-exponential rule: uniform azimuths")
+        parts.append("#if defined(SHS_NB) && SHS_NB == " + str(n))
+        parts.append(f"    __device__ __forceinline__ static const float* eleg() {{ return kExpLeg{n}; }}")
+        parts.append(f"    __device__ __forceinline__ static const float* etrig() {{ return kExpTrig{n}; }}")
+        parts.append(f"    __device__ __forceinline__ static const float* ew() {{ return kExpW{n}; }}")
+        parts.append("#endif")
         parts.append("    __device__ __forceinline__ static float norm(int i) {")
         parts.append("        switch (i) {")
         for i, v in enumerate(N):

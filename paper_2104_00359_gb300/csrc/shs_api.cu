@@ -153,6 +153,9 @@ shs_status check_config(const shs_config* c) {
         return fail(SHS_ERR_UNSUPPORTED, "tensor-core precisions need n_bands = 8");
     if (c->deterministic != 0 && c->deterministic != 1) return fail(SHS_ERR_INVALID_ARG, "deterministic must be 0 or 1");
     if (c->horizon_cull != 0 && c->horizon_cull != 1) return fail(SHS_ERR_INVALID_ARG, "horizon_cull must be 0 or 1");
+    if (c->exp_mode != 0 && c->exp_mode != 1) return fail(SHS_ERR_INVALID_ARG, "exp_mode must be 0 or 1");
+    if (c->exp_mode == 1 && c->precision != SHS_FP32)
+        return fail(SHS_ERR_UNSUPPORTED, "the projected exponential runs in SHS_FP32 only");
     return SHS_OK;
 }
 
@@ -167,6 +170,7 @@ SceneView view_of(const shs_scene_s* s) {
     v.kmax = s->cfg.exp_kmax;
     v.fixed_k = s->cfg.fixed_k;
     v.horizon_cull = s->cfg.horizon_cull;
+    v.exp_mode = s->cfg.exp_mode;
     v.status = s->status;
     return v;
 }
@@ -358,6 +362,7 @@ shs_status shs_config_default(shs_config* cfg) {
     cfg->precision = SHS_FP32;
     cfg->deterministic = 1;
     cfg->horizon_cull = 0;
+    cfg->exp_mode = 0;
     return SHS_OK;
 }
 

@@ -26,6 +26,7 @@ struct SceneView {
     int kmax;
     int fixed_k;
     int horizon_cull;        // 1: drop spheres below the tangent plane, per point
+    int exp_mode;            // 0: scaling + optimal linear step + squarings; 1: projected exponential
     int* status;             // device status word
 };
 

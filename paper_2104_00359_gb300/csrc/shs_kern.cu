@@ -484,6 +484,119 @@ __device__ __forceinline__ void sh_sqr(const float* a, float* o) {
 #endif
 }
 
+// Projected-exponential variant of the SH exponential: V = e0 P_n[exp(f^)],
+// e0 = exp(f_0 y_0), f^ = f without its constant term, by the variant's rule
+// (2n Gauss-Legendre nodes in cos(theta) x 4n azimuths, separable as above):
+// per latitude the azimuthal coefficients of f^, its value and exp at each
+// azimuth, accumulated against the harmonics, projected with the weight.
+// U = P_n[exp(f^)] is returned too (the adjoint needs it).
+// Inline up to 6 bands (an out-of-line call puts its operand arrays on the
+// stack of every kernel that can take this path); out of line above.
+#if SHS_NB <= 6
+#define SHS_PROJEXP_INLINE __forceinline__
+#else
+#define SHS_PROJEXP_INLINE __noinline__
+#endif
+__device__ SHS_PROJEXP_INLINE void proj_exp(const float* __restrict__ f, float* __restrict__ V,
+                                            float* __restrict__ U) {
+    constexpr int EZ = SH::EZ, EP = SH::EP, QF = 2 * NB - 1;
+    const float* leg = SH::eleg();
+    const float* trig = SH::etrig();
+    const float* qw = SH::ew();
+    float F[K], O[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        F[i] = f[i];
+        O[i] = 0.f;
+    }
+#pragma unroll 1
+    for (int za = 0; za < EZ; ++za) {
+        float c[QF], d[QF];
+#pragma unroll
+        for (int q = 0; q < QF; ++q) {
+            c[q] = 0.f;
+            d[q] = 0.f;
+        }
+#pragma unroll
+        for (int i = 1; i < K; ++i) c[harm_of(i)] = fmaf(F[i], leg[za * K + i], c[harm_of(i)]);
+#pragma unroll 1
+        for (int pb = 0; pb < EP; ++pb) {
+            const float* T = trig + pb * QF;
+            float v = 0.f;
+#pragma unroll
+            for (int q = 0; q < QF; ++q) v = fmaf(c[q], T[q], v);
+            const float E = expf(v);
+#pragma unroll
+            for (int q = 0; q < QF; ++q) d[q] = fmaf(E, T[q], d[q]);
+        }
+        const float w = qw[za];
+#pragma unroll
+        for (int i = 0; i < K; ++i) O[i] = fmaf(w * leg[za * K + i], d[harm_of(i)], O[i]);
+    }
+    const float e0 = expf(F[0] * kInvSqrt4Pi);
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        U[i] = O[i];
+        V[i] = e0 * O[i];
+    }
+}
+
+// Adjoint of proj_exp: df from dV.  df_0 = y_0 e0 (dV . U); for j >= 1,
+// df_j = e0 sum_q w_q exp(f^_q) (sum_i dV_i y_i(q)) y_j(q).
+__device__ SHS_PROJEXP_INLINE void proj_exp_adjoint(const float* __restrict__ f, const float* __restrict__ U,
+                                                    const float* __restrict__ dV, float* __restrict__ df) {
+    constexpr int EZ = SH::EZ, EP = SH::EP, QF = 2 * NB - 1;
+    const float* leg = SH::eleg();
+    const float* trig = SH::etrig();
+    const float* qw = SH::ew();
+    float F[K], G[K], O[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        F[i] = f[i];
+        G[i] = dV[i];
+        O[i] = 0.f;
+    }
+#pragma unroll 1
+    for (int za = 0; za < EZ; ++za) {
+        float c[QF], g[QF], d[QF];
+#pragma unroll
+        for (int q = 0; q < QF; ++q) {
+            c[q] = 0.f;
+            g[q] = 0.f;
+            d[q] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const float L = leg[za * K + i];
+            if (i > 0) c[harm_of(i)] = fmaf(F[i], L, c[harm_of(i)]);
+            g[harm_of(i)] = fmaf(G[i], L, g[harm_of(i)]);
+        }
+#pragma unroll 1
+        for (int pb = 0; pb < EP; ++pb) {
+            const float* T = trig + pb * QF;
+            float v = 0.f, dv = 0.f;
+#pragma unroll
+            for (int q = 0; q < QF; ++q) {
+                v = fmaf(c[q], T[q], v);
+                dv = fmaf(g[q], T[q], dv);
+            }
+            const float p = expf(v) * dv;
+#pragma unroll
+            for (int q = 0; q < QF; ++q) d[q] = fmaf(p, T[q], d[q]);
+        }
+        const float w = qw[za];
+#pragma unroll
+        for (int i = 1; i < K; ++i) O[i] = fmaf(w * leg[za * K + i], d[harm_of(i)], O[i]);
+    }
+    const float e0 = expf(F[0] * kInvSqrt4Pi);
+    float de0 = 0.f;
+#pragma unroll
+    for (int i = 0; i < K; ++i) de0 = fmaf(G[i], U[i], de0);
+    df[0] = de0 * e0 * kInvSqrt4Pi;
+#pragma unroll
+    for (int i = 1; i < K; ++i) df[i] = e0 * O[i];
+}
+
 // Clamped-cosine SH for a (not necessarily unit) normal; also returns the unit
 // normal and 1/|n| for the adjoint.
 __device__ __forceinline__ void cosine_lobe(float nx, float ny, float nz, float* H, float& ux,
@@ -573,26 +686,32 @@ __device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_
         for (int i = 0; i < K; ++i) a.saved_f[i * a.n_points + p] = f[i];
         return;
     }
-    float nrm2 = 0.f;
-#pragma unroll
-    for (int i = 1; i < K; ++i) nrm2 = fmaf(f[i], f[i], nrm2);
-    const int k = scaling_k(a.sc, nrm2);
-    const float scale = ldexpf(1.f, -k);
-    const float a0 = expf(nrm2 * scale * scale * kInv8Pi);
-    float S[K];
-    S[0] = a0 * kSqrt4Pi;
-#pragma unroll
-    for (int i = 1; i < K; ++i) S[i] = a0 * (f[i] * scale);
-    for (int t = 0; t < k; ++t) {
-        float T[K];
-        sh_sqr(S, T);
-#pragma unroll
-        for (int i = 0; i < K; ++i) S[i] = T[i];
-    }
-    const float e0 = expf(f[0] * kInvSqrt4Pi);
     float V[K];
+    int k = 0;
+    if (a.sc.exp_mode == 1) {
+        float U[K];
+        proj_exp(f, V, U);
+    } else {
+        float nrm2 = 0.f;
 #pragma unroll
-    for (int i = 0; i < K; ++i) V[i] = e0 * S[i];
+        for (int i = 1; i < K; ++i) nrm2 = fmaf(f[i], f[i], nrm2);
+        k = scaling_k(a.sc, nrm2);
+        const float scale = ldexpf(1.f, -k);
+        const float a0 = expf(nrm2 * scale * scale * kInv8Pi);
+        float S[K];
+        S[0] = a0 * kSqrt4Pi;
+#pragma unroll
+        for (int i = 1; i < K; ++i) S[i] = a0 * (f[i] * scale);
+        for (int t = 0; t < k; ++t) {
+            float T[K];
+            sh_sqr(S, T);
+#pragma unroll
+            for (int i = 0; i < K; ++i) S[i] = T[i];
+        }
+        const float e0 = expf(f[0] * kInvSqrt4Pi);
+#pragma unroll
+        for (int i = 0; i < K; ++i) V[i] = e0 * S[i];
+    }
 
     float H[K], ux, uy, uz, il;
     cosine_lobe(__ldg(a.normals + 3 * p), __ldg(a.normals + 3 * p + 1), __ldg(a.normals + 3 * p + 2),
@@ -976,8 +1095,9 @@ __device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v
 // Adjoint of one 128-point tile of one request: per-point outputs are written,
 // the scene-level sums are added to the block's shared accumulators
 // (s_dl: d_light and loss per warp, s_acc: per warp and sphere).
-// CULLM: horizon culling off (0), on (1), or read from the scene per call (2).
-template <bool PAIRS = true, int CULLM = 2>
+// CULLM: horizon culling off (0), on (1), or read from the scene per call (2);
+// EXPM: the same for the projected-exponential variant.
+template <bool PAIRS = true, int CULLM = 2, int EXPM = 2>
 __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_sph, const float* s_light,
                                               float* s_acc, float (*s_dl)[3 * K + 1], int64_t tile,
                                               int lane, int warp) {
@@ -1018,30 +1138,35 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_
     if (k < 0) k = scaling_k(a.sc, nrm2);
 
     // ---- recompute the exponential, keeping the operand of every squaring
-    const float scale = ldexpf(1.f, -k);
-    const float a0 = expf(nrm2 * scale * scale * kInv8Pi);
-    float g[K];
-    g[0] = 0.f;
-#pragma unroll
-    for (int i = 1; i < K; ++i) g[i] = f[i] * scale;
-    float S[K];
-    S[0] = a0 * kSqrt4Pi;
-#pragma unroll
-    for (int i = 1; i < K; ++i) S[i] = a0 * g[i];
+    // (or, for the projected-exponential variant, U = P_n[exp(f^)])
+    const bool projexp = EXPM == 2 ? a.sc.exp_mode == 1 : EXPM == 1;
+    float scale = 1.f, a0 = 1.f, e0 = 1.f;
+    float g[K], S[K], V[K], U[K];
     float hist[kMaxK][K];
-    for (int t = 0; t < k; ++t) {
-        float T[K];
-        sh_sqr(S, T);
+    if (projexp) {
+        proj_exp(f, V, U);
+    } else {
+        scale = ldexpf(1.f, -k);
+        a0 = expf(nrm2 * scale * scale * kInv8Pi);
+        g[0] = 0.f;
 #pragma unroll
-        for (int i = 0; i < K; ++i) {
-            hist[t][i] = S[i];
-            S[i] = T[i];
+        for (int i = 1; i < K; ++i) g[i] = f[i] * scale;
+        S[0] = a0 * kSqrt4Pi;
+#pragma unroll
+        for (int i = 1; i < K; ++i) S[i] = a0 * g[i];
+        for (int t = 0; t < k; ++t) {
+            float T[K];
+            sh_sqr(S, T);
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                hist[t][i] = S[i];
+                S[i] = T[i];
+            }
         }
-    }
-    const float e0 = expf(f[0] * kInvSqrt4Pi);
-    float V[K];
+        e0 = expf(f[0] * kInvSqrt4Pi);
 #pragma unroll
-    for (int i = 0; i < K; ++i) V[i] = e0 * S[i];
+        for (int i = 0; i < K; ++i) V[i] = e0 * S[i];
+    }
     float H[K], ux, uy, uz, il;
     cosine_lobe(load_or(a.normals, 3 * q, live), load_or(a.normals, 3 * q + 1, live),
                 load_or(a.normals, 3 * q + 2, live), H, ux, uy, uz, il);
@@ -1108,27 +1233,31 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_
     }
 
     // ---- exponential adjoint
-    float de0 = 0.f, dS[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-        de0 = fmaf(dV[i], S[i], de0);
-        dS[i] = e0 * dV[i];
-    }
-    for (int t = k - 1; t >= 0; --t) {
-        float Ht[K], T[K];
-#pragma unroll
-        for (int i = 0; i < K; ++i) Ht[i] = hist[t][i];
-        sh_mul(dS, Ht, T);
-#pragma unroll
-        for (int i = 0; i < K; ++i) dS[i] = 2.f * T[i];
-    }
-    float da = dS[0] * kSqrt4Pi;
-#pragma unroll
-    for (int i = 1; i < K; ++i) da = fmaf(dS[i], g[i], da);
     float dfp[K];
-    dfp[0] = de0 * e0 * kInvSqrt4Pi;
+    if (projexp) {
+        proj_exp_adjoint(f, U, dV, dfp);
+    } else {
+        float de0 = 0.f, dS[K];
 #pragma unroll
-    for (int i = 1; i < K; ++i) dfp[i] = fmaf(a0, dS[i], da * a0 * kInv4Pi * g[i]) * scale;
+        for (int i = 0; i < K; ++i) {
+            de0 = fmaf(dV[i], S[i], de0);
+            dS[i] = e0 * dV[i];
+        }
+        for (int t = k - 1; t >= 0; --t) {
+            float Ht[K], T[K];
+#pragma unroll
+            for (int i = 0; i < K; ++i) Ht[i] = hist[t][i];
+            sh_mul(dS, Ht, T);
+#pragma unroll
+            for (int i = 0; i < K; ++i) dS[i] = 2.f * T[i];
+        }
+        float da = dS[0] * kSqrt4Pi;
+#pragma unroll
+        for (int i = 1; i < K; ++i) da = fmaf(dS[i], g[i], da);
+        dfp[0] = de0 * e0 * kInvSqrt4Pi;
+#pragma unroll
+        for (int i = 1; i < K; ++i) dfp[i] = fmaf(a0, dS[i], da * a0 * kInv4Pi * g[i]) * scale;
+    }
 #pragma unroll
     for (int i = 0; i < K; ++i) dfp[i] *= a.sc.neg_2pi_eps * SH::norm(i);
 
@@ -1237,7 +1366,7 @@ __device__ void finish_scene_sums(const BwdArgs& a, int E) {
 //   [3K+1, 3K+1+4N)  per sphere (d cx, d cy, d cz, d r)
 // Up to 4 bands: four resident blocks per SM (<= 128 registers per thread) for
 // the pair loop; above that the tail state needs the registers.
-template <bool PAIRS, int CULLM>
+template <bool PAIRS, int CULLM, int EXPM>
 __global__ void __launch_bounds__(kBlock, NB <= 4 ? SHS_BWD_MINB : 1) backward_kernel_t(BwdArgs a) {
     extern __shared__ __align__(16) float4 dyn[];
     __shared__ __align__(16) float s_light[3 * KPAD];
@@ -1256,7 +1385,7 @@ __global__ void __launch_bounds__(kBlock, NB <= 4 ? SHS_BWD_MINB : 1) backward_k
 
     const int64_t ntiles = (a.n_points + kBlock - 1) / kBlock;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-        backward_tile<PAIRS, CULLM>(a, s_sph, s_light, s_acc, s_dl, tile, lane, warp);
+        backward_tile<PAIRS, CULLM, EXPM>(a, s_sph, s_light, s_acc, s_dl, tile, lane, warp);
 
     // ---- block reduction, then one scene-level reduction
     __syncthreads();
@@ -1587,10 +1716,10 @@ size_t backward_dyn_smem(int n_spheres) {
 
 template <>
 int backward_blocks_per_sm<NB>(int n_spheres) {
-    cudaFuncSetAttribute(backward_kernel_t<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(backward_kernel_t<true, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(backward_dyn_smem(kMaxSpheres)));
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, backward_kernel_t<true, 0>, kBlock,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, backward_kernel_t<true, 0, 0>, kBlock,
                                                       backward_dyn_smem(n_spheres)) != cudaSuccess || nb < 1)
         nb = 1;
     return nb;
@@ -1702,19 +1831,19 @@ cudaError_t launch_backward<NB>(const BwdArgs& a, cudaStream_t s) {
     const size_t smem = backward_dyn_smem(a.sc.n_spheres);
     static const cudaError_t attr = [] {
         const int bytes = static_cast<int>(backward_dyn_smem(kMaxSpheres));
-        cudaError_t e = cudaFuncSetAttribute(backward_kernel_t<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             bytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(backward_kernel_t<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(backward_kernel_t<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        cudaError_t e = cudaFuncSetAttribute(backward_kernel_t<true, 0, 0>, at, bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(backward_kernel_t<true, 1, 0>, at, bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(backward_kernel_t<true, 0, 1>, at, bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(backward_kernel_t<true, 1, 1>, at, bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(backward_kernel_t<false, 2, 2>, at, bytes);
         return e;
     }();
     cudaError_t err = attr;
     if (err != cudaSuccess) return err;
     if (a.dfp_ws) {
         // split backward: tail pass (per point), then the pair pass (per sphere lane)
-        backward_kernel_t<false, 2><<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
+        backward_kernel_t<false, 2, 2><<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
         count_launch();
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
@@ -1729,10 +1858,14 @@ cudaError_t launch_backward<NB>(const BwdArgs& a, cudaStream_t s) {
             err = cudaGetLastError();
         }
     } else {
-        if (a.sc.horizon_cull)
-            backward_kernel_t<true, 1><<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
-        else
-            backward_kernel_t<true, 0><<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
+        const dim3 grid(static_cast<unsigned>(a.grid));
+        if (a.sc.exp_mode == 1) {
+            if (a.sc.horizon_cull) backward_kernel_t<true, 1, 1><<<grid, kBlock, smem, s>>>(a);
+            else backward_kernel_t<true, 0, 1><<<grid, kBlock, smem, s>>>(a);
+        } else {
+            if (a.sc.horizon_cull) backward_kernel_t<true, 1, 0><<<grid, kBlock, smem, s>>>(a);
+            else backward_kernel_t<true, 0, 0><<<grid, kBlock, smem, s>>>(a);
+        }
         count_launch();
         err = cudaGetLastError();
     }

@@ -131,6 +131,7 @@ extern "C" shs_status shs_shade_backward_noalloc(
     a.sc.kmax = cfg->exp_kmax;
     a.sc.fixed_k = cfg->fixed_k;
     a.sc.horizon_cull = cfg->horizon_cull;
+    a.sc.exp_mode = cfg->exp_mode;
     a.sc.status = status;
     a.n_points = n_points;
     a.points = points;

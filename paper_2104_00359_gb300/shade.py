@@ -30,11 +30,12 @@ class Config:
     precision: int = _lib.SHS_FP32
     deterministic: bool = True
     horizon_cull: bool = False
+    exp_mode: int = 0          # 0: scaling + squarings (Sec. 3.3.2); 1: projected exponential
 
     def to_c(self):
         return ShsConfig(int(self.n_bands), float(self.epsilon), float(self.exp_tau), int(self.exp_kmax),
                          int(self.fixed_k), int(self.precision), int(bool(self.deterministic)),
-                         int(bool(self.horizon_cull)))
+                         int(bool(self.horizon_cull)), int(self.exp_mode))
 
 
 def _stream():

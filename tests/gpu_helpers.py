@@ -55,7 +55,8 @@ def gpu_run(sc, cfg, dB=None, want=None, saved=True, l2_target=None):
                   Config(n_bands=cfg.n_bands, epsilon=cfg.epsilon, exp_tau=cfg.exp_tau,
                          exp_kmax=cfg.exp_kmax, fixed_k=cfg.fixed_k,
                          deterministic=getattr(cfg, "deterministic", True),
-                         horizon_cull=getattr(cfg, "horizon_cull", False)))
+                         horizon_cull=getattr(cfg, "horizon_cull", False),
+                         exp_mode=getattr(cfg, "exp_mode", 0)))
     P = sc["points"].shape[0]
     K = cfg.n_bands ** 2
     sv = scene.new_saved(P, dev)
