@@ -250,6 +250,42 @@ size_t shs_envmap_workspace_bytes(int32_t height, int32_t width, int32_t n_bands
 shs_status shs_project_envmap(const float* env, int32_t height, int32_t width, int32_t n_bands, float* light,
                               void* workspace, size_t workspace_bytes, void* stream);
 
+/* Rasterisation of shaded vertices (the rendering step that follows Eq. 8:
+ * I_R = R(B(x_0), ..., B(x_n), P)), with its adjoint for image-space losses.
+ *   vertices: [V][3] float32 world positions, radiance: [V][3] float32 (e.g.
+ *     shs_shade's output at the vertices), faces: [F][3] int32 vertex indices
+ *     (device memory; a face with an index outside [0, V) is skipped).
+ *   proj: 16 float32 in HOST memory, the row-major 4 x 4 matrix taking
+ *     [x, y, z, 1] to clip coordinates (camera intrinsics and extrinsics).
+ *   image: [height][width][3] float32 device output; face_index: [height][width]
+ *     int32 device output, the triangle shown at each pixel or -1.
+ *   workspace: 256-byte aligned device scratch of at least
+ *     shs_raster_workspace_bytes(V, height, width) bytes, owned by the caller;
+ *     calls that may overlap on the device need separate workspaces.
+ * Pixel (r, c) samples NDC x = -1 + (2c + 1) / width, y = 1 - (2r + 1) / height
+ * (row 0 at the top).  A pixel shows the triangle containing its centre
+ * (either winding) with the smallest NDC depth in [-1, 1], ties to the lower
+ * face index; triangles with a vertex at clip w <= 0 are not drawn (no
+ * near-plane clipping).  Colours are perspective-correct interpolations of the
+ * vertex radiance; uncovered pixels are 0.  Each triangle's thread walks its
+ * pixel bounding box, so screen-filling triangles are slow.  1 <= height,
+ * width <= 16384.  Asynchronous on `stream`. */
+size_t shs_raster_workspace_bytes(int32_t n_vertices, int32_t height, int32_t width);
+shs_status shs_rasterize(const float* vertices, int32_t n_vertices, const int32_t* faces, int32_t n_faces,
+                         const float* proj, const float* radiance, int32_t height, int32_t width, float* image,
+                         int32_t* face_index, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Gradients of sum(d_image * I_R) for the face_index of a shs_rasterize call
+ * with the same mesh, projection and size: d_radiance [V][3] (exact) and
+ * d_vertices [V][3] (through the barycentrics, each pixel's triangle held
+ * fixed: visibility changes carry no gradient); both are overwritten, either
+ * may be NULL.  Accumulated with atomics: rounding varies between runs. */
+shs_status shs_rasterize_backward(const float* vertices, int32_t n_vertices, const int32_t* faces,
+                                  int32_t n_faces, const float* proj, const float* radiance, int32_t height,
+                                  int32_t width, const int32_t* face_index, const float* d_image,
+                                  float* d_radiance, float* d_vertices, void* workspace, size_t workspace_bytes,
+                                  void* stream);
+
 /* Diagnostic: one CTA computes D = A B^T with M = 128 rows, n columns and
  * inner size k on the tensor cores (tcgen05, BF16 operands, FP32 accumulation
  * in tensor memory); split != 0 uses split precision (each operand as the sum

@@ -70,6 +70,12 @@ _SIGS = {
     "shs_shade_batch": (c_int32, [c_void_p, POINTER(ShsRequest), c_int32, c_void_p]),
     "shs_envmap_workspace_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
     "shs_project_envmap": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "shs_raster_workspace_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
+    "shs_rasterize": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_int32,
+                                c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "shs_rasterize_backward": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
+                                         c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
+                                         c_void_p]),
     "shs_tc_gemm_selftest": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p,
                                        c_void_p]),
     "shs_scene_device_status": (c_int32, [c_void_p, c_void_p, POINTER(c_int32)]),

@@ -36,6 +36,8 @@ __all__ = [
     "serving_job",
     "mesh_deformation_scene",
     "environment_map",
+    "uv_grid_faces",
+    "look_at_perspective",
 ]
 
 
@@ -363,3 +365,37 @@ def environment_map(seed=5, height=1024, width=2048, n_suns=2):
         env = env + disc[..., None] * rng.uniform(20.0, 60.0) * rng.uniform(0.8, 1.0, 3)[None, None]
     env = env * rng.uniform(0.95, 1.05, size=env.shape)
     return _f32(env)
+
+
+def uv_grid_faces(n_theta, n_phi):
+    """Triangles [F, 3] int32 of the n_theta x n_phi vertex grid of
+    mesh_deformation_scene (vertex index t * n_phi + p): two per grid cell,
+    wrapping around in phi, none across the poles."""
+    f = []
+    for t in range(n_theta - 1):
+        for p in range(n_phi):
+            a, b = t * n_phi + p, t * n_phi + (p + 1) % n_phi
+            c, d = a + n_phi, b + n_phi
+            f.append((a, c, b))
+            f.append((b, c, d))
+    return np.asarray(f, dtype=np.int32)
+
+
+def look_at_perspective(eye, target=(0.0, 0.0, 0.0), up=(0.0, 0.0, 1.0), fov_deg=45.0, aspect=1.0,
+                        near=0.1, far=20.0):
+    """Row-major 4x4 matrix taking world [x, y, z, 1] to clip coordinates: a
+    camera at ``eye`` looking at ``target`` (OpenGL-style perspective, visible
+    depth mapped to NDC z in [-1, 1])."""
+    eye, target, up = (np.asarray(v, np.float64) for v in (eye, target, up))
+    f = target - eye
+    f /= np.linalg.norm(f)
+    s_ = np.cross(f, up)
+    s_ /= np.linalg.norm(s_)
+    u = np.cross(s_, f)
+    view = np.eye(4)
+    view[0, :3], view[1, :3], view[2, :3] = s_, u, -f
+    view[:3, 3] = -view[:3, :3] @ eye
+    t = 1.0 / np.tan(np.deg2rad(fov_deg) / 2)
+    proj = np.array([[t / aspect, 0, 0, 0], [0, t, 0, 0],
+                     [0, 0, (far + near) / (near - far), 2 * far * near / (near - far)], [0, 0, -1, 0]])
+    return _f32(proj @ view)
