@@ -290,6 +290,7 @@ def bench_ours(args, world, rank, local, dist):
     status = scene.device_status()
     scene.close()
     peaks = load_peaks()
+    fma_peak = measure_fma_peak(lib, dev, stream)
     return dict(
         metric=METRIC, value=value, unit="pairs/s", n_gpus=world, steps=K, warmup=W,
         ms_per_step=mean_ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
@@ -306,6 +307,8 @@ def bench_ours(args, world, rank, local, dist):
                   "kernel_source_hash": kernel_source_hash(),
                   "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                   "flops_per_point": fm["bwd"], "k_mean": k_mean,
+                  "peak_measured": fma_peak, "frac_of_measured": achieved / fma_peak if fma_peak else None,
+                  "peak_measured_source": "shs_fp32_fma_probe: 1216 x 256 threads x 8 FMA chains, CUDA events",
                   "forward": {"achieved": achieved_fwd, "frac": achieved_fwd / peak,
                               "flops_per_point": fm["fwd"]}},
         e2e={"value": world * pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
@@ -315,6 +318,25 @@ def bench_ours(args, world, rank, local, dist):
         wall_s_timed=t1 - t0, hbm_peak_gbs=peaks.get("hbm_gbs"),
         cpu_baseline=cpu_baseline(args) if (rank == 0 and world == 1 and not args.no_cpu) else None,
     )
+
+
+def measure_fma_peak(lib, dev, stream, iters=1 << 16, blocks=152 * 8):
+    """FP32 FMA throughput (TFLOP/s) of the library's probe kernel: best of 3."""
+    import ctypes
+    import torch
+    from paper_2104_00359_gb300 import _lib
+    out = torch.empty(blocks * 256, device=dev)
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    best = None
+    for _ in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _lib.check(lib.shs_fp32_fma_probe(blocks, iters, _lib.ptr(out), sptr), "shs_fp32_fma_probe")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return 16.0 * iters * blocks * 256 / (best * 1e-3) / 1e12
 
 
 def _oracle_step(O, cfg, sc, idx, dB_seed=0):

@@ -286,6 +286,14 @@ shs_status shs_rasterize_backward(const float* vertices, int32_t n_vertices, con
                                   float* d_radiance, float* d_vertices, void* workspace, size_t workspace_bytes,
                                   void* stream);
 
+/* Diagnostic: FP32 FMA throughput probe.  Launches `blocks` blocks of 256
+ * threads; each thread runs 8 independent fused multiply-add chains of
+ * `iters` steps (16 iters flops per thread) and writes one float to
+ * out[blocks * 256] (device).  Timing it gives the measured FP32 peak that
+ * the CUDA-core kernels' roofline fractions are compared with (the paper has
+ * no counterpart; this is instrumentation). */
+shs_status shs_fp32_fma_probe(int32_t blocks, int64_t iters, float* out, void* stream);
+
 /* Diagnostic: one CTA computes D = A B^T with M = 128 rows, n columns and
  * inner size k on the tensor cores (tcgen05, BF16 operands, FP32 accumulation
  * in tensor memory); split != 0 uses split precision (each operand as the sum

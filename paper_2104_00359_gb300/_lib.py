@@ -76,6 +76,7 @@ _SIGS = {
     "shs_rasterize_backward": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
                                          c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
                                          c_void_p]),
+    "shs_fp32_fma_probe": (c_int32, [c_int32, c_int64, c_void_p, c_void_p]),
     "shs_tc_gemm_selftest": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p,
                                        c_void_p]),
     "shs_scene_device_status": (c_int32, [c_void_p, c_void_p, POINTER(c_int32)]),
