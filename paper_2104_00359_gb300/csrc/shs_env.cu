@@ -89,8 +89,16 @@ __device__ __forceinline__ void add_pixel(float v0, float v1, float v2, float c1
     }
 }
 
+#ifndef SHS_ENV_MINB
+#define SHS_ENV_MINB 1
+#endif
+#ifndef SHS_ENV_UNROLL
+#define SHS_ENV_UNROLL 2
+#endif
+constexpr int kEnvUnroll = SHS_ENV_UNROLL;
+
 template <int NB>
-__global__ void __launch_bounds__(kEnvBlock) envmap_rows_kernel(const __grid_constant__ EnvArgs a) {
+__global__ void __launch_bounds__(kEnvBlock, SHS_ENV_MINB) envmap_rows_kernel(const __grid_constant__ EnvArgs a) {
     constexpr int K = NB * NB, NF = 2 * NB - 1, NV = 3 * NF, NOWN = (3 * K + kEnvBlock - 1) / kEnvBlock;
     __shared__ float s_red[kEnvBlock / 32][NV];
     __shared__ float s_row[NV];
@@ -114,7 +122,7 @@ __global__ void __launch_bounds__(kEnvBlock) envmap_rows_kernel(const __grid_con
             const float4* row4 = reinterpret_cast<const float4*>(row);
             const float4* trig4 = reinterpret_cast<const float4*>(a.trig);
             const int groups = a.W >> 2;
-#pragma unroll 2
+#pragma unroll kEnvUnroll
             for (int g = tid; g < groups; g += kEnvBlock) {
                 const float4 q0 = __ldcs(row4 + 3 * g), q1 = __ldcs(row4 + 3 * g + 1), q2 = __ldcs(row4 + 3 * g + 2);
                 const float4 t0 = __ldg(trig4 + 2 * g), t1 = __ldg(trig4 + 2 * g + 1);
