@@ -71,6 +71,7 @@ class Config:
     horizon_cull: bool = False
     exp_mode: int = 0          # 0: scaling + optimal linear + squarings; 1: projected exponential
     exp_rule: tuple | None = None   # (n_theta, n_phi) of the projected exponential; None: (2n, 4n)
+    ol_table: tuple | None = None   # exp_mode 2: (a [M], b [M], s_max), a(s), b(s) on s_m = m s_max / (M-1)
 
 
 def sh_index(l, m):
@@ -301,6 +302,30 @@ def exp_scaling_k(cfg, f):
     return k
 
 
+def ol_coefficients(cfg, s):
+    """Optimal-linear coefficients a(s), b(s) and their derivatives at the
+    norms s of the scaled exponents.  exp_mode 0/1: the Gaussian reading
+    a = b = exp(s^2 / 8 pi).  exp_mode 2: a fitted table, linear between its
+    nodes s_m = m s_max / (M - 1) and constant beyond s_max."""
+    s = np.asarray(s, np.float64)
+    if cfg.exp_mode != 2:
+        a = np.exp(s * s / (2.0 * FOUR_PI))
+        return a, a.copy(), a * s / FOUR_PI, a * s / FOUR_PI
+    ta, tb, s_max = cfg.ol_table
+    ta, tb = np.asarray(ta, np.float64), np.asarray(tb, np.float64)
+    M = ta.shape[0]
+    h = s_max / (M - 1)
+    x = np.clip(s / h, 0.0, M - 1.0)
+    i = np.minimum(np.floor(x).astype(np.int64), M - 2)
+    t = x - i
+    a = ta[i] + t * (ta[i + 1] - ta[i])
+    b = tb[i] + t * (tb[i + 1] - tb[i])
+    inside = s < s_max
+    da = np.where(inside, (ta[i + 1] - ta[i]) / h, 0.0)
+    db = np.where(inside, (tb[i + 1] - tb[i]) / h, 0.0)
+    return a, b, da, db
+
+
 def sh_exp(cfg, C, f, k=None):
     """V = exp*(f) with the steps of the module header.  Returns V and the
     per-point intermediates the adjoint needs."""
@@ -314,9 +339,9 @@ def sh_exp(cfg, C, f, k=None):
     fh = f.copy()
     fh[:, 0] = 0.0
     g = fh / (2.0 ** k)[:, None]
-    gg = np.sum(g * g, axis=-1)
-    a = np.exp(gg / (2.0 * FOUR_PI))
-    S = a[:, None] * g
+    sn = np.sqrt(np.sum(g * g, axis=-1))
+    a, b, da_ds, db_ds = ol_coefficients(cfg, sn)
+    S = b[:, None] * g
     S[:, 0] = a * SQRT_FOUR_PI
     levels = [S]
     for t in range(int(k.max()) if P else 0):
@@ -324,7 +349,7 @@ def sh_exp(cfg, C, f, k=None):
         S = np.where(act, sh_product(C, S, S), S)
         levels.append(S)
     V = e0[:, None] * S
-    return V, dict(k=k, e0=e0, g=g, a=a, levels=levels)
+    return V, dict(k=k, e0=e0, g=g, a=a, b=b, da_ds=da_ds, db_ds=db_ds, s=sn, levels=levels)
 
 
 def projected_exp_rule(n_bands):
@@ -433,11 +458,12 @@ def _sh_exp_adjoint(C, ex, dV):
         act = (k_pt > t)[:, None]
         back = 2.0 * np.einsum("ijk,pi,pk->pj", C, dS, levels[t], optimize=True)
         dS = np.where(act, back, dS)
-    base = g.copy()
-    base[:, 0] = SQRT_FOUR_PI
-    da = np.sum(dS * base, axis=-1)
-    dg = a[:, None] * dS
-    dg += (da * a / FOUR_PI)[:, None] * g          # d a / d g = a g / (4 pi)
+    # S_0 = a(s) sqrt(4 pi), S_i = b(s) g_i (i >= 1), s = |g|
+    b, da_ds, db_ds, sn = ex["b"], ex["da_ds"], ex["db_ds"], ex["s"]
+    dA = dS[:, 0] * SQRT_FOUR_PI
+    dB = np.sum(dS[:, 1:] * g[:, 1:], axis=-1)
+    coef = np.where(sn > 0, (dA * da_ds + dB * db_ds) / np.where(sn > 0, sn, 1.0), 0.0)
+    dg = b[:, None] * dS + coef[:, None] * g
     dg[:, 0] = 0.0
     df = dg / (2.0 ** k_pt)[:, None]
     df[:, 0] = de0 * e0 / SQRT_FOUR_PI

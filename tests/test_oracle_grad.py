@@ -131,3 +131,32 @@ def test_adjoint_of_projected_exponential():
                                    - O.shade_forward(cfg, *[m[k] for k in ORDER])["radiance"])) / (2 * h)
         scale = max(np.abs(fd).max(), 1e-3)
         np.testing.assert_allclose(grads[name], fd, atol=2e-7 * scale + 1e-9, err_msg=name)
+
+
+def test_adjoint_of_fitted_table_step():
+    """exp_mode 2 with the stored fitted table: adjoint against central
+    differences (through a(s), b(s) and their slopes)."""
+    import os
+    from oracle import fit_ol_table as F
+    tab = F.read_table(os.path.join(os.path.dirname(__file__), "golden", "ol_table_n4.txt"))
+    sc = _scene(48, 8, 5, 4)
+    cfg = O.Config(n_bands=4, exp_mode=2, ol_table=tab)
+    dB = np.random.default_rng(49).normal(size=sc["points"].shape)
+    g = O.shade_backward(cfg, *[sc[k] for k in ORDER], dB)
+    grads = dict(points=g["d_points"], normals=g["d_normals"], albedo=g["d_albedo"],
+                 centers=g["d_centers"], radii=g["d_radii"], light=g["d_light"])
+    h = 1e-6
+    for name in ("centers", "radii", "points", "normals", "light"):
+        base = sc[name]
+        fd = np.zeros_like(base)
+        it = np.nditer(base, flags=["multi_index"])
+        for _ in it:
+            idx = it.multi_index
+            p, m = dict(sc), dict(sc)
+            p[name], m[name] = base.copy(), base.copy()
+            p[name][idx] += h
+            m[name][idx] -= h
+            fd[idx] = np.sum(dB * (O.shade_forward(cfg, *[p[k] for k in ORDER])["radiance"]
+                                   - O.shade_forward(cfg, *[m[k] for k in ORDER])["radiance"])) / (2 * h)
+        scale = max(np.abs(fd).max(), 1e-3)
+        np.testing.assert_allclose(grads[name], fd, atol=2e-7 * scale + 1e-9, err_msg=name)

@@ -550,3 +550,77 @@ def test_projected_exp_rule_converges_to_the_projection():
     # the fine rule is itself converged: it agrees with a finer one
     Vff, _ = O.sh_exp_projected(n, f, rule=O.sphere_quadrature(96, 192))
     assert np.abs(Vff - Vf).max() < 1e-12 * np.abs(Vf).max()
+
+
+# --------------------------------------------------------------------------- fitted optimal linear table
+
+def test_gaussian_table_reduces_to_the_default_step():
+    """exp_mode 2 with a fine table of a = b = exp(s^2 / 8 pi) is the default
+    step up to piecewise-linear interpolation error (h^2 / 8 max|a''|)."""
+    n = 4
+    C = O.gaunt_tensor(n)
+    rng = np.random.default_rng(30)
+    f = rng.normal(0, 0.8, size=(50, 16))
+    s = np.linspace(0.0, 1.0, 4097)
+    a = np.exp(s * s / (8 * np.pi))
+    V0, _ = O.sh_exp(O.Config(n_bands=n), C, f)
+    V2, _ = O.sh_exp(O.Config(n_bands=n, exp_mode=2, ol_table=(a, a, 1.0)), C, f)
+    h = s[1]
+    bound = h * h / 8 * (1 / (4 * np.pi)) * np.exp(1 / (8 * np.pi)) * 3
+    assert np.abs(V2 - V0).max() <= 2 ** 6 * bound * np.abs(V0).max()
+
+
+def test_table_interpolation_and_clamp():
+    """The table is read as the library reads it: linear between nodes,
+    constant past s_max, with slopes zero there."""
+    cfg = O.Config(n_bands=2, exp_mode=2, ol_table=(np.array([1.0, 2.0, 4.0]), np.array([3.0, 1.0, 1.0]), 2.0))
+    a, b, da, db = O.ol_coefficients(cfg, np.array([0.0, 0.5, 1.0, 1.5, 2.0, 7.0]))
+    np.testing.assert_allclose(a, [1.0, 1.5, 2.0, 3.0, 4.0, 4.0])
+    np.testing.assert_allclose(b, [3.0, 2.0, 1.0, 1.0, 1.0, 1.0])
+    np.testing.assert_allclose(da, [1.0, 1.0, 2.0, 2.0, 0.0, 0.0])
+    np.testing.assert_allclose(db, [-2.0, -2.0, 0.0, 0.0, 0.0, 0.0])
+
+
+def test_fitted_table_is_a_stationary_point_of_its_objective():
+    """The fit on a small ensemble: it lowers the objective below the
+    Gaussian reading's, and no single node moves it lower (the regularised
+    cost is stationary)."""
+    from oracle import fit_ol_table as F
+    prob = F.Problem(4, F.ensemble(4, 120, seed=3), rule=O.sphere_quadrature(24, 48))
+    M, smax = 9, 1.0
+    a, b = F.fit(prob, M, smax)
+    ga, gb = F.gaussian_table(M, smax)
+    assert prob.objective(a, b, smax) < prob.objective(ga, gb, smax)
+    H = F.hat_basis(prob.s, M, smax)
+    D2 = np.diff(np.eye(M), 2, axis=0)
+    Reg = 1e-3 * np.eye(2 * M) + 1.0 * np.kron(np.eye(2), D2.T @ D2)
+    N = prob.g.shape[0]
+
+    def cost(a, b):
+        R = (prob.run(H @ a, H @ b) - prob.T) * np.sqrt(prob.w)[:, None]
+        d = np.concatenate([a - ga, b - gb])
+        return np.sum(R * R) + N * d @ Reg @ d
+
+    c0 = cost(a, b)
+    for m in range(2 * M):
+        for step in (1e-3, -1e-3):
+            aa, bb = a.copy(), b.copy()
+            (aa if m < M else bb)[m % M] += step
+            assert cost(aa, bb) >= c0 - 1e-9 * c0
+
+
+def test_stored_table_is_what_the_fit_script_writes():
+    """tests/golden/ol_table_n4.txt is reproduced by the committed script from
+    the oracle, and on a held-out ensemble it is no worse than the Gaussian
+    reading."""
+    import tempfile
+    from oracle import fit_ol_table as F
+    path = os.path.join(os.path.dirname(__file__), "golden", "ol_table_n4.txt")
+    a, b, smax = F.read_table(path)
+    prob = F.Problem(4, F.ensemble(4, 1500, 0))
+    fa, fb = F.fit(prob, a.shape[0], smax)
+    np.testing.assert_allclose(fa, a, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(fb, b, rtol=0, atol=1e-9)
+    ho = F.Problem(4, F.ensemble(4, 1500, 7))
+    ga, gb = F.gaussian_table(a.shape[0], smax)
+    assert ho.objective(a, b, smax) <= ho.objective(ga, gb, smax)
