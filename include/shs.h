@@ -86,8 +86,13 @@ typedef struct {
                            /*    gradient through that selection)                          */
     int32_t exp_mode;      /* 0: the SH exponential by scaling, optimal linear step and    */
                            /*    squarings (Sec. 3.3.2);  1: projected exponential         */
-                           /*    P_n[exp(f)] by a 2n x 4n quadrature (FP32 precision only) */
+                           /*    P_n[exp(f)] by a 2n x 4n quadrature (FP32 precision only);*/
+                           /*    2: as 0, with the optimal linear coefficients a(s), b(s)  */
+                           /*    from a fitted table (shs_scene_set_ol_table)              */
 } shs_config;
+
+/* Largest node count of an optimal linear coefficient table. */
+#define SHS_OL_TABLE_MAX 4096
 
 /* Fills *cfg with n_bands=4, epsilon=3, exp_tau=1, exp_kmax=16, fixed_k=-1,
  * precision=SHS_FP32, deterministic=1, horizon_cull=0, exp_mode=0. */
@@ -108,6 +113,19 @@ shs_status shs_scene_create(const shs_config* cfg, int32_t n_spheres,
 /* Replaces centres, radii and/or lighting (NULL = unchanged) on `stream`. */
 shs_status shs_scene_update(shs_scene_t scene, const float* centers,
                             const float* radii, const float* light, void* stream);
+
+/* Optimal linear step of the SH exponential (Sec. 3.3.2, after Ren et al.'s
+ * scaling / squaring setting): with g the scaled exponent (zero DC) and
+ * s = |g| its coefficient norm, exp*(g) ~ a(s) sqrt(4 pi) e_0 + b(s) g.
+ * exp_mode 0 uses a = b = exp(s^2 / 8 pi).  For exp_mode 2 this call sets a
+ * fitted table: `table` is HOST memory [2][m], row 0 = a at the nodes
+ * s_i = i s_max / (m - 1), row 1 = b; a(s), b(s) are linear between nodes
+ * and constant beyond s_max.  2 <= m <= SHS_OL_TABLE_MAX, s_max > 0, every
+ * entry finite (SHS_ERR_INVALID_ARG otherwise, and for a scene whose
+ * exp_mode is not 2).  The call synchronises the device and copies the
+ * table into scene-owned device memory; the caller keeps `table`.  Shading
+ * an exp_mode 2 scene before a table is set fails with SHS_ERR_INVALID_ARG. */
+shs_status shs_scene_set_ol_table(shs_scene_t scene, const float* table, int32_t m, float s_max);
 
 /* Frees the scene after synchronising the device.  NULL is accepted. */
 shs_status shs_scene_destroy(shs_scene_t scene);
@@ -171,7 +189,8 @@ shs_status shs_shade_backward_l2(shs_scene_t scene, int64_t n_points, const floa
  * of about 35 KB compiled into the library, which every GPU that loads the
  * library holds until the process exits.
  *   Limits: n_bands <= 8 and n_spheres <= 1024; larger requests return
- *   SHS_ERR_INVALID_ARG with a message naming the limit.
+ *   SHS_ERR_INVALID_ARG with a message naming the limit.  exp_mode 2 (a
+ *   table held by a scene) returns SHS_ERR_UNSUPPORTED.
  *   Set-up: the first call on each device looks up that array's device address
  *   (cudaGetSymbolAddress) with the device current; make that first call
  *   before any stream capture.

@@ -53,6 +53,7 @@ _SIGS = {
     "shs_scene_create": (c_int32, [POINTER(ShsConfig), c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                    POINTER(c_void_p)]),
     "shs_scene_update": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "shs_scene_set_ol_table": (c_int32, [c_void_p, _F, c_int32, c_float]),
     "shs_scene_destroy": (c_int32, [c_void_p]),
     "shs_scene_info": (c_int32, [c_void_p, POINTER(ShsConfig), POINTER(c_int32)]),
     "shs_saved_bytes": (c_size_t, [c_void_p, c_int64]),

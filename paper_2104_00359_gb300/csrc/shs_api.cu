@@ -84,6 +84,9 @@ struct shs_scene_s {
     int64_t fwork_points;
     float* bwork;          // [K][P] adjoint coefficients of the split backward (>= 6 bands)
     int64_t bwork_points;
+    float2* ol_table;      // exp_mode 2: (a, b) per node
+    int ol_m;
+    float ol_inv_h;
 };
 
 struct shs_batch_s {
@@ -153,7 +156,7 @@ shs_status check_config(const shs_config* c) {
         return fail(SHS_ERR_UNSUPPORTED, "tensor-core precisions need n_bands = 8");
     if (c->deterministic != 0 && c->deterministic != 1) return fail(SHS_ERR_INVALID_ARG, "deterministic must be 0 or 1");
     if (c->horizon_cull != 0 && c->horizon_cull != 1) return fail(SHS_ERR_INVALID_ARG, "horizon_cull must be 0 or 1");
-    if (c->exp_mode != 0 && c->exp_mode != 1) return fail(SHS_ERR_INVALID_ARG, "exp_mode must be 0 or 1");
+    if (c->exp_mode < 0 || c->exp_mode > 2) return fail(SHS_ERR_INVALID_ARG, "exp_mode must be 0, 1 or 2");
     if (c->exp_mode == 1 && c->precision != SHS_FP32)
         return fail(SHS_ERR_UNSUPPORTED, "the projected exponential runs in SHS_FP32 only");
     return SHS_OK;
@@ -171,6 +174,9 @@ SceneView view_of(const shs_scene_s* s) {
     v.fixed_k = s->cfg.fixed_k;
     v.horizon_cull = s->cfg.horizon_cull;
     v.exp_mode = s->cfg.exp_mode;
+    v.ol_table = s->ol_table;
+    v.ol_m = s->ol_m;
+    v.ol_inv_h = s->ol_inv_h;
     v.status = s->status;
     return v;
 }
@@ -327,10 +333,13 @@ void free_scene(shs_scene_s* s) {
     cudaFree(s->b3l);
     cudaFree(s->fwork);
     cudaFree(s->bwork);
+    cudaFree(s->ol_table);
     delete s;
 }
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool table_ready(const shs_scene_s* s) { return s->cfg.exp_mode != 2 || s->ol_table != nullptr; }
 
 }  // namespace
 
@@ -447,6 +456,33 @@ shs_status shs_scene_update(shs_scene_t sc, const float* centers, const float* r
     return SHS_OK;
 }
 
+shs_status shs_scene_set_ol_table(shs_scene_t sc, const float* table, int32_t m, float s_max) {
+    if (!sc) return fail(SHS_ERR_INVALID_ARG, "scene is NULL");
+    if (sc->cfg.exp_mode != 2) return fail(SHS_ERR_INVALID_ARG, "the scene's exp_mode is not 2");
+    if (!table) return fail(SHS_ERR_INVALID_ARG, "table is NULL");
+    if (m < 2 || m > SHS_OL_TABLE_MAX) return fail(SHS_ERR_INVALID_ARG, "m %d not in 2..%d", m, SHS_OL_TABLE_MAX);
+    if (!(s_max > 0.f) || !(s_max < 1e30f)) return fail(SHS_ERR_INVALID_ARG, "s_max must be finite and > 0");
+    std::vector<float2> ab(static_cast<size_t>(m));
+    for (int i = 0; i < m; ++i) {
+        const float x = table[i], y = table[m + i];
+        if (!std::isfinite(x) || !std::isfinite(y)) return fail(SHS_ERR_INVALID_ARG, "table entry %d is not finite", i);
+        ab[i] = make_float2(x, y);
+    }
+    // the previous table may still be read by queued kernels
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && sc->ol_m != m) {
+        cudaFree(sc->ol_table);
+        sc->ol_table = nullptr;
+        sc->ol_m = 0;
+        e = cudaMalloc(&sc->ol_table, sizeof(float2) * m);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(sc->ol_table, ab.data(), sizeof(float2) * m, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload coefficient table");
+    sc->ol_m = m;
+    sc->ol_inv_h = static_cast<float>((m - 1) / static_cast<double>(s_max));
+    return SHS_OK;
+}
+
 shs_status shs_scene_destroy(shs_scene_t sc) {
     if (!sc) return SHS_OK;
     cudaError_t e = cudaDeviceSynchronize();
@@ -485,6 +521,7 @@ shs_status shs_shade(shs_scene_t sc, int64_t n_points, const float* points, cons
     if (n_points == 0) return SHS_OK;
     if (!points || !normals || !albedo || !radiance) return fail(SHS_ERR_INVALID_ARG, "NULL input/output array");
     if (saved && (reinterpret_cast<uintptr_t>(saved) & 15u)) return fail(SHS_ERR_INVALID_ARG, "saved not 16-byte aligned");
+    if (!table_ready(sc)) return fail(SHS_ERR_INVALID_ARG, "exp_mode 2 needs shs_scene_set_ol_table first");
     FwdArgs a;
     a.sc = view_of(sc);
     a.n_points = n_points;
@@ -556,6 +593,7 @@ static shs_status backward_common(shs_scene_t sc, int64_t n_points, const float*
         return e == cudaSuccess ? SHS_OK : cuda_fail(e, "zero empty outputs");
     }
     if (!points || !normals || !albedo) return fail(SHS_ERR_INVALID_ARG, "NULL input array");
+    if (!table_ready(sc)) return fail(SHS_ERR_INVALID_ARG, "exp_mode 2 needs shs_scene_set_ol_table first");
     BwdArgs a;
     a.sc = view_of(sc);
     a.n_points = n_points;
@@ -650,6 +688,7 @@ shs_status shs_shade_batch(shs_batch_t batch, const shs_request* reqs, int32_t n
     for (int i = 0; i < n_reqs; ++i) {
         const shs_request& r = reqs[i];
         if (!r.scene) return fail(SHS_ERR_INVALID_ARG, "request %d: scene is NULL", i);
+        if (!table_ready(r.scene)) return fail(SHS_ERR_INVALID_ARG, "request %d: exp_mode 2 without a table", i);
         if (r.n_points < 0) return fail(SHS_ERR_INVALID_ARG, "request %d: n_points < 0", i);
         if (r.n_points > 0 && (!r.points || !r.normals || !r.albedo || !r.radiance))
             return fail(SHS_ERR_INVALID_ARG, "request %d: NULL input/output array", i);

@@ -26,7 +26,11 @@ struct SceneView {
     int kmax;
     int fixed_k;
     int horizon_cull;        // 1: drop spheres below the tangent plane, per point
-    int exp_mode;            // 0: scaling + optimal linear step + squarings; 1: projected exponential
+    int exp_mode;            // 0: scaling + optimal linear step + squarings; 1: projected exponential;
+                             // 2: as 0 with the optimal linear coefficients from a fitted table
+    const float2* ol_table;  // exp_mode 2: (a, b) at the nodes s_m = m h, m = 0..ol_m-1
+    int ol_m;
+    float ol_inv_h;          // 1 / h
     int* status;             // device status word
 };
 

@@ -374,6 +374,37 @@ __device__ __forceinline__ void pair_backward_grad(float px, float py, float pz,
 }
 
 // Number of squarings: least k >= 0 with |f_hat| <= tau 2^k, capped at kmax.
+// Optimal linear step exp*(g) ~ a(s) sqrt(4 pi) e_0 + b(s) g at s = |g|
+// (Sec. 3.3.2): the Gaussian reading a = b = exp(s^2 / 8 pi), or, for
+// exp_mode 2, a fitted table that is linear between its nodes and constant
+// past the last one.  ca and cb are (da/ds) / s and (db/ds) / s, the factors
+// of g in the adjoint (zero at s = 0 and past the table).
+struct OLCoef {
+    float a, b, ca, cb;
+};
+__device__ __forceinline__ OLCoef ol_coef(const SceneView& sc, float s2) {
+    OLCoef r;
+    if (sc.exp_mode != 2) {
+        r.a = expf(s2 * kInv8Pi);
+        r.b = r.a;
+        r.ca = r.a * kInv4Pi;
+        r.cb = r.ca;
+        return r;
+    }
+    const float s = sqrtf(s2);
+    const float last = static_cast<float>(sc.ol_m - 1);
+    const float x = fminf(s * sc.ol_inv_h, last);
+    const int i = min(static_cast<int>(x), sc.ol_m - 2);
+    const float t = x - static_cast<float>(i);
+    const float2 lo = __ldg(sc.ol_table + i), hi = __ldg(sc.ol_table + i + 1);
+    r.a = fmaf(t, hi.x - lo.x, lo.x);
+    r.b = fmaf(t, hi.y - lo.y, lo.y);
+    const float c = (x < last && s > 0.f) ? sc.ol_inv_h / s : 0.f;
+    r.ca = (hi.x - lo.x) * c;
+    r.cb = (hi.y - lo.y) * c;
+    return r;
+}
+
 __device__ __forceinline__ int scaling_k(const SceneView& sc, float nrm2) {
     if (sc.fixed_k >= 0) return sc.fixed_k;
     int k = 0;
@@ -697,11 +728,11 @@ __device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_
         for (int i = 1; i < K; ++i) nrm2 = fmaf(f[i], f[i], nrm2);
         k = scaling_k(a.sc, nrm2);
         const float scale = ldexpf(1.f, -k);
-        const float a0 = expf(nrm2 * scale * scale * kInv8Pi);
+        const OLCoef ol = ol_coef(a.sc, nrm2 * scale * scale);
         float S[K];
-        S[0] = a0 * kSqrt4Pi;
+        S[0] = ol.a * kSqrt4Pi;
 #pragma unroll
-        for (int i = 1; i < K; ++i) S[i] = a0 * (f[i] * scale);
+        for (int i = 1; i < K; ++i) S[i] = ol.b * (f[i] * scale);
         for (int t = 0; t < k; ++t) {
             float T[K];
             sh_sqr(S, T);
@@ -850,10 +881,10 @@ __global__ void __launch_bounds__(128, 1) tail_tc_kernel(const __grid_constant__
         const int k = scaling_k(a.sc, nrm2);
         const float e0 = expf(S[0] * kInvSqrt4Pi);
         const float scale = ldexpf(1.f, -k);
-        const float a0 = expf(nrm2 * scale * scale * kInv8Pi);
-        S[0] = a0 * kSqrt4Pi;
+        const OLCoef ol = ol_coef(a.sc, nrm2 * scale * scale);
+        S[0] = ol.a * kSqrt4Pi;
 #pragma unroll
-        for (int i = 1; i < K; ++i) S[i] = a0 * (S[i] * scale);
+        for (int i = 1; i < K; ++i) S[i] = ol.b * (S[i] * scale);
         if (tid == 0) s_kmax = 0;
         __syncthreads();
         atomicMax(&s_kmax, k);
@@ -1140,20 +1171,21 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_
     // ---- recompute the exponential, keeping the operand of every squaring
     // (or, for the projected-exponential variant, U = P_n[exp(f^)])
     const bool projexp = EXPM == 2 ? a.sc.exp_mode == 1 : EXPM == 1;
-    float scale = 1.f, a0 = 1.f, e0 = 1.f;
+    float scale = 1.f, e0 = 1.f;
+    OLCoef ol{1.f, 1.f, 0.f, 0.f};
     float g[K], S[K], V[K], U[K];
     float hist[kMaxK][K];
     if (projexp) {
         proj_exp(f, V, U);
     } else {
         scale = ldexpf(1.f, -k);
-        a0 = expf(nrm2 * scale * scale * kInv8Pi);
+        ol = ol_coef(a.sc, nrm2 * scale * scale);
         g[0] = 0.f;
 #pragma unroll
         for (int i = 1; i < K; ++i) g[i] = f[i] * scale;
-        S[0] = a0 * kSqrt4Pi;
+        S[0] = ol.a * kSqrt4Pi;
 #pragma unroll
-        for (int i = 1; i < K; ++i) S[i] = a0 * g[i];
+        for (int i = 1; i < K; ++i) S[i] = ol.b * g[i];
         for (int t = 0; t < k; ++t) {
             float T[K];
             sh_sqr(S, T);
@@ -1251,12 +1283,15 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_
 #pragma unroll
             for (int i = 0; i < K; ++i) dS[i] = 2.f * T[i];
         }
-        float da = dS[0] * kSqrt4Pi;
+        // S_0 = a(s) sqrt(4 pi), S_i = b(s) g_i: dg_i = b dS_i + (dA a'/s + dB b'/s) g_i
+        const float dA = dS[0] * kSqrt4Pi;
+        float dB = 0.f;
 #pragma unroll
-        for (int i = 1; i < K; ++i) da = fmaf(dS[i], g[i], da);
+        for (int i = 1; i < K; ++i) dB = fmaf(dS[i], g[i], dB);
+        const float cg = fmaf(dA, ol.ca, dB * ol.cb);
         dfp[0] = de0 * e0 * kInvSqrt4Pi;
 #pragma unroll
-        for (int i = 1; i < K; ++i) dfp[i] = fmaf(a0, dS[i], da * a0 * kInv4Pi * g[i]) * scale;
+        for (int i = 1; i < K; ++i) dfp[i] = fmaf(ol.b, dS[i], cg * g[i]) * scale;
     }
 #pragma unroll
     for (int i = 0; i < K; ++i) dfp[i] *= a.sc.neg_2pi_eps * SH::norm(i);

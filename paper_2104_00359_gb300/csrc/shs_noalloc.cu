@@ -72,6 +72,9 @@ extern "C" shs_status shs_shade_backward_noalloc(
     void* stream) {
     int st = shs::validate_config(cfg);
     if (st != SHS_OK) return static_cast<shs_status>(st);
+    if (cfg->exp_mode == 2)
+        return static_cast<shs_status>(shs::report_error(
+            SHS_ERR_UNSUPPORTED, "no-alloc backward: exp_mode 2 needs a scene's coefficient table"));
     const int K = cfg->n_bands * cfg->n_bands;
     if (K > kMaxK)
         return static_cast<shs_status>(shs::report_error(
@@ -132,6 +135,9 @@ extern "C" shs_status shs_shade_backward_noalloc(
     a.sc.fixed_k = cfg->fixed_k;
     a.sc.horizon_cull = cfg->horizon_cull;
     a.sc.exp_mode = cfg->exp_mode;
+    a.sc.ol_table = nullptr;
+    a.sc.ol_m = 0;
+    a.sc.ol_inv_h = 0.f;
     a.sc.status = status;
     a.n_points = n_points;
     a.points = points;

@@ -12,6 +12,7 @@ from __future__ import annotations
 import ctypes
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import _lib
@@ -30,7 +31,8 @@ class Config:
     precision: int = _lib.SHS_FP32
     deterministic: bool = True
     horizon_cull: bool = False
-    exp_mode: int = 0          # 0: scaling + squarings (Sec. 3.3.2); 1: projected exponential
+    exp_mode: int = 0          # 0: scaling + squarings (Sec. 3.3.2); 1: projected exponential;
+                               # 2: as 0 with a fitted optimal linear table (Scene.set_ol_table)
 
     def to_c(self):
         return ShsConfig(int(self.n_bands), float(self.epsilon), float(self.exp_tau), int(self.exp_kmax),
@@ -75,6 +77,17 @@ class Scene:
         r = _dev_f32(radii, (self.n_spheres,), "radii") if radii is not None and self.n_spheres else None
         L = _dev_f32(light, (3, self.K), "light") if light is not None else None
         check(self.lib.shs_scene_update(self.handle, ptr(c), ptr(r), ptr(L), _stream()), "shs_scene_update")
+
+    def set_ol_table(self, a, b, s_max):
+        """Optimal linear coefficients a(s), b(s) at the nodes s_i = i s_max / (m-1)
+        (exp_mode 2); host arrays, copied into the scene."""
+        a = np.asarray(a, np.float64).ravel()
+        b = np.asarray(b, np.float64).ravel()
+        if a.shape != b.shape:
+            raise ValueError("a and b must have the same length")
+        tab = np.ascontiguousarray(np.concatenate([a, b]), np.float32)
+        check(self.lib.shs_scene_set_ol_table(self.handle, tab.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                              int(a.shape[0]), float(s_max)), "shs_scene_set_ol_table")
 
     def close(self):
         if getattr(self, "handle", None):

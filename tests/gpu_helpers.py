@@ -57,6 +57,8 @@ def gpu_run(sc, cfg, dB=None, want=None, saved=True, l2_target=None):
                          deterministic=getattr(cfg, "deterministic", True),
                          horizon_cull=getattr(cfg, "horizon_cull", False),
                          exp_mode=getattr(cfg, "exp_mode", 0)))
+    if getattr(cfg, "exp_mode", 0) == 2:
+        scene.set_ol_table(*cfg.ol_table)
     P = sc["points"].shape[0]
     K = cfg.n_bands ** 2
     sv = scene.new_saved(P, dev)

@@ -50,7 +50,8 @@ def test_config_validation_without_gpu(lib):
     assert (cfg.n_bands, cfg.epsilon, cfg.exp_tau, cfg.exp_kmax, cfg.fixed_k) == (4, 3.0, 1.0, 16, -1)
     h = ctypes.c_void_p()
     for field, value, expect in (("n_bands", 9, 1), ("n_bands", 0, 1), ("exp_kmax", 17, 1),
-                                 ("precision", 7, 1), ("precision", 2, 2), ("horizon_cull", 2, 1), ("exp_mode", 2, 1),
+                                 ("precision", 7, 1), ("precision", 2, 2), ("horizon_cull", 2, 1), ("exp_mode", 3, 1),
+                                 ("exp_mode", -1, 1),
                                  ("exp_tau", 0.0, 1), ("deterministic", 2, 1)):
         bad = ShsConfig()
         lib.shs_config_default(ctypes.byref(bad))
@@ -64,6 +65,8 @@ def test_config_validation_without_gpu(lib):
     st = lib.shs_scene_create(ctypes.byref(cfg), 3, None, None, ctypes.c_void_p(16), None, ctypes.byref(h))
     assert st == 1
     assert lib.shs_saved_bytes(None, 100) == 0
+    tab = (ctypes.c_float * 4)(1, 1, 1, 1)
+    assert lib.shs_scene_set_ol_table(None, tab, 2, 1.0) == 1
     assert lib.shs_shade(None, 10, None, None, None, None, None, None) == 1
     assert lib.shs_status_string(5) == b"device wait timed out"
 
