@@ -378,13 +378,15 @@ __device__ __forceinline__ void pair_backward_grad(float px, float py, float pz,
 // (Sec. 3.3.2): the Gaussian reading a = b = exp(s^2 / 8 pi), or, for
 // exp_mode 2, a fitted table that is linear between its nodes and constant
 // past the last one.  ca and cb are (da/ds) / s and (db/ds) / s, the factors
-// of g in the adjoint (zero at s = 0 and past the table).
+// of g in the adjoint (zero at s = 0 and past the table).  TAB: Gaussian only
+// (0), table only (1), or chosen by the scene's exp_mode (2).
 struct OLCoef {
     float a, b, ca, cb;
 };
+template <int TAB = 2>
 __device__ __forceinline__ OLCoef ol_coef(const SceneView& sc, float s2) {
     OLCoef r;
-    if (sc.exp_mode != 2) {
+    if (TAB == 0 || (TAB == 2 && sc.exp_mode != 2)) {
         r.a = expf(s2 * kInv8Pi);
         r.b = r.a;
         r.ca = r.a * kInv4Pi;
@@ -1127,7 +1129,9 @@ __device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v
 // the scene-level sums are added to the block's shared accumulators
 // (s_dl: d_light and loss per warp, s_acc: per warp and sphere).
 // CULLM: horizon culling off (0), on (1), or read from the scene per call (2);
-// EXPM: the same for the projected-exponential variant.
+// EXPM: the exponential's form: the Gaussian optimal linear step (0), the
+// projected exponential (1), the tabulated optimal linear step (3), or the
+// scene's exp_mode read per call (2).
 template <bool PAIRS = true, int CULLM = 2, int EXPM = 2>
 __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_sph, const float* s_light,
                                               float* s_acc, float (*s_dl)[3 * K + 1], int64_t tile,
@@ -1179,7 +1183,7 @@ __device__ __forceinline__ void backward_tile(const BwdArgs& a, const float4* s_
         proj_exp(f, V, U);
     } else {
         scale = ldexpf(1.f, -k);
-        ol = ol_coef(a.sc, nrm2 * scale * scale);
+        ol = ol_coef<EXPM == 0 ? 0 : EXPM == 3 ? 1 : 2>(a.sc, nrm2 * scale * scale);
         g[0] = 0.f;
 #pragma unroll
         for (int i = 1; i < K; ++i) g[i] = f[i] * scale;
@@ -1871,6 +1875,8 @@ cudaError_t launch_backward<NB>(const BwdArgs& a, cudaStream_t s) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(backward_kernel_t<true, 1, 0>, at, bytes);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(backward_kernel_t<true, 0, 1>, at, bytes);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(backward_kernel_t<true, 1, 1>, at, bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(backward_kernel_t<true, 0, 3>, at, bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(backward_kernel_t<true, 1, 3>, at, bytes);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(backward_kernel_t<false, 2, 2>, at, bytes);
         return e;
     }();
@@ -1897,6 +1903,9 @@ cudaError_t launch_backward<NB>(const BwdArgs& a, cudaStream_t s) {
         if (a.sc.exp_mode == 1) {
             if (a.sc.horizon_cull) backward_kernel_t<true, 1, 1><<<grid, kBlock, smem, s>>>(a);
             else backward_kernel_t<true, 0, 1><<<grid, kBlock, smem, s>>>(a);
+        } else if (a.sc.exp_mode == 2) {
+            if (a.sc.horizon_cull) backward_kernel_t<true, 1, 3><<<grid, kBlock, smem, s>>>(a);
+            else backward_kernel_t<true, 0, 3><<<grid, kBlock, smem, s>>>(a);
         } else {
             if (a.sc.horizon_cull) backward_kernel_t<true, 1, 0><<<grid, kBlock, smem, s>>>(a);
             else backward_kernel_t<true, 0, 0><<<grid, kBlock, smem, s>>>(a);
