@@ -100,6 +100,20 @@ def profiled_traffic(kernel, workload_tag):
     return None
 
 
+def read_ol_table(path):
+    """(a, b, s_max) of a fitted optimal linear table file (columns s a b;
+    s_max on the '# n_bands' header line)."""
+    rows, s_max = [], None
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("# n_bands"):
+                s_max = float(line.split()[4])
+            elif line.strip() and not line.startswith("#"):
+                rows.append([float(x) for x in line.split()])
+    rows = np.array(rows)
+    return rows[:, 1].copy(), rows[:, 2].copy(), s_max
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -612,10 +626,18 @@ def bench_heightfield(args, world, rank, local):
     T = {k: torch.from_numpy(sc[k]).to(dev) for k in ("points", "normals", "albedo", "centers", "radii", "light")}
     P, N = sc["points"].shape[0], sc["centers"].shape[0]
     out = {}
-    # (name, precision, exp_mode): exp_mode 1 is the projected-exponential variant
-    all_precs = (("fp32", 0, 0), ("bf16_split_tc", 2, 0), ("fp16_split_tc", 3, 0), ("fp32_projexp", 0, 1))
+    # (name, precision, exp_mode): exp_mode 1 is the projected-exponential
+    # variant, 2 the optimal linear step with the fitted 8-band table
+    all_precs = (("fp32", 0, 0), ("bf16_split_tc", 2, 0), ("fp16_split_tc", 3, 0), ("fp32_projexp", 0, 1),
+                 ("fp32_oltable", 0, 2))
+    # the library stores the table as float32: give the oracle the same values
+    table = tuple(np.float32(x).astype(np.float64) if i < 2 else x for i, x in
+                  enumerate(read_ol_table(os.path.join(ROOT, "tests", "golden", "ol_table_n8.txt"))))
+    fine = None
     for prec_name, prec, mode in [x for x in all_precs if x[0] in args.precisions.split(",")]:
         scene = Scene(T["centers"], T["radii"], T["light"], Config(n_bands=8, precision=prec, exp_mode=mode))
+        if mode == 2:
+            scene.set_ol_table(*table)
         saved = scene.new_saved(P, dev)
         dB = torch.randn((P, 3), device=dev)
         times_f, times_b = [], []
@@ -635,24 +657,26 @@ def bench_heightfield(args, world, rank, local):
         sel = np.sort(np.random.default_rng(1).choice(P, 256, replace=False))
         args_o = [sc[f][sel] if f in ("points", "normals", "albedo") else sc[f]
                   for f in ("points", "normals", "albedo", "centers", "radii", "light")]
-        ref = O.shade_forward(O.Config(n_bands=8, exp_mode=mode), *args_o, k=k[sel])["radiance"]
+        ocfg = O.Config(n_bands=8, exp_mode=mode, ol_table=table if mode == 2 else None)
+        ref = O.shade_forward(ocfg, *args_o, k=k[sel])["radiance"]
         got = B.cpu().numpy()[sel]
         err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
         out[prec_name] = {"fwd_ms": statistics.fmean(times_f), "bwd_ms": statistics.fmean(times_b),
                           "pairs_per_s_fwd": P * N / (statistics.fmean(times_f) * 1e-3),
                           "pairs_per_s_fwd_bwd": P * N / ((statistics.fmean(times_f) + statistics.fmean(times_b)) * 1e-3),
                           "radiance_max_rel_err_vs_fp64": float(err.max()), "k_mean": float(k.mean())}
-        if mode == 1:
-            # accuracy of both exponential methods (FP64) against the projection of
+        if mode in (1, 2):
+            # accuracy of the exponential methods (FP64) against the projection of
             # exp(f) by a fine rule (64 x 128 nodes) on the same sample
-            fine = O.shade_forward(O.Config(n_bands=8, exp_mode=1, exp_rule=(64, 128)), *args_o)["radiance"]
-            sq = O.shade_forward(O.Config(n_bands=8), *args_o)["radiance"]
+            if fine is None:
+                fine = O.shade_forward(O.Config(n_bands=8, exp_mode=1, exp_rule=(64, 128)), *args_o)["radiance"]
 
             def rel(x):
                 d = np.abs(x - fine) / np.maximum(np.abs(fine), 1e-3 * np.abs(fine).max())
                 return {"max": float(d.max()), "median": float(np.median(d))}
-            out[prec_name]["vs_fine_projection_fp64"] = {"projected_2n_x_4n": rel(ref),
-                                                         "scaling_squaring": rel(sq)}
+            sq = O.shade_forward(O.Config(n_bands=8), *args_o)["radiance"]
+            out[prec_name]["vs_fine_projection_fp64"] = {
+                "projected_2n_x_4n" if mode == 1 else "fitted_ol_table": rel(ref), "scaling_squaring": rel(sq)}
         scene.close()
     first = next(iter(out.values()))
     return dict(metric="height field 1024^2 x 300 spheres, n_bands=8: pairs/sec and error vs FP64 per precision",
@@ -762,8 +786,9 @@ def main():
     ap.add_argument("--workload", choices=("capsule", "serving", "heightfield", "envmap"), default="capsule",
                     help="capsule: the 512x512 G-buffer step (default); serving: the mixed request stream")
     ap.add_argument("--hf-res", type=int, default=1024, help="height-field grid side (heightfield workload)")
-    ap.add_argument("--precisions", default="fp32,bf16_split_tc,fp16_split_tc,fp32_projexp",
-                    help="heightfield workload: comma list of fp32, bf16_split_tc, fp16_split_tc, fp32_projexp")
+    ap.add_argument("--precisions", default="fp32,bf16_split_tc,fp16_split_tc,fp32_projexp,fp32_oltable",
+                    help="heightfield workload: comma list of fp32, bf16_split_tc, fp16_split_tc, fp32_projexp, "
+                         "fp32_oltable")
     ap.add_argument("--env-res", type=int, default=4096, help="environment map rows (width = 2 x rows)")
     ap.add_argument("--serve-jobs", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=2000)

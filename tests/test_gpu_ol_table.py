@@ -16,14 +16,16 @@ from gpu_helpers import FIELDS, gpu_run, grad_err, rel_err
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
-TABLE = os.path.join(os.path.dirname(__file__), "golden", "ol_table_n4.txt")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def _cfg(n, **kw):
-    """The library takes the table as float32, like every other input, so the
-    oracle is given the same float32 values (the slopes of a table of values
-    near 1 carry their rounding, about 1e-4 of the gradients' scale)."""
-    a, b, s_max = F.read_table(TABLE)
+    """The 8-band table at 8 bands, the 4-band one otherwise (any table is a
+    valid input).  The library takes the table as float32, like every other
+    input, so the oracle is given the same float32 values (the slopes of a
+    table of values near 1 carry their rounding, about 1e-4 of the gradients'
+    scale)."""
+    a, b, s_max = F.read_table(os.path.join(GOLDEN, "ol_table_n8.txt" if n == 8 else "ol_table_n4.txt"))
     a, b = (np.asarray(x, np.float32).astype(np.float64) for x in (a, b))
     return O.Config(n_bands=n, exp_mode=2, ol_table=(a, b, s_max), **kw)
 

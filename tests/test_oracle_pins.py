@@ -624,3 +624,13 @@ def test_stored_table_is_what_the_fit_script_writes():
     ho = F.Problem(4, F.ensemble(4, 1500, 7))
     ga, gb = F.gaussian_table(a.shape[0], smax)
     assert ho.objective(a, b, smax) <= ho.objective(ga, gb, smax)
+
+
+def test_stored_8_band_table_beats_the_gaussian_step_on_held_out_points():
+    """At 8 bands the fitted table lowers the whole method's error against the
+    projected exponential on an ensemble it was not fitted on."""
+    from oracle import fit_ol_table as F
+    a, b, smax = F.read_table(os.path.join(os.path.dirname(__file__), "golden", "ol_table_n8.txt"))
+    ho = F.Problem(8, F.ensemble(8, 150, 7), rule=O.sphere_quadrature(40, 80))
+    ga, gb = F.gaussian_table(a.shape[0], smax)
+    assert ho.objective(a, b, smax) < 0.6 * ho.objective(ga, gb, smax)
