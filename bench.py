@@ -58,7 +58,7 @@ def gaunt_nnz(n):
 
 
 def flop_model(n, n_spheres, k_mean):
-    """Algorithmic FP32 flops per shading point (stated in the design doc):
+    """Algorithmic FP32 flops per shading point:
     pair terms 4n^2+5n+14 (fwd) and 9n^2+10n+50 (bwd) per sphere; tails
     2 nnz_sym k + 2 nnz + 10K (fwd) and 2 nnz_sym k + 2 nnz k + 6 nnz + 18K (bwd)."""
     K = n * n

@@ -55,7 +55,7 @@ typedef struct shs_scene_s* shs_scene_t;
 typedef enum {
     SHS_OK = 0,
     SHS_ERR_INVALID_ARG = 1, /* bad size, NULL where required, out-of-range config */
-    SHS_ERR_UNSUPPORTED = 2, /* valid request this build does not implement      */
+    SHS_ERR_UNSUPPORTED = 2, /* valid request the library does not implement     */
     SHS_ERR_OOM = 3,         /* device allocation failed                          */
     SHS_ERR_CUDA = 4,        /* a CUDA runtime call failed (see shs_last_error)   */
     SHS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up                */

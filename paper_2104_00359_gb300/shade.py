@@ -33,6 +33,7 @@ class Config:
     horizon_cull: bool = False
     exp_mode: int = 0          # 0: scaling + squarings (Sec. 3.3.2); 1: projected exponential;
                                # 2: as 0 with a fitted optimal linear table (Scene.set_ol_table)
+    ol_table: tuple | None = None  # exp_mode 2: (a, b, s_max), set on every Scene made with this config
 
     def to_c(self):
         return ShsConfig(int(self.n_bands), float(self.epsilon), float(self.exp_tau), int(self.exp_kmax),
@@ -71,6 +72,8 @@ class Scene:
         check(self.lib.shs_scene_create(ctypes.byref(cfg), self.n_spheres, ptr(c), ptr(r), ptr(L), _stream(),
                                         ctypes.byref(h)), "shs_scene_create")
         self.handle = h
+        if self.config.exp_mode == 2 and self.config.ol_table is not None:
+            self.set_ol_table(*self.config.ol_table)
 
     def update(self, centers=None, radii=None, light=None):
         c = _dev_f32(centers, (self.n_spheres, 3), "centers") if centers is not None and self.n_spheres else None

@@ -67,6 +67,11 @@ def test_config_validation_without_gpu(lib):
     assert lib.shs_saved_bytes(None, 100) == 0
     tab = (ctypes.c_float * 4)(1, 1, 1, 1)
     assert lib.shs_scene_set_ol_table(None, tab, 2, 1.0) == 1
+    # the no-alloc backward has no scene to hold a table: refused before any CUDA call
+    c2 = ShsConfig()
+    lib.shs_config_default(ctypes.byref(c2))
+    c2.exp_mode = 2
+    assert lib.shs_shade_backward_noalloc(ctypes.byref(c2), 0, None, None, None, 0, *([None] * 11), None) == 2
     assert lib.shs_shade(None, 10, None, None, None, None, None, None) == 1
     assert lib.shs_status_string(5) == b"device wait timed out"
 

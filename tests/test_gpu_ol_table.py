@@ -113,3 +113,40 @@ def test_ol_table_on_the_tensor_core_tail():
     scene.close()
     ref = O.shade_forward(cfg, *[sc[x] for x in FIELDS], k=k)["radiance"]
     assert rel_err(B.cpu().numpy(), ref).max() <= 2e-3
+
+
+def test_table_scene_in_the_serving_batch():
+    """A job whose scene uses the table, batched with default jobs by the
+    continuous-batching server, gives the same results as alone."""
+    from paper_2104_00359_gb300 import Config, serve
+    jobs = []
+    for j, mode in enumerate((2, 0, 2)):
+        sc = S.random_scene(880 + j, 700 + 300 * j, 30, 4, inside_fraction=0.05)
+        target = np.random.default_rng(j).uniform(0, 1, sc["points"].shape).astype(np.float32)
+        cfg = _cfg(4)
+        jobs.append((j, sc, target, Config(n_bands=4, exp_mode=mode, ol_table=cfg.ol_table if mode == 2 else None)))
+    srv = serve.Server(hbm_budget_bytes=1e9, n_slots=3, max_batch=4)
+    for j, sc, target, c in jobs:
+        assert srv.add_job(j, sc["points"], sc["normals"], sc["albedo"], sc["centers"], sc["radii"],
+                           sc["light"], c, target=target)
+    runner = serve.PerCallRunner(srv.jobs)
+    alone = {}
+    for j, *_ in jobs:
+        runner.run(serve.Request(-1, j, "fwdbwd", 0.0)).synchronize()
+        job = srv.jobs[j]
+        alone[j] = (job.radiance.cpu().numpy().copy(), job.grads["d_light"].cpu().numpy().copy())
+    got = {}
+
+    def grab(r, job):
+        got[r.job_id] = (job.radiance.cpu().numpy().copy(), job.grads["d_light"].cpu().numpy().copy())
+
+    for j, *_ in jobs:
+        srv.submit(j, "fwdbwd", on_done=grab)
+    srv.drain()
+    srv.close()
+    for j, sc, target, c in jobs:
+        assert rel_err(got[j][0], alone[j][0]).max() <= TOL
+        assert rel_err(got[j][1], alone[j][1]).max() <= TOL
+    # and the table jobs follow the oracle's table method
+    ref = O.shade_forward(_cfg(4), *[jobs[0][1][x] for x in FIELDS])["radiance"]
+    assert rel_err(got[0][0], ref).max() <= TOL
