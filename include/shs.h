@@ -305,6 +305,35 @@ shs_status shs_rasterize_backward(const float* vertices, int32_t n_vertices, con
                                   float* d_radiance, float* d_vertices, void* workspace, size_t workspace_bytes,
                                   void* stream);
 
+/* ---- Scene chain: linear deformation and rigid pose (Sec. 3.3.1, 3.5) ----
+ * For an array of n_rows rows (mesh vertices, normals or sphere centres):
+ *   x_rest[m] = base[m] + basis[m] p,   x[m] = R(w) x_rest[m] + t
+ * base [n_rows][3], basis [n_rows][3][n_params] (row-major), p [n_params],
+ * pose [6] = (w, t) with R(w) = exp([w]x) (axis-angle, Rodrigues' formula);
+ * direction = 1 drops t (normals).  All pointers are device memory, float32.
+ * 1 <= n_params <= SHS_CHAIN_MAX_PARAMS, n_rows >= 0 (0: nothing to do).
+ * Bad sizes, NULL pointers or direction outside {0, 1}: SHS_ERR_INVALID_ARG. */
+#define SHS_CHAIN_MAX_PARAMS 256
+
+/* x [n_rows][3] (and x_rest, if not NULL) on `stream`. */
+shs_status shs_chain_forward(const float* base, const float* basis, int64_t n_rows, int32_t n_params,
+                             const float* p, const float* pose, int32_t direction, float* x_rest, float* x,
+                             void* stream);
+
+/* Bytes of the workspace shs_chain_backward needs (0 for invalid sizes). */
+size_t shs_chain_workspace_bytes(int64_t n_rows, int32_t n_params);
+
+/* Adjoint for the upstream gradient d_x [n_rows][3]: writes (overwrites)
+ *   d_p [n_params]  = sum_m basis[m]^T R^T d_x[m]
+ *   d_pose [6]      = (dL/dw, dL/dt), dL/dt = sum_m d_x[m] (0 for directions),
+ *                     dL/dw_a = sum_m d_x[m]^T (dR/dw_a) x_rest[m]
+ * The sums are formed in a fixed order (deterministic).  workspace: device,
+ * 16-byte aligned, >= shs_chain_workspace_bytes(n_rows, n_params), owned by
+ * the caller and free again when the stream reaches the end of the call. */
+shs_status shs_chain_backward(const float* base, const float* basis, int64_t n_rows, int32_t n_params,
+                              const float* p, const float* pose, int32_t direction, const float* d_x,
+                              float* d_p, float* d_pose, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Diagnostic: FP32 FMA throughput probe.  Launches `blocks` blocks of 256
  * threads; each thread runs 8 independent fused multiply-add chains of
  * `iters` steps (16 iters flops per thread) and writes one float to

@@ -77,6 +77,11 @@ _SIGS = {
     "shs_rasterize_backward": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
                                          c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t,
                                          c_void_p]),
+    "shs_chain_forward": (c_int32, [c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int32, c_void_p,
+                                    c_void_p, c_void_p]),
+    "shs_chain_workspace_bytes": (c_size_t, [c_int64, c_int32]),
+    "shs_chain_backward": (c_int32, [c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int32, c_void_p,
+                                     c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "shs_fp32_fma_probe": (c_int32, [c_int32, c_int64, c_void_p, c_void_p]),
     "shs_tc_gemm_selftest": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p,
                                        c_void_p]),

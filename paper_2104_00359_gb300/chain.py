@@ -13,9 +13,64 @@ a parameter vector p (v = v0 + A_v p, n = n0 + A_n p, c = c0 + A_c p), then a
 
 from __future__ import annotations
 
+import ctypes
+
 import torch
 
+from . import _lib
+from ._lib import check, ptr
 from .shade import Scene, shade
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, name):
+    if not (t.is_cuda and t.dtype == torch.float32):
+        raise TypeError(f"{name} must be a float32 CUDA tensor")
+    return t.contiguous()
+
+
+class DeformPose(torch.autograd.Function):
+    """x = R(w) (base + basis p) + t (t dropped for directions), forward and
+    adjoint in the library's chain kernels; gradients flow to p and the pose
+    (base and basis are constants of the model)."""
+
+    @staticmethod
+    def forward(ctx, base, basis, p, pose, direction):
+        lib = _lib.load()
+        base, basis, p, pose = (_dev(t.detach(), n) for t, n in
+                                ((base, "base"), (basis, "basis"), (p, "p"), (pose, "pose")))
+        M, D = int(base.shape[0]), int(p.shape[0])
+        if tuple(basis.shape) != (M, 3, D) or tuple(pose.shape) != (6,):
+            raise ValueError(f"basis {tuple(basis.shape)} / pose {tuple(pose.shape)} do not match M={M}, D={D}")
+        x = torch.empty((M, 3), dtype=torch.float32, device=base.device)
+        check(lib.shs_chain_forward(ptr(base), ptr(basis), M, D, ptr(p), ptr(pose), int(direction), None, ptr(x),
+                                    _stream()), "shs_chain_forward")
+        ctx.save_for_backward(base, basis, p, pose)
+        ctx.direction = int(direction)
+        return x
+
+    @staticmethod
+    def backward(ctx, dx):
+        lib = _lib.load()
+        base, basis, p, pose = ctx.saved_tensors
+        M, D = int(base.shape[0]), int(p.shape[0])
+        dx = _dev(dx, "dx")
+        d_p = torch.empty((D,), dtype=torch.float32, device=base.device)
+        d_pose = torch.empty((6,), dtype=torch.float32, device=base.device)
+        nbytes = int(lib.shs_chain_workspace_bytes(M, D))
+        ws = torch.empty((max(nbytes, 16) + 3) // 4, dtype=torch.float32, device=base.device)
+        check(lib.shs_chain_backward(ptr(base), ptr(basis), M, D, ptr(p), ptr(pose), ctx.direction, ptr(dx),
+                                     ptr(d_p), ptr(d_pose), ptr(ws), ws.numel() * 4, _stream()),
+              "shs_chain_backward")
+        return None, None, d_p, d_pose, None
+
+
+def deform_pose(base, basis, p, pose, direction=False):
+    """R(w) (base + basis p) + t for pose = (w, t) [6]; direction drops t."""
+    return DeformPose.apply(base, basis, p, pose, bool(direction))
 
 
 def rodrigues(w):
@@ -35,13 +90,15 @@ def rodrigues(w):
 
 
 def pose(points, normals, centers, w, t):
-    """Apply the rigid pose (w, t): x -> R x + t, n -> R n."""
+    """Apply the rigid pose (w, t) to already deformed arrays: x -> R x + t,
+    n -> R n (torch ops; the rendering path uses the fused chain kernels)."""
     R = rodrigues(w)
     return points @ R.T + t, normals @ R.T, centers @ R.T + t
 
 
 def affine_deform(base, basis, p):
-    """base [M, 3] + basis [M, 3, D] @ p [D]."""
+    """base [M, 3] + basis [M, 3, D] @ p [D] (torch ops, for set-up and
+    checks; the rendering path uses the fused chain kernels)."""
     return base + torch.einsum("mcd,d->mc", basis, p)
 
 
@@ -50,12 +107,12 @@ def render_views(p, poses, model, radii, light, albedo, scenes):
 
     model: dict with v0, A_v, n0, A_n, c0, A_c (tensors on the device);
     poses: [V, 6] (axis-angle, translation); scenes: one Scene per view."""
-    v = affine_deform(model["v0"], model["A_v"], p)
-    n = affine_deform(model["n0"], model["A_n"], p)
-    c = affine_deform(model["c0"], model["A_c"], p)
     out = []
     for i, sc in enumerate(scenes):
-        pv, pn, pc = pose(v, n, c, poses[i, :3], poses[i, 3:])
+        q = poses[i]
+        pv = deform_pose(model["v0"], model["A_v"], p, q)
+        pn = deform_pose(model["n0"], model["A_n"], p, q, direction=True)
+        pc = deform_pose(model["c0"], model["A_c"], p, q)
         out.append(shade(pv, pn, albedo, pc, radii, light, sc))
     return torch.stack(out)
 

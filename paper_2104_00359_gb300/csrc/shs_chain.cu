@@ -1,0 +1,299 @@
+// Scene chain above the shading path (Sec. 3.3.1, Sec. 3.5): per array of M
+// rows (vertices, normals or sphere centres) a linear deformation model and a
+// rigid pose,
+//   x_rest[m] = base[m] + basis[m] p   (basis[m]: 3 x D, row-major [M][3][D])
+//   x[m]      = R(w) x_rest[m] + t     (t dropped for directions)
+// with R(w) = exp([w]x) (Rodrigues' formula), and the adjoint to p and to the
+// pose (w, t).
+//
+// The basis is the only large operand (M * 3 * D floats), read once per pass:
+// one warp per row, lanes striding the D parameters, so each row's 3 D floats
+// are read as contiguous 128-byte segments.  The adjoint's sums over rows are
+// kept per lane / per warp, combined per block in a fixed order, and the
+// blocks' partial rows are added in a fixed order by a second kernel, which
+// also turns dL/dR into dL/dw.
+
+#include <cmath>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "shs.h"
+#include "shs_internal.h"
+
+namespace {
+
+constexpr int kChainWarps = 8;                  // 256-thread blocks
+constexpr int kChainThreads = 32 * kChainWarps;
+constexpr int kChainMaxD = SHS_CHAIN_MAX_PARAMS;
+constexpr int kChainPerLane = kChainMaxD / 32;  // parameters a lane accumulates
+constexpr int kChainMaxBlocks = 152 * 4;
+constexpr int kChainExtra = 12;                 // dL/dR (9, row-major) and dL/dt (3)
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// R(w) = I + A K + B K^2, K = [w]x, A = sin th / th, B = (1 - cos th) / th^2
+// written as 2 sin^2(th/2) / th^2 (no cancellation at small th); series below
+// th = 1e-3.
+__device__ __forceinline__ void rotation(const float* pose, float* R) {
+    const float wx = __ldg(pose), wy = __ldg(pose + 1), wz = __ldg(pose + 2);
+    const float t2 = wx * wx + wy * wy + wz * wz;
+    float A, B;
+    if (t2 < 1e-6f) {
+        A = 1.f - t2 * (1.f / 6.f);
+        B = 0.5f - t2 * (1.f / 24.f);
+    } else {
+        const float th = sqrtf(t2);
+        float s, c, sh, ch;
+        sincosf(th, &s, &c);
+        sincosf(0.5f * th, &sh, &ch);
+        A = s / th;
+        const float q = sh / (0.5f * th);
+        B = 0.5f * q * q;
+    }
+    // K^2 = w w^T - t2 I
+    R[0] = 1.f + B * (wx * wx - t2);
+    R[1] = -A * wz + B * wx * wy;
+    R[2] = A * wy + B * wx * wz;
+    R[3] = A * wz + B * wy * wx;
+    R[4] = 1.f + B * (wy * wy - t2);
+    R[5] = -A * wx + B * wy * wz;
+    R[6] = -A * wy + B * wz * wx;
+    R[7] = A * wx + B * wz * wy;
+    R[8] = 1.f + B * (wz * wz - t2);
+}
+
+__global__ void __launch_bounds__(kChainThreads) chain_forward_kernel(const float* base, const float* basis, int64_t M,
+                                                                      int D, const float* p, const float* pose,
+                                                                      int direction, float* x_rest, float* x) {
+    __shared__ float s_p[kChainMaxD];
+    for (int d = threadIdx.x; d < D; d += kChainThreads) s_p[d] = __ldg(p + d);
+    __syncthreads();
+    float R[9];
+    rotation(pose, R);
+    const float tx = direction ? 0.f : __ldg(pose + 3), ty = direction ? 0.f : __ldg(pose + 4),
+                tz = direction ? 0.f : __ldg(pose + 5);
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * kChainWarps;
+    for (int64_t m = static_cast<int64_t>(blockIdx.x) * kChainWarps + (threadIdx.x >> 5); m < M; m += warps) {
+        const float* row = basis + m * 3 * D;
+        float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            for (int d = lane; d < D; d += 32) acc[c] = fmaf(__ldcs(row + c * D + d), s_p[d], acc[c]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] = warp_sum(acc[c]) + __ldg(base + 3 * m + c);
+        if (lane == 0) {
+            if (x_rest) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) x_rest[3 * m + c] = acc[c];
+            }
+            x[3 * m] = fmaf(R[0], acc[0], fmaf(R[1], acc[1], fmaf(R[2], acc[2], tx)));
+            x[3 * m + 1] = fmaf(R[3], acc[0], fmaf(R[4], acc[1], fmaf(R[5], acc[2], ty)));
+            x[3 * m + 2] = fmaf(R[6], acc[0], fmaf(R[7], acc[1], fmaf(R[8], acc[2], tz)));
+        }
+    }
+}
+
+// Partial sums of one block: [0, D) dL/dp, then dL/dR (9), dL/dt (3).
+__global__ void __launch_bounds__(kChainThreads) chain_backward_kernel(const float* base, const float* basis, int64_t M,
+                                                                       int D, const float* p, const float* pose,
+                                                                       int direction, const float* g, float* partials) {
+    __shared__ float s_p[kChainMaxD];
+    __shared__ float s_dp[kChainWarps][kChainMaxD];
+    __shared__ float s_ex[kChainWarps][kChainExtra];
+    for (int d = threadIdx.x; d < D; d += kChainThreads) s_p[d] = __ldg(p + d);
+    __syncthreads();
+    float R[9];
+    rotation(pose, R);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float dp[kChainPerLane];
+#pragma unroll
+    for (int j = 0; j < kChainPerLane; ++j) dp[j] = 0.f;
+    float ex[kChainExtra];
+#pragma unroll
+    for (int i = 0; i < kChainExtra; ++i) ex[i] = 0.f;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * kChainWarps;
+    for (int64_t m = static_cast<int64_t>(blockIdx.x) * kChainWarps + warp; m < M; m += warps) {
+        const float g0 = __ldg(g + 3 * m), g1 = __ldg(g + 3 * m + 1), g2 = __ldg(g + 3 * m + 2);
+        // R^T g: the gradient in the rest frame
+        const float r0 = fmaf(R[0], g0, fmaf(R[3], g1, R[6] * g2));
+        const float r1 = fmaf(R[1], g0, fmaf(R[4], g1, R[7] * g2));
+        const float r2 = fmaf(R[2], g0, fmaf(R[5], g1, R[8] * g2));
+        const float* row = basis + m * 3 * D;
+        float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < kChainPerLane; ++j) {
+            const int d = lane + 32 * j;
+            if (d < D) {
+                const float b0 = __ldcs(row + d), b1 = __ldcs(row + D + d), b2 = __ldcs(row + 2 * D + d);
+                const float pd = s_p[d];
+                acc[0] = fmaf(b0, pd, acc[0]);
+                acc[1] = fmaf(b1, pd, acc[1]);
+                acc[2] = fmaf(b2, pd, acc[2]);
+                dp[j] = fmaf(b0, r0, fmaf(b1, r1, fmaf(b2, r2, dp[j])));
+            }
+        }
+        float xr[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xr[c] = warp_sum(acc[c]) + __ldg(base + 3 * m + c);
+        const float gg[3] = {g0, g1, g2};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) ex[3 * a + b] = fmaf(gg[a], xr[b], ex[3 * a + b]);
+            if (!direction) ex[9 + a] += gg[a];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kChainPerLane; ++j) {
+        const int d = lane + 32 * j;
+        if (d < D) s_dp[warp][d] = dp[j];
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < kChainExtra; ++i) s_ex[warp][i] = ex[i];
+    }
+    __syncthreads();
+    const int E = D + kChainExtra;
+    for (int i = threadIdx.x; i < E; i += kChainThreads) {
+        float t = 0.f;
+        for (int w = 0; w < kChainWarps; ++w) t += i < D ? s_dp[w][i] : s_ex[w][i - D];
+        partials[static_cast<int64_t>(blockIdx.x) * E + i] = t;
+    }
+}
+
+// Fixed-order sum of the blocks' partial rows; thread 0 then maps dL/dR to
+// dL/dw in double precision:
+// dR/dw_a = A K_a + B (K_a K + K K_a) + (A'/th) w_a K + (B'/th) w_a K^2.
+__global__ void __launch_bounds__(kChainThreads) chain_reduce_kernel(const float* partials, int nblk, int D,
+                                                                     const float* pose, float* d_p, float* d_pose) {
+    __shared__ float s_ex[kChainExtra];
+    const int E = D + kChainExtra;
+    for (int i = threadIdx.x; i < E; i += kChainThreads) {
+        float t = 0.f;
+        for (int b = 0; b < nblk; ++b) t += partials[static_cast<int64_t>(b) * E + i];
+        if (i < D) d_p[i] = t;
+        else s_ex[i - D] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double w[3] = {pose[0], pose[1], pose[2]};
+    const double t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double A, B, dA, dB;
+    if (t2 < 1e-6) {
+        A = 1.0 - t2 / 6.0 + t2 * t2 / 120.0;
+        B = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
+        dA = -1.0 / 3.0 + t2 / 30.0;
+        dB = -1.0 / 12.0 + t2 / 180.0;
+    } else {
+        const double th = sqrt(t2);
+        double s, c;
+        sincos(th, &s, &c);
+        A = s / th;
+        B = (1.0 - c) / t2;
+        dA = (th * c - s) / (t2 * th);
+        dB = (th * s - 2.0 * (1.0 - c)) / (t2 * t2);
+    }
+    const double K[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
+    double K2[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) K2[3 * r + c] = w[r] * w[c] - (r == c ? t2 : 0.0);
+    for (int a = 0; a < 3; ++a) {
+        double Ka[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        // [e_a]x
+        if (a == 0) { Ka[5] = -1.0; Ka[7] = 1.0; }
+        if (a == 1) { Ka[2] = 1.0; Ka[6] = -1.0; }
+        if (a == 2) { Ka[1] = -1.0; Ka[3] = 1.0; }
+        double acc = 0.0;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double kk = 0.0;
+                for (int q = 0; q < 3; ++q) kk += Ka[3 * r + q] * K[3 * q + c] + K[3 * r + q] * Ka[3 * q + c];
+                const double G = A * Ka[3 * r + c] + B * kk + dA * w[a] * K[3 * r + c] + dB * w[a] * K2[3 * r + c];
+                acc += G * s_ex[3 * r + c];
+            }
+        d_pose[a] = static_cast<float>(acc);
+    }
+    for (int a = 0; a < 3; ++a) d_pose[3 + a] = s_ex[9 + a];
+}
+
+int chain_grid(int64_t M) {
+    const int64_t need = (M + kChainWarps - 1) / kChainWarps;
+    return static_cast<int>(need < kChainMaxBlocks ? (need > 0 ? need : 1) : kChainMaxBlocks);
+}
+
+shs_status check_chain(const float* base, const float* basis, int64_t M, int32_t D, const float* p,
+                       const float* pose) {
+    if (M < 0) return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "M < 0"));
+    if (D < 1 || D > kChainMaxD)
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "D %d not in 1..%d", D, kChainMaxD));
+    if (M > (int64_t(1) << 40) / (3 * static_cast<int64_t>(D)))
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "M x 3 x D too large"));
+    if (!p || !pose) return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL p or pose"));
+    if (M > 0 && (!base || !basis))
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL base or basis"));
+    return SHS_OK;
+}
+
+}  // namespace
+
+extern "C" size_t shs_chain_workspace_bytes(int64_t n_rows, int32_t n_params) {
+    if (n_rows < 0 || n_params < 1 || n_params > kChainMaxD) return 0;
+    return sizeof(float) * static_cast<size_t>(chain_grid(n_rows)) * (n_params + kChainExtra);
+}
+
+extern "C" shs_status shs_chain_forward(const float* base, const float* basis, int64_t n_rows, int32_t n_params,
+                                        const float* p, const float* pose, int32_t direction, float* x_rest,
+                                        float* x, void* stream) {
+    shs_status st = check_chain(base, basis, n_rows, n_params, p, pose);
+    if (st != SHS_OK) return st;
+    if (direction != 0 && direction != 1)
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "direction must be 0 or 1"));
+    if (n_rows == 0) return SHS_OK;
+    if (!x) return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL x"));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t need = (n_rows + kChainWarps - 1) / kChainWarps;
+    const int grid = static_cast<int>(need < 152 * 64 ? need : 152 * 64);
+    chain_forward_kernel<<<grid, kChainThreads, 0, s>>>(base, basis, n_rows, n_params, p, pose, direction, x_rest, x);
+    shs::count_launch();
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SHS_OK : static_cast<shs_status>(shs::report_cuda(e, "chain forward"));
+}
+
+extern "C" shs_status shs_chain_backward(const float* base, const float* basis, int64_t n_rows, int32_t n_params,
+                                         const float* p, const float* pose, int32_t direction, const float* d_x,
+                                         float* d_p, float* d_pose, void* workspace, size_t workspace_bytes,
+                                         void* stream) {
+    shs_status st = check_chain(base, basis, n_rows, n_params, p, pose);
+    if (st != SHS_OK) return st;
+    if (direction != 0 && direction != 1)
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "direction must be 0 or 1"));
+    if (!d_p || !d_pose || !workspace)
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL d_p, d_pose or workspace"));
+    if (n_rows > 0 && !d_x) return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL d_x"));
+    if (reinterpret_cast<uintptr_t>(workspace) & 15u)
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "workspace not 16-byte aligned"));
+    if (workspace_bytes < shs_chain_workspace_bytes(n_rows, n_params))
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "workspace of %zu bytes < %zu needed",
+                                                         workspace_bytes,
+                                                         shs_chain_workspace_bytes(n_rows, n_params)));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float* partials = static_cast<float*>(workspace);
+    int nblk = 0;
+    if (n_rows > 0) {
+        nblk = chain_grid(n_rows);
+        chain_backward_kernel<<<nblk, kChainThreads, 0, s>>>(base, basis, n_rows, n_params, p, pose, direction, d_x,
+                                                             partials);
+        shs::count_launch();
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return static_cast<shs_status>(shs::report_cuda(e, "chain backward"));
+    }
+    chain_reduce_kernel<<<1, kChainThreads, 0, s>>>(partials, nblk, n_params, pose, d_p, d_pose);
+    shs::count_launch();
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SHS_OK : static_cast<shs_status>(shs::report_cuda(e, "chain reduce"));
+}

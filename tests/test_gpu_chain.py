@@ -82,11 +82,11 @@ def _gpu(m, p0, poses0, wts, cfg_kw):
     # per-point squaring counts of every view, for the oracle
     ks = []
     with torch.no_grad():
-        v = chain.affine_deform(T["v0"], T["A_v"], p)
-        n = chain.affine_deform(T["n0"], T["A_n"], p)
-        c = chain.affine_deform(T["c0"], T["A_c"], p)
         for i, sc in enumerate(scenes):
-            pv, pn, pc = chain.pose(v, n, c, poses[i, :3], poses[i, 3:])
+            q = poses[i].detach()
+            pv = chain.deform_pose(T["v0"], T["A_v"], p.detach(), q)
+            pn = chain.deform_pose(T["n0"], T["A_n"], p.detach(), q, direction=True)
+            pc = chain.deform_pose(T["c0"], T["A_c"], p.detach(), q)
             sc.update(pc, T["radii"], T["light"])
             sv = sc.new_saved(pv.shape[0], dev)
             sc.shade(pv, pn, T["albedo"], saved=sv)
