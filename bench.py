@@ -687,6 +687,108 @@ def bench_heightfield(args, world, rank, local):
                 precisions=out)
 
 
+def bench_chain(args, world, rank, local):
+    """Mesh-deformation batch: 16 views x 50,000 vertices, 200 spheres, 60
+    deformation parameters, n = 4.  A step renders every view (chain kernels
+    -> shading) and back-propagates to the parameters and poses.  The chain
+    kernels are HBM-bound (the [M, 3, D] basis read once per pass): their
+    bytes/s, with L2 flushed before each timed launch, against the measured
+    copy bandwidth."""
+    import ctypes
+    import torch
+    from paper_2104_00359_gb300 import Config, _lib, chain, synthetic
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = _lib.load()
+    m = synthetic.mesh_deformation_scene(seed=2 + rank)
+    T = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in m.items() if k != "n_bands"}
+    M, D = int(T["v0"].shape[0]), int(T["A_v"].shape[2])
+    V, N = int(T["poses"].shape[0]), int(T["c0"].shape[0])
+    stream = torch.cuda.current_stream()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    flush = torch.empty(256 * 2 ** 20 // 4, device=dev)
+    # chain kernels alone, on the vertex array
+    p = torch.from_numpy(np.random.default_rng(1).normal(0, 1, D).astype(np.float32)).to(dev)
+    q = T["poses"][0].contiguous()
+    x = torch.empty((M, 3), device=dev)
+    g = torch.randn((M, 3), device=dev)
+    d_p, d_q = torch.empty(D, device=dev), torch.empty(6, device=dev)
+    need = int(lib.shs_chain_workspace_bytes(M, D))
+    ws = torch.empty(need // 4 + 4, device=dev)
+    tf, tb = [], []
+    for it in range(args.warmup + max(3, min(args.steps, 50))):
+        flush.zero_()
+        e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+        e0.record(stream)
+        _lib.check(lib.shs_chain_forward(_lib.ptr(T["v0"]), _lib.ptr(T["A_v"]), M, D, _lib.ptr(p), _lib.ptr(q), 0,
+                                         None, _lib.ptr(x), sptr), "shs_chain_forward")
+        e1.record(stream)
+        flush.zero_()
+        e2.record(stream)
+        _lib.check(lib.shs_chain_backward(_lib.ptr(T["v0"]), _lib.ptr(T["A_v"]), M, D, _lib.ptr(p), _lib.ptr(q), 0,
+                                          _lib.ptr(g), _lib.ptr(d_p), _lib.ptr(d_q), _lib.ptr(ws), need, sptr),
+                   "shs_chain_backward")
+        e3.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            tf.append(e0.elapsed_time(e1))
+            tb.append(e2.elapsed_time(e3))
+    fwd_ms, bwd_ms = statistics.fmean(tf), statistics.fmean(tb)
+    chain_bytes = 4 * (M * 3 * D + 2 * M * 3)          # basis + base in, x out (backward: g in)
+    # the whole step: every view through the chain kernels and the shading path
+    pp = torch.zeros(D, device=dev, requires_grad=True)
+    poses = T["poses"].clone().requires_grad_(True)
+    cfg = Config(n_bands=m["n_bands"])
+    scenes = chain.make_view_scenes(V, T["c0"], T["radii"], T["light"], cfg)
+    W = torch.randn((V, M, 3), device=dev)
+    steps = max(3, min(args.steps, 20))
+    launches0 = None
+    times = []
+    with ClockSampler(local) as clk:
+        for it in range(args.warmup + steps):
+            if it == args.warmup:
+                launches0 = lib.shs_launch_count()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            pp.grad = None
+            poses.grad = None
+            e0.record(stream)
+            B = chain.render_views(pp, poses, T, T["radii"], T["light"], T["albedo"], scenes)
+            (B * W).sum().backward()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+    for sc in scenes:
+        sc.close()
+    step_ms = statistics.fmean(times)
+    hbm = load_peaks().get("hbm_gbs")
+    ach = chain_bytes / (fwd_ms * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        from oracle import chain_oracle as CO
+        gn = g.cpu().numpy()
+        t = time.perf_counter()
+        CO.deform_pose(m["v0"], m["A_v"], p.cpu().numpy(), q.cpu().numpy())
+        CO.deform_pose_backward(m["v0"], m["A_v"], p.cpu().numpy(), q.cpu().numpy(), gn)
+        dt = time.perf_counter() - t
+        cpu = {"value": 2 * chain_bytes / dt, "unit": "bytes/s", "cores": 1, "kind": "oracle",
+               "sample": f"chain forward + backward on the {M} x 3 x {D} vertex basis, float64 numpy, {dt:.1f} s"}
+    return dict(
+        metric="mesh-deformation batch: point-sphere pairs/sec fwd+bwd through chain + shading (16 views)",
+        value=V * M * N / (step_ms * 1e-3), unit="pairs/s", n_gpus=world, steps=steps, warmup=args.warmup,
+        ms_per_step=step_ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+        data="synthetic", impl="ours",
+        config={"workload": f"mesh deformation {V} views x {M} vertices, {N} spheres, {D} parameters, n_bands=4",
+                "views": V, "vertices": M, "spheres": N, "params": D, "l2_flush_between_chain_launches": True},
+        chain_kernels={"fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "bytes_per_launch": chain_bytes},
+        roofline={"bound": "hbm", "kernel": "chain_forward_kernel (vertices)", "achieved": ach, "peak": hbm,
+                  "unit": "GB/s", "frac": ach / hbm if hbm else None, "traffic": None,
+                  "backward": {"achieved": chain_bytes / (bwd_ms * 1e-3) / 1e9,
+                               "frac": chain_bytes / (bwd_ms * 1e-3) / 1e9 / hbm if hbm else None}},
+        gpu_launches=(lib.shs_launch_count() - launches0) if launches0 is not None else None,
+        clocks=clk.summary(), cpu_baseline=cpu)
+
+
 def bench_envmap(args, world, rank, local):
     """Eq. 9 projection of an equirectangular HDR map (default 4096 x 8192,
     402 MB, larger than L2) onto SH lighting, n = 8 and n = 4.  The kernel
@@ -783,7 +885,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--atomic", action="store_true", help="unordered (atomic) scene-gradient reduction")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--workload", choices=("capsule", "serving", "heightfield", "envmap"), default="capsule",
+    ap.add_argument("--workload", choices=("capsule", "serving", "heightfield", "envmap", "chain"), default="capsule",
                     help="capsule: the 512x512 G-buffer step (default); serving: the mixed request stream")
     ap.add_argument("--hf-res", type=int, default=1024, help="height-field grid side (heightfield workload)")
     ap.add_argument("--precisions", default="fp32,bf16_split_tc,fp16_split_tc,fp32_projexp,fp32_oltable",
@@ -803,6 +905,8 @@ def main():
         res = bench_heightfield(args, world, rank, local)
     elif args.workload == "envmap":
         res = bench_envmap(args, world, rank, local)
+    elif args.workload == "chain":
+        res = bench_chain(args, world, rank, local)
     else:
         res = bench_ours(args, world, rank, local, dist)
     if rank == 0 and res is not None:

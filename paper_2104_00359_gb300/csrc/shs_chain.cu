@@ -25,7 +25,6 @@ namespace {
 constexpr int kChainWarps = 8;                  // 256-thread blocks
 constexpr int kChainThreads = 32 * kChainWarps;
 constexpr int kChainMaxD = SHS_CHAIN_MAX_PARAMS;
-constexpr int kChainPerLane = kChainMaxD / 32;  // parameters a lane accumulates
 constexpr int kChainMaxBlocks = 152 * 4;
 constexpr int kChainExtra = 12;                 // dL/dR (9, row-major) and dL/dt (3)
 
@@ -66,93 +65,148 @@ __device__ __forceinline__ void rotation(const float* pose, float* R) {
     R[8] = 1.f + B * (wz * wz - t2);
 }
 
-__global__ void __launch_bounds__(kChainThreads) chain_forward_kernel(const float* base, const float* basis, int64_t M,
+// Rows per warp and step: all of their basis loads are issued before any is
+// used, so a warp keeps RW * 3 * PL independent loads in flight.
+#ifndef SHS_CHAIN_ROWS
+#define SHS_CHAIN_ROWS 4
+#endif
+#ifdef SHS_CHAIN_MINB
+#define SHS_CHAIN_BOUNDS __launch_bounds__(kChainThreads, SHS_CHAIN_MINB)
+#else
+#define SHS_CHAIN_BOUNDS __launch_bounds__(kChainThreads)
+#endif
+constexpr int kChainRowsPerStep = SHS_CHAIN_ROWS;
+
+// PL: parameters per lane (D <= 32 PL).  Loads beyond D or M read nothing and
+// count as zero.
+template <int PL>
+__global__ void SHS_CHAIN_BOUNDS chain_forward_kernel(const float* base, const float* basis, int64_t M,
                                                                       int D, const float* p, const float* pose,
                                                                       int direction, float* x_rest, float* x) {
-    __shared__ float s_p[kChainMaxD];
-    for (int d = threadIdx.x; d < D; d += kChainThreads) s_p[d] = __ldg(p + d);
+    constexpr int RW = kChainRowsPerStep;
+    __shared__ float s_p[32 * PL];
+    for (int d = threadIdx.x; d < 32 * PL; d += kChainThreads) s_p[d] = d < D ? __ldg(p + d) : 0.f;
     __syncthreads();
     float R[9];
     rotation(pose, R);
     const float tx = direction ? 0.f : __ldg(pose + 3), ty = direction ? 0.f : __ldg(pose + 4),
                 tz = direction ? 0.f : __ldg(pose + 5);
     const int lane = threadIdx.x & 31;
-    const int64_t warps = static_cast<int64_t>(gridDim.x) * kChainWarps;
-    for (int64_t m = static_cast<int64_t>(blockIdx.x) * kChainWarps + (threadIdx.x >> 5); m < M; m += warps) {
-        const float* row = basis + m * 3 * D;
-        float acc[3] = {0.f, 0.f, 0.f};
+    const int64_t step = static_cast<int64_t>(gridDim.x) * kChainWarps * RW;
+    for (int64_t m0 = (static_cast<int64_t>(blockIdx.x) * kChainWarps + (threadIdx.x >> 5)) * RW; m0 < M;
+         m0 += step) {
+        float b[RW][3][PL];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            for (int d = lane; d < D; d += 32) acc[c] = fmaf(__ldcs(row + c * D + d), s_p[d], acc[c]);
+        for (int r = 0; r < RW; ++r) {
+            const int64_t m = m0 + r;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c] = warp_sum(acc[c]) + __ldg(base + 3 * m + c);
-        if (lane == 0) {
-            if (x_rest) {
+            for (int c = 0; c < 3; ++c) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) x_rest[3 * m + c] = acc[c];
+                for (int j = 0; j < PL; ++j) {
+                    const int d = lane + 32 * j;
+                    b[r][c][j] = (m < M && d < D) ? __ldcs(basis + (m * 3 + c) * D + d) : 0.f;
+                }
             }
-            x[3 * m] = fmaf(R[0], acc[0], fmaf(R[1], acc[1], fmaf(R[2], acc[2], tx)));
-            x[3 * m + 1] = fmaf(R[3], acc[0], fmaf(R[4], acc[1], fmaf(R[5], acc[2], ty)));
-            x[3 * m + 2] = fmaf(R[6], acc[0], fmaf(R[7], acc[1], fmaf(R[8], acc[2], tz)));
+        }
+        float acc[RW][3];
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float t = 0.f;
+#pragma unroll
+                for (int j = 0; j < PL; ++j) t = fmaf(b[r][c][j], s_p[lane + 32 * j], t);
+                acc[r][c] = warp_sum(t);
+            }
+        }
+        if (lane < RW) {
+            // lane r writes row m0 + r (register arrays indexed by a compile-time r)
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const int64_t m = m0 + r;
+                if (lane != r || m >= M) continue;
+                const float a0 = acc[r][0] + __ldg(base + 3 * m), a1 = acc[r][1] + __ldg(base + 3 * m + 1),
+                            a2 = acc[r][2] + __ldg(base + 3 * m + 2);
+                if (x_rest) {
+                    x_rest[3 * m] = a0;
+                    x_rest[3 * m + 1] = a1;
+                    x_rest[3 * m + 2] = a2;
+                }
+                x[3 * m] = fmaf(R[0], a0, fmaf(R[1], a1, fmaf(R[2], a2, tx)));
+                x[3 * m + 1] = fmaf(R[3], a0, fmaf(R[4], a1, fmaf(R[5], a2, ty)));
+                x[3 * m + 2] = fmaf(R[6], a0, fmaf(R[7], a1, fmaf(R[8], a2, tz)));
+            }
         }
     }
 }
 
 // Partial sums of one block: [0, D) dL/dp, then dL/dR (9), dL/dt (3).
-__global__ void __launch_bounds__(kChainThreads) chain_backward_kernel(const float* base, const float* basis, int64_t M,
+template <int PL>
+__global__ void SHS_CHAIN_BOUNDS chain_backward_kernel(const float* base, const float* basis, int64_t M,
                                                                        int D, const float* p, const float* pose,
                                                                        int direction, const float* g, float* partials) {
-    __shared__ float s_p[kChainMaxD];
-    __shared__ float s_dp[kChainWarps][kChainMaxD];
+    constexpr int RW = kChainRowsPerStep;
+    __shared__ float s_p[32 * PL];
+    __shared__ float s_dp[kChainWarps][32 * PL];
     __shared__ float s_ex[kChainWarps][kChainExtra];
-    for (int d = threadIdx.x; d < D; d += kChainThreads) s_p[d] = __ldg(p + d);
+    for (int d = threadIdx.x; d < 32 * PL; d += kChainThreads) s_p[d] = d < D ? __ldg(p + d) : 0.f;
     __syncthreads();
     float R[9];
     rotation(pose, R);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float dp[kChainPerLane];
+    float dp[PL];
 #pragma unroll
-    for (int j = 0; j < kChainPerLane; ++j) dp[j] = 0.f;
+    for (int j = 0; j < PL; ++j) dp[j] = 0.f;
     float ex[kChainExtra];
 #pragma unroll
     for (int i = 0; i < kChainExtra; ++i) ex[i] = 0.f;
-    const int64_t warps = static_cast<int64_t>(gridDim.x) * kChainWarps;
-    for (int64_t m = static_cast<int64_t>(blockIdx.x) * kChainWarps + warp; m < M; m += warps) {
-        const float g0 = __ldg(g + 3 * m), g1 = __ldg(g + 3 * m + 1), g2 = __ldg(g + 3 * m + 2);
-        // R^T g: the gradient in the rest frame
-        const float r0 = fmaf(R[0], g0, fmaf(R[3], g1, R[6] * g2));
-        const float r1 = fmaf(R[1], g0, fmaf(R[4], g1, R[7] * g2));
-        const float r2 = fmaf(R[2], g0, fmaf(R[5], g1, R[8] * g2));
-        const float* row = basis + m * 3 * D;
-        float acc[3] = {0.f, 0.f, 0.f};
+    const int64_t step = static_cast<int64_t>(gridDim.x) * kChainWarps * RW;
+    for (int64_t m0 = (static_cast<int64_t>(blockIdx.x) * kChainWarps + warp) * RW; m0 < M; m0 += step) {
+        float b[RW][3][PL], gg[RW][3];
 #pragma unroll
-        for (int j = 0; j < kChainPerLane; ++j) {
-            const int d = lane + 32 * j;
-            if (d < D) {
-                const float b0 = __ldcs(row + d), b1 = __ldcs(row + D + d), b2 = __ldcs(row + 2 * D + d);
-                const float pd = s_p[d];
-                acc[0] = fmaf(b0, pd, acc[0]);
-                acc[1] = fmaf(b1, pd, acc[1]);
-                acc[2] = fmaf(b2, pd, acc[2]);
-                dp[j] = fmaf(b0, r0, fmaf(b1, r1, fmaf(b2, r2, dp[j])));
+        for (int r = 0; r < RW; ++r) {
+            const int64_t m = m0 + r;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                gg[r][c] = m < M ? __ldg(g + 3 * m + c) : 0.f;
+#pragma unroll
+                for (int j = 0; j < PL; ++j) {
+                    const int d = lane + 32 * j;
+                    b[r][c][j] = (m < M && d < D) ? __ldcs(basis + (m * 3 + c) * D + d) : 0.f;
+                }
             }
         }
-        float xr[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) xr[c] = warp_sum(acc[c]) + __ldg(base + 3 * m + c);
-        const float gg[3] = {g0, g1, g2};
+        for (int r = 0; r < RW; ++r) {
+            // R^T g: the gradient in the rest frame
+            const float r0 = fmaf(R[0], gg[r][0], fmaf(R[3], gg[r][1], R[6] * gg[r][2]));
+            const float r1 = fmaf(R[1], gg[r][0], fmaf(R[4], gg[r][1], R[7] * gg[r][2]));
+            const float r2 = fmaf(R[2], gg[r][0], fmaf(R[5], gg[r][1], R[8] * gg[r][2]));
+            float xr[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
+            for (int c = 0; c < 3; ++c) {
+                float t = 0.f;
 #pragma unroll
-            for (int b = 0; b < 3; ++b) ex[3 * a + b] = fmaf(gg[a], xr[b], ex[3 * a + b]);
-            if (!direction) ex[9 + a] += gg[a];
+                for (int j = 0; j < PL; ++j) t = fmaf(b[r][c][j], s_p[lane + 32 * j], t);
+                xr[c] = warp_sum(t);
+            }
+#pragma unroll
+            for (int j = 0; j < PL; ++j) dp[j] = fmaf(b[r][0][j], r0, fmaf(b[r][1][j], r1, fmaf(b[r][2][j], r2, dp[j])));
+            const int64_t m = m0 + r;
+            if (m < M) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) xr[c] += __ldg(base + 3 * m + c);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) ex[3 * a + c] = fmaf(gg[r][a], xr[c], ex[3 * a + c]);
+                    if (!direction) ex[9 + a] += gg[r][a];
+                }
+            }
         }
     }
 #pragma unroll
-    for (int j = 0; j < kChainPerLane; ++j) {
-        const int d = lane + 32 * j;
-        if (d < D) s_dp[warp][d] = dp[j];
-    }
+    for (int j = 0; j < PL; ++j) s_dp[warp][lane + 32 * j] = dp[j];
     if (lane == 0) {
 #pragma unroll
         for (int i = 0; i < kChainExtra; ++i) s_ex[warp][i] = ex[i];
@@ -222,9 +276,53 @@ __global__ void __launch_bounds__(kChainThreads) chain_reduce_kernel(const float
 }
 
 int chain_grid(int64_t M) {
-    const int64_t need = (M + kChainWarps - 1) / kChainWarps;
+    const int64_t per = static_cast<int64_t>(kChainWarps) * kChainRowsPerStep;
+    const int64_t need = (M + per - 1) / per;
     return static_cast<int>(need < kChainMaxBlocks ? (need > 0 ? need : 1) : kChainMaxBlocks);
 }
+
+template <template <int> class F, typename... A>
+void by_lanes(int D, A&&... args) {
+    if (D <= 32) F<1>::go(args...);
+    else if (D <= 64) F<2>::go(args...);
+    else if (D <= 128) F<4>::go(args...);
+    else F<8>::go(args...);
+}
+// Blocks of `kernel` the device holds at once (one wave): the kernels loop
+// over their rows, so a single resident wave avoids paying block start-up per
+// four rows.  Falls back to 152 blocks if the occupancy query fails.
+template <typename K>
+int resident_blocks(K kernel) {
+    int dev = 0, sms = 152, per = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kChainThreads, 0) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        return 152;
+    }
+    return sms * per;
+}
+
+int clamp_grid(int64_t need, int resident) {
+    const int64_t g = need < resident ? need : resident;
+    return static_cast<int>(g > 0 ? g : 1);
+}
+
+template <int PL> struct Fwd {
+    static void go(int64_t need, cudaStream_t s, const float* base, const float* basis, int64_t M, int D,
+                   const float* p, const float* pose, int dir, float* xr, float* x) {
+        static const int resident = resident_blocks(chain_forward_kernel<PL>);
+        chain_forward_kernel<PL><<<clamp_grid(need, resident), kChainThreads, 0, s>>>(base, basis, M, D, p, pose, dir,
+                                                                                       xr, x);
+    }
+};
+template <int PL> struct Bwd {
+    static void go(int64_t need, cudaStream_t s, const float* base, const float* basis, int64_t M, int D,
+                   const float* p, const float* pose, int dir, const float* g, float* partials, int* nblk) {
+        static const int resident = resident_blocks(chain_backward_kernel<PL>);
+        *nblk = clamp_grid(need < kChainMaxBlocks ? need : kChainMaxBlocks, resident);
+        chain_backward_kernel<PL><<<*nblk, kChainThreads, 0, s>>>(base, basis, M, D, p, pose, dir, g, partials);
+    }
+};
 
 shs_status check_chain(const float* base, const float* basis, int64_t M, int32_t D, const float* p,
                        const float* pose) {
@@ -256,9 +354,8 @@ extern "C" shs_status shs_chain_forward(const float* base, const float* basis, i
     if (n_rows == 0) return SHS_OK;
     if (!x) return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL x"));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int64_t need = (n_rows + kChainWarps - 1) / kChainWarps;
-    const int grid = static_cast<int>(need < 152 * 64 ? need : 152 * 64);
-    chain_forward_kernel<<<grid, kChainThreads, 0, s>>>(base, basis, n_rows, n_params, p, pose, direction, x_rest, x);
+    const int64_t per = static_cast<int64_t>(kChainWarps) * kChainRowsPerStep;
+    by_lanes<Fwd>(n_params, (n_rows + per - 1) / per, s, base, basis, n_rows, n_params, p, pose, direction, x_rest, x);
     shs::count_launch();
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SHS_OK : static_cast<shs_status>(shs::report_cuda(e, "chain forward"));
@@ -285,9 +382,9 @@ extern "C" shs_status shs_chain_backward(const float* base, const float* basis, 
     float* partials = static_cast<float*>(workspace);
     int nblk = 0;
     if (n_rows > 0) {
-        nblk = chain_grid(n_rows);
-        chain_backward_kernel<<<nblk, kChainThreads, 0, s>>>(base, basis, n_rows, n_params, p, pose, direction, d_x,
-                                                             partials);
+        const int64_t per = static_cast<int64_t>(kChainWarps) * kChainRowsPerStep;
+        by_lanes<Bwd>(n_params, (n_rows + per - 1) / per, s, base, basis, n_rows, n_params, p, pose, direction, d_x,
+                      partials, &nblk);
         shs::count_launch();
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return static_cast<shs_status>(shs::report_cuda(e, "chain backward"));
