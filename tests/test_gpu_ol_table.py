@@ -150,3 +150,26 @@ def test_table_scene_in_the_serving_batch():
     # and the table jobs follow the oracle's table method
     ref = O.shade_forward(_cfg(4), *[jobs[0][1][x] for x in FIELDS])["radiance"]
     assert rel_err(got[0][0], ref).max() <= TOL
+
+
+def test_ol_table_with_horizon_cull_backward():
+    """The table step and horizon culling together (the fused backward is
+    compiled per combination); points whose cull decision is within rounding
+    of the tangent plane are left out, as in the culling tests."""
+    sc = S.random_scene(890, 300, 33, 4, inside_fraction=0.05)
+    nh = sc["normals"].astype(np.float64)
+    nh /= np.linalg.norm(nh, axis=1, keepdims=True)
+    d = sc["centers"].astype(np.float64)[None] - sc["points"].astype(np.float64)[:, None]
+    margin = np.einsum("pjc,pc->pj", d, nh) + sc["radii"].astype(np.float64)[None]
+    keep = np.all(np.abs(margin) > 1e-4 * (1.0 + np.abs(d).sum(-1)), axis=1)
+    for k in ("points", "normals", "albedo"):
+        sc[k] = np.ascontiguousarray(sc[k][keep])
+    cfg = _cfg(4, horizon_cull=True)
+    dB = np.random.default_rng(11).normal(size=sc["points"].shape).astype(np.float32)
+    B, k, f, g, status = gpu_run(sc, cfg, dB=dB)
+    assert status == 0
+    ref = O.shade_backward(cfg, *[sc[x] for x in FIELDS], dB)
+    assert rel_err(B, ref["forward"]["radiance"]).max() <= TOL
+    for name in ("d_light", "d_albedo", "d_centers", "d_radii", "d_points", "d_normals"):
+        err = grad_err(name, g[name], ref)
+        assert err.max() <= TOL, f"{name}: max err {err.max():.3e}"
