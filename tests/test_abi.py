@@ -131,3 +131,31 @@ def test_envmap_projection_argument_checks_without_gpu(lib):
                  (one, 16, 32, 4, one, one, need - 4), (one, 16, 32, 4, one, ctypes.c_void_p(20), need)):
         assert lib.shs_project_envmap(*args, None) == 1, args
         assert lib.shs_last_error()
+
+
+def test_chain_argument_checks_without_gpu(lib):
+    """Size query and argument validation of the scene-chain calls run on the
+    host (no device call for a rejected or empty request)."""
+    assert lib.shs_chain_workspace_bytes(-1, 4) == 0
+    assert lib.shs_chain_workspace_bytes(10, 0) == 0
+    assert lib.shs_chain_workspace_bytes(10, 257) == 0
+    assert lib.shs_chain_workspace_bytes(0, 60) == 4 * (60 + 12)           # one partial row
+    assert lib.shs_chain_workspace_bytes(1000, 60) == 4 * 32 * (60 + 12)    # 32 blocks of 8 warps x 4 rows
+    assert lib.shs_chain_workspace_bytes(50000, 60) == 4 * 608 * (60 + 12)  # capped at 608 partial rows
+    assert lib.shs_chain_workspace_bytes(10 ** 7, 60) == 4 * 608 * (60 + 12)
+    one = ctypes.c_void_p(16)
+    for args in ((one, one, -1, 4, one, one, 0, None, one), (one, one, 5, 0, one, one, 0, None, one),
+                 (one, one, 5, 257, one, one, 0, None, one), (one, one, 5, 4, None, one, 0, None, one),
+                 (one, one, 5, 4, one, None, 0, None, one), (None, one, 5, 4, one, one, 0, None, one),
+                 (one, one, 5, 4, one, one, 2, None, one), (one, one, 5, 4, one, one, 0, None, None)):
+        assert lib.shs_chain_forward(*args, None) == 1, args
+        assert lib.shs_last_error()
+    assert lib.shs_chain_forward(None, None, 0, 4, one, one, 0, None, None, None) == 0
+    need = lib.shs_chain_workspace_bytes(5, 4)
+    for args in ((one, one, 5, 4, one, one, 0, None, one, one, one, need),
+                 (one, one, 5, 4, one, one, 0, one, None, one, one, need),
+                 (one, one, 5, 4, one, one, 0, one, one, one, None, need),
+                 (one, one, 5, 4, one, one, 0, one, one, one, one, need - 4),
+                 (one, one, 5, 4, one, one, 0, one, one, one, ctypes.c_void_p(20), need),
+                 (one, one, 5, 4, one, one, 3, one, one, one, one, need)):
+        assert lib.shs_chain_backward(*args, None) == 1, args
