@@ -634,3 +634,24 @@ def test_stored_8_band_table_beats_the_gaussian_step_on_held_out_points():
     ho = F.Problem(8, F.ensemble(8, 150, 7), rule=O.sphere_quadrature(40, 80))
     ga, gb = F.gaussian_table(a.shape[0], smax)
     assert ho.objective(a, b, smax) < 0.6 * ho.objective(ga, gb, smax)
+
+
+def test_table_lookup_matches_numpy_interp():
+    """a(s), b(s) agree with numpy's piecewise-linear interpolation (which
+    clamps past the ends) on random tables, and the slopes with its one-sided
+    differences away from nodes."""
+    rng = np.random.default_rng(40)
+    M, smax = 17, 1.3
+    nodes = np.linspace(0.0, smax, M)
+    ta, tb = rng.normal(1.0, 0.1, M), rng.normal(1.0, 0.1, M)
+    cfg = O.Config(n_bands=2, exp_mode=2, ol_table=(ta, tb, smax))
+    s = rng.uniform(0.0, 1.6 * smax, 500)
+    a, b, da, db = O.ol_coefficients(cfg, s)
+    np.testing.assert_allclose(a, np.interp(s, nodes, ta), atol=1e-14)
+    np.testing.assert_allclose(b, np.interp(s, nodes, tb), atol=1e-14)
+    h = 1e-7
+    far = np.abs(s / (smax / (M - 1)) - np.round(s / (smax / (M - 1)))) > 1e-3
+    np.testing.assert_allclose(da[far], ((np.interp(s + h, nodes, ta) - np.interp(s - h, nodes, ta)) / (2 * h))[far],
+                               atol=1e-6)
+    np.testing.assert_allclose(db[far], ((np.interp(s + h, nodes, tb) - np.interp(s - h, nodes, tb)) / (2 * h))[far],
+                               atol=1e-6)
