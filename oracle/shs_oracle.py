@@ -43,7 +43,11 @@ Readings where the paper is silent (each is also a configuration field):
     4. k squarings V <- V * V (truncated triple product)
     5. V <- e0 * V
   Parity of these constants is unpinned against the paper (it prints none);
-  they are pinned to the definitions stated above.
+  they are pinned to the definitions stated above.  Variants: exp_mode 1
+  replaces steps 2-4 by the projection of exp(fh~) by a quadrature rule;
+  exp_mode 2 takes a and b in step 3 from a table a(s), b(s), s = |g|,
+  linear between its nodes and constant past the last (``ol_table``; the
+  fitted tables come from oracle/fit_ol_table.py).
 """
 
 from __future__ import annotations
