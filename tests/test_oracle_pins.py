@@ -655,3 +655,21 @@ def test_table_lookup_matches_numpy_interp():
                                atol=1e-6)
     np.testing.assert_allclose(db[far], ((np.interp(s + h, nodes, tb) - np.interp(s - h, nodes, tb)) / (2 * h))[far],
                                atol=1e-6)
+
+
+def test_fit_script_command_line(tmp_path):
+    """The fit script's command line (as written into the table headers) runs
+    and writes a table that read_table reads back."""
+    import subprocess
+    import sys
+    from oracle import fit_ol_table as F
+    out = tmp_path / "t.txt"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-m", "oracle.fit_ol_table", "--n-bands", "3", "--nodes", "5",
+                        "--dirs", "60", "--out", str(out)], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    a, b, smax = F.read_table(str(out))
+    assert a.shape == (5,) and b.shape == (5,) and smax == 1.0
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(b))
+    with open(out) as fh:
+        assert "python -m oracle.fit_ol_table --n-bands 3 --nodes 5" in fh.read()
