@@ -199,7 +199,13 @@ shs_status shs_shade_backward_l2(shs_scene_t scene, int64_t n_points, const floa
  *   (different streams, or different host threads) race and corrupt each
  *   other's results; order them on one stream.
  *   The scene-level sums (d_light, d_centers, d_radii) are accumulated with
- *   atomics, so their last bits can differ from run to run.
+ *   atomics, so their last bits can differ from run to run; cfg->deterministic
+ *   = 1 returns SHS_ERR_UNSUPPORTED.
+ *   Errors on the device: a block whose bounded wait for its staged spheres
+ *   gives up sets a status word in the array and returns; the call then
+ *   leaves d_light, d_centers, d_radii and that block's per-point gradients
+ *   unwritten.  Read the word with shs_noalloc_device_status before the next
+ *   call on the device (each call clears it).
  * It calls no cudaMalloc, cudaFree or allocating library routine. */
 shs_status shs_shade_backward_noalloc(const shs_config* cfg, int32_t n_spheres,
                                       const float* centers, const float* radii,
@@ -209,6 +215,12 @@ shs_status shs_shade_backward_noalloc(const shs_config* cfg, int32_t n_spheres,
                                       const float* d_radiance, float* d_light,
                                       float* d_albedo, float* d_centers, float* d_radii,
                                       float* d_points, float* d_normals, void* stream);
+
+/* Synchronises `stream`, then reports and clears the device-side status word
+ * of shs_shade_backward_noalloc's static array on the current device: 0 = the
+ * last call's kernels raised nothing, otherwise that shs_status (e.g.
+ * SHS_ERR_TIMEOUT).  Allocates nothing. */
+shs_status shs_noalloc_device_status(void* stream, int32_t* device_status);
 
 /* ---- Batched shading for serving many jobs (continuous batching) ----------
  * A batch call runs the forward pass (Eq. 8) of up to 32 requests, each on its

@@ -66,6 +66,7 @@ _SIGS = {
     "shs_shade_backward_noalloc": (c_int32, [POINTER(ShsConfig), c_int32, c_void_p, c_void_p, c_void_p, c_int64,
                                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                              c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "shs_noalloc_device_status": (c_int32, [c_void_p, POINTER(c_int32)]),
     "shs_batch_create": (c_int32, [POINTER(c_void_p)]),
     "shs_batch_destroy": (c_int32, [c_void_p]),
     "shs_shade_batch": (c_int32, [c_void_p, POINTER(ShsRequest), c_int32, c_void_p]),

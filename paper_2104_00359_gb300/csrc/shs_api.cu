@@ -784,6 +784,16 @@ shs_status shs_scene_device_status(shs_scene_t sc, void* stream, int32_t* device
     cudaError_t e = cudaMemcpyAsync(&v, sc->status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemsetAsync(sc->status, 0, sizeof(int), s);
+    if (e == cudaSuccess && v != 0) {
+        // A block that gave up before adding its share left the unordered
+        // accumulators part-filled and their counters short of the grid: the
+        // next launch would finish early with stale sums.  Start them afresh.
+        e = cudaMemsetAsync(sc->partials, 0, sizeof(float) * sc->partial_stride, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sc->counter, 0, sizeof(unsigned int), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sc->batch_acc, 0, sizeof(float) * sc->partial_stride, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sc->batch_counter, 0, sizeof(unsigned int), s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "read device status");
     *device_status = v;
     return SHS_OK;

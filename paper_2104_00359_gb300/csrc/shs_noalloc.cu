@@ -72,6 +72,10 @@ extern "C" shs_status shs_shade_backward_noalloc(
     void* stream) {
     int st = shs::validate_config(cfg);
     if (st != SHS_OK) return static_cast<shs_status>(st);
+    if (cfg->deterministic)
+        return static_cast<shs_status>(shs::report_error(
+            SHS_ERR_UNSUPPORTED, "no-alloc backward: deterministic sums need per-block partials, which a fixed "
+                                 "array cannot hold for every grid; the sums here use atomics"));
     if (cfg->exp_mode == 2)
         return static_cast<shs_status>(shs::report_error(
             SHS_ERR_UNSUPPORTED, "no-alloc backward: exp_mode 2 needs a scene's coefficient table"));
@@ -163,4 +167,26 @@ extern "C" shs_status shs_shade_backward_noalloc(
     a.grid = static_cast<int>(tiles < max_grid ? tiles : max_grid);
     e = shs::launch_backward_nb(cfg->n_bands, a, s);
     return e == cudaSuccess ? SHS_OK : static_cast<shs_status>(shs::report_cuda(e, "launch no-alloc backward"));
+}
+
+// Reads and clears the status word of the current device's array: 0, or the
+// shs_status a kernel of the last no-alloc backward raised (SHS_ERR_TIMEOUT
+// when a block's bounded wait for its staged spheres gave up; that call's
+// scene-level sums and the failed tiles' per-point gradients were then not
+// written).  Synchronises `stream`.  Allocates nothing.
+extern "C" shs_status shs_noalloc_device_status(void* stream, int32_t* device_status) {
+    if (!device_status) return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL argument"));
+    float* scratch = nullptr;
+    const int st = scratch_for_current_device(&scratch);
+    if (st != SHS_OK) return static_cast<shs_status>(st);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int* status = reinterpret_cast<int*>(scratch + kStatusOff);
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return static_cast<shs_status>(shs::report_cuda(e, "read no-alloc status"));
+    *device_status = v;
+    return SHS_OK;
 }

@@ -17,6 +17,7 @@ from gpu_helpers import FIELDS, gpu_run, grad_err, oracle_k_consistent, rel_err
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
+TOL_GRAD_8 = 3e-4
 
 
 def _oracle_forward(sc, cfg, k):
@@ -104,10 +105,21 @@ def _check_backward(sc, cfg, saved=True, tol=TOL, want=None):
     return g, ref
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_backward_all_gradients(n):
+    """Every gradient output against the oracle, horizon culling off.  From 7
+    bands the triple products run through the quadrature and the adjoint runs
+    back through the k squarings, each doubling the relative rounding of its
+    operand: gradients there are gated at 3e-4 (the radiance stays at 1e-4)."""
     sc = S.random_scene(200 + n, 300, 9, n, inside_fraction=0.1)
-    _check_backward(sc, O.Config(n_bands=n))
+    _check_backward(sc, O.Config(n_bands=n), tol=TOL if n <= 6 else TOL_GRAD_8)
+
+
+@pytest.mark.parametrize("n", [7, 8])
+def test_backward_all_gradients_recompute(n):
+    """As above with saved = NULL: the split backward recomputes f."""
+    sc = S.random_scene(210 + n, 260, 11, n, inside_fraction=0.1)
+    _check_backward(sc, O.Config(n_bands=n), saved=False, tol=TOL_GRAD_8)
 
 
 def test_backward_plane_grid():

@@ -73,13 +73,18 @@ def test_mixed_batches_match_requests_alone():
         ref = alone[(r.job_id, r.op)]
         assert rel_err(res["radiance"], ref["radiance"]).max() <= TOL
         if r.op == "fwdbwd":
+            # the batched adjoint against the FP64 oracle, for the L2 loss of
+            # the radiance this request computed, and against the result alone
             sc = by_job[r.job_id]
-            dB = ref["radiance"].astype(np.float64) - jobs[r.job_id][2]
+            dB = res["radiance"].astype(np.float64) - jobs[r.job_id][2]
             o = O.shade_backward(O.Config(n_bands=sc["n_bands"]), *[sc[f] for f in FIELDS], dB)
             for name in ("d_light", "d_albedo", "d_centers", "d_radii"):
+                assert grad_err(name, res[name], o).max() <= TOL, (r.req_id, name, "vs oracle")
                 base = dict(o)
                 base[name] = ref[name]
-                assert grad_err(name, res[name], base).max() <= TOL, (r.req_id, name)
+                assert grad_err(name, res[name], base).max() <= TOL, (r.req_id, name, "vs alone")
+            loss_ref = 0.5 * float(np.sum(dB ** 2))
+            assert abs(res["loss"] - loss_ref) <= 1e-5 * loss_ref
             assert abs(res["loss"] - ref["loss"]) <= 1e-5 * abs(ref["loss"])
     srv.close()
 
