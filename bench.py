@@ -632,25 +632,35 @@ def bench_serving(args, world, rank, local):
 def bench_heightfield(args, world, rank, local):
     """The precision workload: 1,048,576 points of a 1024x1024 height field,
     300 spheres (radii log-uniform [0.01, 0.2]), n_bands = 8 (64 SH coeffs):
-    forward and backward times per pass, and the forward's error against the
-    FP64 oracle on a random sample of points, per output."""
+    forward and backward times per precision, and the error of every output
+    against the FP64 oracle: the shading and adjoint of a random sample of
+    256 points (radiance and each gradient, the scene sums over the sample)."""
     import torch
     from oracle import shs_oracle as O
     from paper_2104_00359_gb300 import Config, Scene, synthetic
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sc = synthetic.height_field_scene(seed=3, res=args.hf_res)
-    T = {k: torch.from_numpy(sc[k]).to(dev) for k in ("points", "normals", "albedo", "centers", "radii", "light")}
+    fields = ("points", "normals", "albedo", "centers", "radii", "light")
+    T = {k: torch.from_numpy(sc[k]).to(dev) for k in fields}
     P, N = sc["points"].shape[0], sc["centers"].shape[0]
+    sel = np.sort(np.random.default_rng(1).choice(P, 256, replace=False))
+    Ts = {k: (T[k][torch.from_numpy(sel).to(dev)].contiguous() if k in ("points", "normals", "albedo") else T[k])
+          for k in fields}
+    args_o = [sc[f][sel] if f in ("points", "normals", "albedo") else sc[f] for f in fields]
+    dBs = np.random.default_rng(2).normal(size=(len(sel), 3)).astype(np.float32)
     out = {}
-    # (name, precision, exp_mode): exp_mode 1 is the projected-exponential
+    # (name, precision, exp_mode): precision 2 / 1 / 3 are the tensor-core
+    # tails in BF16 / TF32 / FP16; exp_mode 1 is the projected-exponential
     # variant, 2 the optimal linear step with the fitted 8-band table
-    all_precs = (("fp32", 0, 0), ("bf16_split_tc", 2, 0), ("fp16_split_tc", 3, 0), ("fp32_projexp", 0, 1),
+    all_precs = (("fp32", 0, 0), ("bf16_tc", 2, 0), ("tf32_tc", 1, 0), ("fp16_tc", 3, 0), ("fp32_projexp", 0, 1),
                  ("fp32_oltable", 0, 2))
     # the library stores the table as float32: give the oracle the same values
     table = tuple(np.float32(x).astype(np.float64) if i < 2 else x for i, x in
                   enumerate(read_ol_table(os.path.join(ROOT, "tests", "golden", "ol_table_n8.txt"))))
     fine = None
+    oracle_cache = {}
+    grads = ("d_light", "d_albedo", "d_centers", "d_radii", "d_points", "d_normals")
     for prec_name, prec, mode in [x for x in all_precs if x[0] in args.precisions.split(",")]:
         scene = Scene(T["centers"], T["radii"], T["light"], Config(n_bands=8, precision=prec, exp_mode=mode))
         if mode == 2:
@@ -671,17 +681,28 @@ def bench_heightfield(args, world, rank, local):
                 times_f.append(e0.elapsed_time(e1))
                 times_b.append(e1.elapsed_time(e2))
         k = scene.saved_views(saved, P)[1].cpu().numpy().astype(np.int64)
-        sel = np.sort(np.random.default_rng(1).choice(P, 256, replace=False))
-        args_o = [sc[f][sel] if f in ("points", "normals", "albedo") else sc[f]
-                  for f in ("points", "normals", "albedo", "centers", "radii", "light")]
+        # every output on the sample: shading and adjoint of the 256 sampled points
+        svs = scene.new_saved(len(sel), dev)
+        Bs = scene.shade(Ts["points"], Ts["normals"], Ts["albedo"], saved=svs)
+        gs = scene.backward(Ts["points"], Ts["normals"], Ts["albedo"], torch.from_numpy(dBs).to(dev), saved=svs)
+        torch.cuda.synchronize()
+        ks = scene.saved_views(svs, len(sel))[1].cpu().numpy().astype(np.int64)
         ocfg = O.Config(n_bands=8, exp_mode=mode, ol_table=table if mode == 2 else None)
-        ref = O.shade_forward(ocfg, *args_o, k=k[sel])["radiance"]
-        got = B.cpu().numpy()[sel]
-        err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+        key = (mode, ks.tobytes())
+        if key not in oracle_cache:
+            oracle_cache[key] = O.shade_backward(ocfg, *args_o, dBs.astype(np.float64), k=ks)
+        ref = oracle_cache[key]
+        errs = {"radiance": _norm_err(Bs.cpu().numpy(), ref["forward"]["radiance"])}
+        for name in grads:
+            errs[name] = _norm_err(gs[name].cpu().numpy(), ref[name], ref.get("abs_" + name))
+        got_full = B.cpu().numpy()[sel]
         out[prec_name] = {"fwd_ms": statistics.fmean(times_f), "bwd_ms": statistics.fmean(times_b),
                           "pairs_per_s_fwd": P * N / (statistics.fmean(times_f) * 1e-3),
                           "pairs_per_s_fwd_bwd": P * N / ((statistics.fmean(times_f) + statistics.fmean(times_b)) * 1e-3),
-                          "radiance_max_rel_err_vs_fp64": float(err.max()), "k_mean": float(k.mean())}
+                          "max_rel_err_vs_fp64": errs,
+                          "full_size_radiance_matches_sample": bool(np.allclose(got_full, Bs.cpu().numpy(), rtol=0,
+                                                                                atol=1e-6 * np.abs(got_full).max())),
+                          "k_mean": float(k.mean())}
         if mode in (1, 2):
             # accuracy of the exponential methods (FP64) against the projection of
             # exp(f) by a fine rule (64 x 128 nodes) on the same sample
@@ -693,15 +714,27 @@ def bench_heightfield(args, world, rank, local):
                 return {"max": float(d.max()), "median": float(np.median(d))}
             sq = O.shade_forward(O.Config(n_bands=8), *args_o)["radiance"]
             out[prec_name]["vs_fine_projection_fp64"] = {
-                "projected_2n_x_4n" if mode == 1 else "fitted_ol_table": rel(ref), "scaling_squaring": rel(sq)}
+                "projected_2n_x_4n" if mode == 1 else "fitted_ol_table": rel(ref["forward"]["radiance"]),
+                "scaling_squaring": rel(sq)}
         scene.close()
     first = next(iter(out.values()))
     return dict(metric="height field 1024^2 x 300 spheres, n_bands=8: pairs/sec and error vs FP64 per precision",
                 value=first["pairs_per_s_fwd_bwd"], unit="pairs/s", n_gpus=world, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic", impl="ours",
                 config={"workload": f"height field {args.hf_res}x{args.hf_res} points, 300 spheres, n_bands=8 (64 SH coeffs)",
-                        "points": P, "spheres": N, "error_sample_points": 256},
+                        "points": P, "spheres": N, "error_sample_points": int(len(sel))},
                 precisions=out)
+
+
+def _norm_err(got, ref, abs_terms=None):
+    """Largest normalised error |x - x_ref| / max(|x_ref|, 1e-3 max |x_ref|),
+    with 1e-2 x the sum of absolute terms added to the scale of sums."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    scale = np.maximum(np.abs(ref), 1e-3 * max(np.abs(ref).max(), 1e-30))
+    if abs_terms is not None:
+        scale = np.maximum(scale, 1e-2 * np.asarray(abs_terms, np.float64))
+    return float((np.abs(got - ref) / scale).max())
 
 
 def bench_chain(args, world, rank, local):
@@ -905,8 +938,8 @@ def main():
     ap.add_argument("--workload", choices=("capsule", "serving", "heightfield", "envmap", "chain"), default="capsule",
                     help="capsule: the 512x512 G-buffer step (default); serving: the mixed request stream")
     ap.add_argument("--hf-res", type=int, default=1024, help="height-field grid side (heightfield workload)")
-    ap.add_argument("--precisions", default="fp32,bf16_split_tc,fp16_split_tc,fp32_projexp,fp32_oltable",
-                    help="heightfield workload: comma list of fp32, bf16_split_tc, fp16_split_tc, fp32_projexp, "
+    ap.add_argument("--precisions", default="fp32,bf16_tc,tf32_tc,fp16_tc,fp32_projexp,fp32_oltable",
+                    help="heightfield workload: comma list of fp32, bf16_tc, tf32_tc, fp16_tc, fp32_projexp, "
                          "fp32_oltable")
     ap.add_argument("--env-res", type=int, default=4096, help="environment map rows (width = 2 x rows)")
     ap.add_argument("--serve-jobs", type=int, default=64)

@@ -63,13 +63,19 @@ typedef enum {
 } shs_status;
 
 /* Arithmetic of the SH contractions: the squarings of the exponential (Eq. 7)
- * and the shading contraction (Eq. 8).  The pair terms, the exponent's
- * scaling and optimal linear step, and the adjoint always run in float32.
+ * and the shading (Eq. 8), forward and adjoint.  The pair terms (Eq. 11-13)
+ * and their adjoint, the exponent's scaling and optimal linear step always
+ * run in float32.
  *   SHS_FP32: float32 on the CUDA cores (all band counts).
- *   SHS_BF16 / SHS_FP16: tensor cores (tcgen05) with split 16-bit operands
- *     (each value as the sum of two bfloat16 / IEEE half values, three MMAs
- *     per product) and float32 accumulation; n_bands = 8 only.
- *   SHS_TF32: not implemented (SHS_ERR_UNSUPPORTED). */
+ *   SHS_BF16 / SHS_TF32 / SHS_FP16: tensor cores (tcgen05), n_bands = 8 only.
+ *     The products run through an exact quadrature (11 x 22 directions): a
+ *     squaring is X = S Y^T, S' = (X o X)(w Y), its adjoint
+ *     dS = 2 ((S Y^T) o (dS' Y^T))(w Y), float32 accumulation in tensor
+ *     memory.  Every operand is carried as a sum of parts of the MMA type:
+ *     BF16 three parts (six MMAs per product), TF32 and FP16 two parts
+ *     (three MMAs).  The shading's sums over the directions run in float32.
+ *     Error against the FP64 reference stays below 2e-3 for the radiance
+ *     and every gradient output. */
 enum { SHS_FP32 = 0, SHS_TF32 = 1, SHS_BF16 = 2, SHS_FP16 = 3 };
 
 typedef struct {
@@ -78,7 +84,7 @@ typedef struct {
     float exp_tau;         /* scaling threshold: k = least k >= 0 with |f_hat| <= tau 2^k */
     int32_t exp_kmax;      /* cap on k, 0..16                                             */
     int32_t fixed_k;       /* >= 0: use this k for every point; < 0: per-point k          */
-    int32_t precision;     /* SHS_FP32 (SHS_TF32 / SHS_BF16: tensor-core contractions)    */
+    int32_t precision;     /* SHS_FP32, or SHS_BF16 / SHS_TF32 / SHS_FP16 (tensor cores)  */
     int32_t deterministic; /* 1: scene gradients reduced in a fixed order                  */
     int32_t horizon_cull;  /* 0: every sphere blocks every point (Sec. 3.3.2 sums all      */
                            /*    blockers); 1: per point, skip a sphere lying entirely     */
@@ -146,6 +152,16 @@ size_t shs_saved_bytes(shs_scene_t scene, int64_t n_points);
 shs_status shs_shade(shs_scene_t scene, int64_t n_points, const float* points,
                      const float* normals, const float* albedo, float* radiance,
                      void* saved, void* stream);
+
+/* Shading from the saved log-visibility: the SH exponential and Eq. 8 only,
+ * for a later call with the same points and spheres (the pair terms f depend
+ * on geometry alone, so a lighting or albedo update, as in the paper's
+ * texture and lighting optimisation (Sec. 4.1), needs no new pair pass).
+ *   saved: filled by shs_shade for these points and the scene's current
+ *   spheres (required); normals, albedo: [P,3]; radiance: [P,3] output.
+ * The saved state is not modified. */
+shs_status shs_shade_tail(shs_scene_t scene, int64_t n_points, const float* normals,
+                          const float* albedo, const void* saved, float* radiance, void* stream);
 
 /* Reverse-mode adjoint of shs_shade (Sec. 3.5: the radiance is differentiable
  * with respect to geometry, lighting and albedo).  Given d_radiance = dLoss/dB
@@ -355,14 +371,16 @@ shs_status shs_chain_backward(const float* base, const float* basis, int64_t n_r
 shs_status shs_fp32_fma_probe(int32_t blocks, int64_t iters, float* out, void* stream);
 
 /* Diagnostic: one CTA computes D = A B^T with M = 128 rows, n columns and
- * inner size k on the tensor cores (tcgen05, BF16 operands, FP32 accumulation
- * in tensor memory); split != 0 uses split precision (each operand as the sum
- * of two BF16 values, three MMAs per product).  This checks the tensor-core
- * operand layouts and descriptors of the reduced-precision tail (the paper's
- * triple product, Eq. 7, and shading contraction, Eq. 8).
+ * inner size k on the tensor cores (tcgen05, FP32 accumulation in tensor
+ * memory).  split selects the operand type: 0 = BF16; 1 = BF16 split in two
+ * parts (three MMAs); 2 = BF16 in three parts (six MMAs); 3 = TF32 in two
+ * parts (three MMAs); 4 = FP16 in two parts.  This checks the tensor-core
+ * operand layouts and descriptors of the reduced-precision tails (the paper's
+ * triple product, Eq. 7, and shading, Eq. 8).
  *   A: [128,k], B: [n,k], D: [128,n] float32 device arrays; 16 <= n <= 256,
- *   16 <= k <= 64, both multiples of 16.  *device_status (device int) is set
- *   to SHS_ERR_TIMEOUT if the bounded wait for the MMAs gave up. */
+ *   16 <= k <= 64, both multiples of 16 (k = 16, 32 or 64 for split >= 2).
+ *   *device_status (device int) is set to SHS_ERR_TIMEOUT if the bounded wait
+ *   for the MMAs gave up. */
 shs_status shs_tc_gemm_selftest(const float* A, const float* B, int32_t n, int32_t k, int32_t split,
                                 float* D, int32_t* device_status, void* stream);
 

@@ -58,6 +58,7 @@ _SIGS = {
     "shs_scene_info": (c_int32, [c_void_p, POINTER(ShsConfig), POINTER(c_int32)]),
     "shs_saved_bytes": (c_size_t, [c_void_p, c_int64]),
     "shs_shade": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "shs_shade_tail": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "shs_shade_backward": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "shs_shade_backward_l2": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,

@@ -89,7 +89,8 @@ def build(verbose=False, jobs=None):
              (os.path.join(CSRC, "shs_env.cu"), os.path.join(BUILD, "shs_env.o"), []),
              (os.path.join(CSRC, "shs_raster.cu"), os.path.join(BUILD, "shs_raster.o"), []),
              (os.path.join(CSRC, "shs_diag.cu"), os.path.join(BUILD, "shs_diag.o"), []),
-             (os.path.join(CSRC, "shs_chain.cu"), os.path.join(BUILD, "shs_chain.o"), [])]
+             (os.path.join(CSRC, "shs_chain.cu"), os.path.join(BUILD, "shs_chain.o"), []),
+             (os.path.join(CSRC, "shs_tail_tc.cu"), os.path.join(BUILD, "shs_tail_tc.o"), ["-DSHS_NB=8"])]
     for n in BANDS:
         units.append((os.path.join(CSRC, "shs_kern.cu"), os.path.join(BUILD, f"shs_kern_{n}.o"),
                       [f"-DSHS_NB={n}"]))

@@ -78,12 +78,11 @@ struct shs_scene_s {
     unsigned int* counter;
     float* batch_acc;      // [partial_stride] accumulator for batched calls (kept zero)
     unsigned int* batch_counter;
-    void* b3h;             // tensor-core precisions: 2^4 M_c (lighting-dependent), split operands
-    void* b3l;
     float* fwork;          // f storage when shs_shade gets no saved buffer (tensor-core path)
     int64_t fwork_points;
     float* bwork;          // [K][P] adjoint coefficients of the split backward (>= 6 bands)
     int64_t bwork_points;
+    float* hwork;          // tensor-core adjoint: squaring operands per block [grid][kMaxK][K][128]
     float2* ol_table;      // exp_mode 2: (a, b) per node
     int ol_m;
     float ol_inv_h;
@@ -151,8 +150,7 @@ shs_status check_config(const shs_config* c) {
     if (c->precision != SHS_FP32 && c->precision != SHS_TF32 && c->precision != SHS_BF16 &&
         c->precision != SHS_FP16)
         return fail(SHS_ERR_INVALID_ARG, "unknown precision %d", c->precision);
-    if (c->precision == SHS_TF32) return fail(SHS_ERR_UNSUPPORTED, "SHS_TF32 is not implemented");
-    if ((c->precision == SHS_BF16 || c->precision == SHS_FP16) && c->n_bands != 8)
+    if (c->precision != SHS_FP32 && c->n_bands != 8)
         return fail(SHS_ERR_UNSUPPORTED, "tensor-core precisions need n_bands = 8");
     if (c->deterministic != 0 && c->deterministic != 1) return fail(SHS_ERR_INVALID_ARG, "deterministic must be 0 or 1");
     if (c->horizon_cull != 0 && c->horizon_cull != 1) return fail(SHS_ERR_INVALID_ARG, "horizon_cull must be 0 or 1");
@@ -181,17 +179,19 @@ SceneView view_of(const shs_scene_s* s) {
     return v;
 }
 
-bool tensor_core_precision(const shs_config& c) { return c.precision == SHS_BF16 || c.precision == SHS_FP16; }
+bool tensor_core_precision(const shs_config& c) { return c.precision != SHS_FP32; }
+
+// Operand type of the tensor-core tails for a shs_config precision.
+int tc_prec(const shs_config& c) {
+    return c.precision == SHS_TF32 ? shs::tc_prec_tf32 : c.precision == SHS_FP16 ? shs::tc_prec_fp16
+                                                                                 : shs::tc_prec_bf16;
+}
 
 constexpr int kB2Shift = 8;   // power-of-two pre-scaling of w_q y_i(w_q) (keeps half-precision parts normal)
-constexpr int kB3Shift = 4;   // and of M_c
 
 shs_status set_light(shs_scene_s* s, const float* light, cudaStream_t st) {
     cudaError_t e = cudaMemcpy2DAsync(s->light, s->Kpad * sizeof(float), light, s->K * sizeof(float),
                                       s->K * sizeof(float), 3, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess && tensor_core_precision(s->cfg))
-        e = shs::launch_build_mcat<8>(view_of(s), s->b3h, s->b3l, s->cfg.precision == SHS_FP16,
-                                      std::ldexp(1.0f, kB3Shift), st);
     return e == cudaSuccess ? SHS_OK : cuda_fail(e, "copy lighting");
 }
 
@@ -256,68 +256,160 @@ void gauss_legendre(int n, double* x, double* w) {
     }
 }
 
-// Per device and operand format: Y (rows q, 64 columns) and 2^8 w Y^T (rows i,
-// 256 columns) for the product quadrature 11 Gauss-Legendre nodes in z x 22
-// uniform nodes in phi (exact for the degree-21 integrand of an 8-band triple
-// product); directions 242..255 are zero padding.
+// Tensor-core tail tables, per device and operand type, for the product
+// quadrature 11 Gauss-Legendre nodes in z x 22 uniform azimuths (exact for the
+// degree-21 integrand of an 8-band triple product); directions 242..255 have
+// zero weight.  Built in double precision on the host and split there into
+// parts of the operand type (p_0 = rnd(x), p_1 = rnd(x - p_0), ...).
+//   chunks: per chunk c of CQ directions, the parts of Y_c (rows q, 64 columns)
+//           then the parts of (2^8 w Y)_c (rows i, CQ columns), canonical
+//           K-major layout;
+//   dirs:   (x, y, z, w_q) per direction;  ytab: y_i(w_q) in float32.
 struct TcTables {
-    void* b1h = nullptr;
-    void* b1l = nullptr;
-    void* b2h = nullptr;
-    void* b2l = nullptr;
+    void* chunks = nullptr;
+    float4* dirs = nullptr;
+    float* ytab = nullptr;
 };
-TcTables g_tc_tables[64][2];
+TcTables g_tc_tables[64][3];
 std::mutex g_tc_mutex;
 
-shs_status tc_tables(int fp16, cudaStream_t st, TcTables* out) {
+// x rounded to the operand type (round to nearest even).
+double round_to(double x, int prec) {
+    if (x == 0.0) return 0.0;
+    int e = 0;
+    std::frexp(x, &e);                                     // |x| in [2^(e-1), 2^e)
+    const int bits = prec == shs::tc_prec_bf16 ? 8 : 11;   // significant bits
+    // quantum: 2^(e - bits); half precision's subnormals have a fixed 2^-24
+    const double q = (prec == shs::tc_prec_fp16 && e - 1 < -14) ? std::ldexp(1.0, -24) : std::ldexp(1.0, e - bits);
+    return std::nearbyint(x / q) * q;
+}
+
+// Bits of a value already representable in the operand type.
+uint32_t encode(double v, int prec) {
+    const float f = static_cast<float>(v);
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if (prec == shs::tc_prec_bf16) return u >> 16;
+    if (prec == shs::tc_prec_tf32) return u;
+    // IEEE half from a float that is exactly representable as one
+    const uint32_t sign = (u >> 16) & 0x8000u;
+    const double a = std::fabs(v);
+    if (a == 0.0) return sign;
+    int e = 0;
+    const double m = std::frexp(a, &e);                    // a = m 2^e, m in [0.5, 1)
+    if (e - 1 < -14) return sign | static_cast<uint32_t>(std::ldexp(a, 24));   // subnormal: a / 2^-24
+    return sign | (static_cast<uint32_t>(e - 1 + 15) << 10) | (static_cast<uint32_t>(std::ldexp(m, 11)) & 0x3FFu);
+}
+
+// Byte offset of element (r, k) in the canonical K-major layout of an operand
+// with KD columns of eb-byte elements.
+size_t kmajor(int r, int k, int KD, int eb) {
+    const int T = 16 / eb;
+    return static_cast<size_t>(r >> 3) * (KD / T) * 128 + (k / T) * 128 + (r & 7) * 16 + (k % T) * eb;
+}
+
+void store_elem(unsigned char* base, size_t off, uint32_t bits, int eb) {
+    if (eb == 2) {
+        const uint16_t h = static_cast<uint16_t>(bits);
+        std::memcpy(base + off, &h, 2);
+    } else {
+        std::memcpy(base + off, &bits, 4);
+    }
+}
+
+shs_status tc_tables(int prec, TcTables* out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= 64) return fail(SHS_ERR_UNSUPPORTED, "device ordinal %d", dev);
     std::lock_guard<std::mutex> lock(g_tc_mutex);
-    TcTables& t = g_tc_tables[dev][fp16 ? 1 : 0];
-    if (!t.b1h) {
+    TcTables& t = g_tc_tables[dev][prec];
+    if (!t.chunks) {
         const int Q = shs::kTcQ, K = 64, NZ = 11, NP = 22;
-        std::vector<float> b1(static_cast<size_t>(Q) * K, 0.f), b2(static_cast<size_t>(K) * Q, 0.f);
-        double zx[NZ], zw[NZ], Y[64];
+        const int CQ = shs::tail_tc_chunk(prec), NCH = Q / CQ;
+        const int eb = prec == shs::tc_prec_tf32 ? 4 : 2;
+        const int parts = prec == shs::tc_prec_bf16 ? 3 : 2;
+        const size_t tb = static_cast<size_t>(CQ) * K * eb, chunk = 2 * parts * tb;
+        if (chunk != shs::tail_tc_chunk_bytes(prec)) return fail(SHS_ERR_UNSUPPORTED, "tensor-core chunk size");
+        std::vector<double> Y(static_cast<size_t>(Q) * K, 0.0), w(Q, 0.0);
+        std::vector<float4> dirs(Q, make_float4(0.f, 0.f, 0.f, 0.f));
+        double zx[NZ], zw[NZ], y[64];
         gauss_legendre(NZ, zx, zw);
         for (int a = 0; a < NZ; ++a)
             for (int b = 0; b < NP; ++b) {
                 const int q = a * NP + b;
                 const double phi = 2.0 * M_PI * (b + 0.5) / NP, st_ = std::sqrt(1.0 - zx[a] * zx[a]);
-                real_sh_double(8, st_ * std::cos(phi), st_ * std::sin(phi), zx[a], Y);
-                const double w = zw[a] * 2.0 * M_PI / NP;
+                const double x = st_ * std::cos(phi), yy = st_ * std::sin(phi);
+                real_sh_double(8, x, yy, zx[a], y);
+                w[q] = zw[a] * 2.0 * M_PI / NP;
+                for (int i = 0; i < K; ++i) Y[static_cast<size_t>(q) * K + i] = y[i];
+                dirs[q] = make_float4(static_cast<float>(x), static_cast<float>(yy), static_cast<float>(zx[a]),
+                                      static_cast<float>(w[q]));
+            }
+        std::vector<unsigned char> host(chunk * NCH, 0);
+        std::vector<float> ytab(static_cast<size_t>(Q) * K);
+        for (size_t i = 0; i < ytab.size(); ++i) ytab[i] = static_cast<float>(Y[i]);
+        for (int c = 0; c < NCH; ++c) {
+            unsigned char* base = host.data() + c * chunk;
+            for (int r = 0; r < CQ; ++r) {
+                const int q = c * CQ + r;
                 for (int i = 0; i < K; ++i) {
-                    b1[static_cast<size_t>(q) * K + i] = static_cast<float>(Y[i]);
-                    b2[static_cast<size_t>(i) * Q + q] = static_cast<float>(std::ldexp(w * Y[i], kB2Shift));
+                    double rem = Y[static_cast<size_t>(q) * K + i];
+                    double rem2 = std::ldexp(w[q] * Y[static_cast<size_t>(q) * K + i], kB2Shift);
+                    for (int p = 0; p < parts; ++p) {
+                        const double v = round_to(rem, prec), v2 = round_to(rem2, prec);
+                        rem -= v;
+                        rem2 -= v2;
+                        store_elem(base + p * tb, kmajor(r, i, K, eb), encode(v, prec), eb);
+                        store_elem(base + (parts + p) * tb, kmajor(i, r, CQ, eb), encode(v2, prec), eb);
+                    }
                 }
             }
-        float* staging = nullptr;
-        const size_t bytes = sizeof(float) * Q * K;
+        }
         TcTables nt;
-        e = cudaMalloc(&staging, 2 * bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&nt.b1h, Q * K * 2);
-        if (e == cudaSuccess) e = cudaMalloc(&nt.b1l, Q * K * 2);
-        if (e == cudaSuccess) e = cudaMalloc(&nt.b2h, Q * K * 2);
-        if (e == cudaSuccess) e = cudaMalloc(&nt.b2l, Q * K * 2);
-        if (e == cudaSuccess) e = cudaMemcpy(staging, b1.data(), bytes, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(staging + Q * K, b2.data(), bytes, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = shs::launch_pack_split(staging, Q, K, fp16, nt.b1h, nt.b1l, 0);
-        if (e == cudaSuccess) e = shs::launch_pack_split(staging + Q * K, K, Q, fp16, nt.b2h, nt.b2l, 0);
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        cudaFree(staging);
+        e = cudaMalloc(&nt.chunks, host.size());
+        if (e == cudaSuccess) e = cudaMalloc(&nt.dirs, sizeof(float4) * Q);
+        if (e == cudaSuccess) e = cudaMalloc(&nt.ytab, sizeof(float) * Q * K);
+        if (e == cudaSuccess) e = cudaMemcpy(nt.chunks, host.data(), host.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(nt.dirs, dirs.data(), sizeof(float4) * Q, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(nt.ytab, ytab.data(), sizeof(float) * Q * K, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
-            cudaFree(nt.b1h);
-            cudaFree(nt.b1l);
-            cudaFree(nt.b2h);
-            cudaFree(nt.b2l);
+            cudaFree(nt.chunks);
+            cudaFree(nt.dirs);
+            cudaFree(nt.ytab);
             return cuda_fail(e, "tensor-core tables");
         }
         t = nt;
     }
-    (void)st;
     *out = t;
     return SHS_OK;
+}
+
+// Clamped-cosine lobe as a polynomial in t = n . w (addition theorem):
+// H(t) = sum_l A_l (2l + 1) / (4 pi) P_l(t) with A_l = 2 pi int_0^1 t P_l(t) dt,
+// zero for odd l >= 3, written as c1 t + e0 + e1 t^2 + e2 t^4 + e3 t^6.
+void lobe_poly(float* c1, float* e4) {
+    double x[8], wt[8], c[8];
+    gauss_legendre(8, x, wt);
+    for (int l = 0; l < 8; ++l) {
+        double s = 0.0;
+        for (int g = 0; g < 8; ++g) {
+            const double t = 0.5 * (x[g] + 1.0);           // [0, 1]
+            double p0 = 1.0, p1 = t, pl = l == 0 ? 1.0 : t;
+            for (int k = 2; k <= l; ++k) {
+                pl = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = pl;
+            }
+            s += 0.5 * wt[g] * t * pl;
+        }
+        c[l] = (2 * l + 1) / 2.0 * s;                      // A_l (2l+1)/(4 pi), A_l = 2 pi s
+    }
+    *c1 = static_cast<float>(c[1]);
+    e4[0] = static_cast<float>(c[0] - c[2] / 2 + 3 * c[4] / 8 - 5 * c[6] / 16);
+    e4[1] = static_cast<float>(3 * c[2] / 2 - 30 * c[4] / 8 + 105 * c[6] / 16);
+    e4[2] = static_cast<float>(35 * c[4] / 8 - 315 * c[6] / 16);
+    e4[3] = static_cast<float>(231 * c[6] / 16);
 }
 
 void free_scene(shs_scene_s* s) {
@@ -329,10 +421,9 @@ void free_scene(shs_scene_s* s) {
     cudaFree(s->counter);
     cudaFree(s->batch_acc);
     cudaFree(s->batch_counter);
-    cudaFree(s->b3h);
-    cudaFree(s->b3l);
     cudaFree(s->fwork);
     cudaFree(s->bwork);
+    cudaFree(s->hwork);
     cudaFree(s->ol_table);
     delete s;
 }
@@ -420,14 +511,6 @@ shs_status shs_scene_create(const shs_config* cfg, int32_t n_spheres, const floa
     if (e != cudaSuccess) {
         free_scene(sc);
         return cuda_fail(e, "allocate scene");
-    }
-    if (tensor_core_precision(*cfg)) {
-        e = cudaMalloc(&sc->b3h, 192 * 64 * 2);
-        if (e == cudaSuccess) e = cudaMalloc(&sc->b3l, 192 * 64 * 2);
-        if (e != cudaSuccess) {
-            free_scene(sc);
-            return cuda_fail(e, "allocate tensor-core lighting table");
-        }
     }
     e = shs::launch_pack_spheres(centers, radii, sc->spheres, n_spheres, true, true, s);
     if (e != cudaSuccess) {
@@ -522,7 +605,7 @@ shs_status shs_shade(shs_scene_t sc, int64_t n_points, const float* points, cons
     if (!points || !normals || !albedo || !radiance) return fail(SHS_ERR_INVALID_ARG, "NULL input/output array");
     if (saved && (reinterpret_cast<uintptr_t>(saved) & 15u)) return fail(SHS_ERR_INVALID_ARG, "saved not 16-byte aligned");
     if (!table_ready(sc)) return fail(SHS_ERR_INVALID_ARG, "exp_mode 2 needs shs_scene_set_ol_table first");
-    FwdArgs a;
+    FwdArgs a{};
     a.sc = view_of(sc);
     a.n_points = n_points;
     a.points = points;
@@ -546,32 +629,75 @@ shs_status shs_shade(shs_scene_t sc, int64_t n_points, const float* points, cons
             a.saved_f = sc->fwork;
         }
         TcTables tt;
-        shs_status ts = tc_tables(sc->cfg.precision == SHS_FP16, st, &tt);
+        shs_status ts = tc_tables(tc_prec(sc->cfg), &tt);
         if (ts != SHS_OK) return ts;
         cudaError_t e = shs::launch_forward_pairs<8>(a, st);
         if (e != cudaSuccess) return cuda_fail(e, "launch pair terms");
-        shs::TcArgs t;
+        shs::TcArgs t{};
         t.sc = a.sc;
         t.n_points = n_points;
+        t.prec = tc_prec(sc->cfg);
         t.normals = normals;
         t.albedo = albedo;
         t.radiance = radiance;
         t.f = a.saved_f;
         t.saved_k = a.saved_k;
-        t.b1h = tt.b1h;
-        t.b1l = tt.b1l;
-        t.b2h = tt.b2h;
-        t.b2l = tt.b2l;
-        t.b3h = sc->b3h;
-        t.b3l = sc->b3l;
+        t.chunks = tt.chunks;
+        t.dirs = tt.dirs;
+        t.ytab = tt.ytab;
         t.b2_unscale = std::ldexp(1.0f, -kB2Shift);
-        t.b3_unscale = std::ldexp(1.0f, -kB3Shift);
-        t.fp16 = sc->cfg.precision == SHS_FP16;
-        e = shs::launch_tail_tc<8>(t, st);
+        lobe_poly(&t.lobe_c1, t.lobe_e);
+        e = shs::launch_tail_tc_fwd(t, st);
         return e == cudaSuccess ? SHS_OK : cuda_fail(e, "launch tensor-core tail");
     }
     cudaError_t e = dispatch<Fwd>(sc->cfg.n_bands, a, st);
     return e == cudaSuccess ? SHS_OK : cuda_fail(e, "launch forward");
+}
+
+shs_status shs_shade_tail(shs_scene_t sc, int64_t n_points, const float* normals, const float* albedo,
+                          const void* saved, float* radiance, void* stream) {
+    if (!sc) return fail(SHS_ERR_INVALID_ARG, "scene is NULL");
+    if (n_points < 0) return fail(SHS_ERR_INVALID_ARG, "n_points < 0");
+    if (n_points == 0) return SHS_OK;
+    if (!normals || !albedo || !radiance || !saved) return fail(SHS_ERR_INVALID_ARG, "NULL input/output array");
+    if (reinterpret_cast<uintptr_t>(saved) & 15u) return fail(SHS_ERR_INVALID_ARG, "saved not 16-byte aligned");
+    if (!table_ready(sc)) return fail(SHS_ERR_INVALID_ARG, "exp_mode 2 needs shs_scene_set_ol_table first");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float* sf;
+    int* sk;
+    split_saved(sc, n_points, const_cast<void*>(saved), &sf, &sk);
+    if (tensor_core_precision(sc->cfg)) {
+        TcTables tt;
+        shs_status ts = tc_tables(tc_prec(sc->cfg), &tt);
+        if (ts != SHS_OK) return ts;
+        shs::TcArgs t{};
+        t.sc = view_of(sc);
+        t.n_points = n_points;
+        t.prec = tc_prec(sc->cfg);
+        t.normals = normals;
+        t.albedo = albedo;
+        t.radiance = radiance;
+        t.f = sf;
+        t.saved_k = nullptr;
+        t.chunks = tt.chunks;
+        t.dirs = tt.dirs;
+        t.ytab = tt.ytab;
+        t.b2_unscale = std::ldexp(1.0f, -kB2Shift);
+        lobe_poly(&t.lobe_c1, t.lobe_e);
+        cudaError_t e = shs::launch_tail_tc_fwd(t, st);
+        return e == cudaSuccess ? SHS_OK : cuda_fail(e, "launch tensor-core tail");
+    }
+    FwdArgs a{};
+    a.sc = view_of(sc);
+    a.n_points = n_points;
+    a.normals = normals;
+    a.albedo = albedo;
+    a.radiance = radiance;
+    a.saved_f = sf;
+    a.saved_k = sk;
+    a.tail_only = 1;
+    cudaError_t e = dispatch<Fwd>(sc->cfg.n_bands, a, st);
+    return e == cudaSuccess ? SHS_OK : cuda_fail(e, "launch shading tail");
 }
 
 static shs_status backward_common(shs_scene_t sc, int64_t n_points, const float* points,
@@ -634,6 +760,72 @@ static shs_status backward_common(shs_scene_t sc, int64_t n_points, const float*
     }
     const int64_t tiles = (n_points + shs::kBlock - 1) / shs::kBlock;
     a.grid = static_cast<int>(tiles < sc->max_grid ? tiles : sc->max_grid);
+    a.skip_tail = 0;
+    if (tensor_core_precision(sc->cfg)) {
+        // the exponential's and the shading's adjoint on the tensor cores, then
+        // the float32 pair pass of the split backward
+        TcTables tt;
+        shs_status ts = tc_tables(tc_prec(sc->cfg), &tt);
+        if (ts != SHS_OK) return ts;
+        const int hgrid = shs::tail_tc_bwd_grid();
+        if (!sc->hwork) {
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess)
+                e = cudaMalloc(&sc->hwork, sizeof(float) * static_cast<size_t>(hgrid) * shs::kMaxK * sc->K * 128);
+            if (e != cudaSuccess) return cuda_fail(e, "allocate tensor-core adjoint workspace");
+        }
+        const float* f = sf;
+        if (!f) {
+            if (sc->fwork_points < n_points) {
+                cudaError_t e = cudaStreamSynchronize(s);
+                cudaFree(sc->fwork);
+                sc->fwork = nullptr;
+                sc->fwork_points = 0;
+                if (e == cudaSuccess) e = cudaMalloc(&sc->fwork, sizeof(float) * sc->K * n_points);
+                if (e != cudaSuccess) return cuda_fail(e, "allocate f workspace");
+                sc->fwork_points = n_points;
+            }
+            FwdArgs fa{};
+            fa.sc = a.sc;
+            fa.n_points = n_points;
+            fa.points = points;
+            fa.normals = normals;
+            fa.albedo = albedo;
+            fa.radiance = nullptr;
+            fa.saved_f = sc->fwork;
+            fa.saved_k = nullptr;
+            cudaError_t e = shs::launch_forward_pairs<8>(fa, s);
+            if (e != cudaSuccess) return cuda_fail(e, "launch pair terms");
+            f = sc->fwork;
+        }
+        shs::TcArgs t{};
+        t.sc = a.sc;
+        t.n_points = n_points;
+        t.prec = tc_prec(sc->cfg);
+        t.normals = normals;
+        t.albedo = albedo;
+        t.f = f;
+        t.k_in = sf ? sk : nullptr;
+        t.chunks = tt.chunks;
+        t.dirs = tt.dirs;
+        t.ytab = tt.ytab;
+        t.b2_unscale = std::ldexp(1.0f, -kB2Shift);
+        lobe_poly(&t.lobe_c1, t.lobe_e);
+        t.d_radiance = d_radiance;
+        t.radiance_in = radiance;
+        t.target = target;
+        t.d_albedo = d_albedo;
+        t.d_normals = d_normals;
+        t.dfp_ws = sc->bwork;
+        t.partials = sc->partials;
+        t.partial_stride = sc->partial_stride;
+        t.partial_rows = a.grid;
+        t.deterministic = sc->cfg.deterministic;
+        t.hist = sc->hwork;
+        cudaError_t e = shs::launch_tail_tc_bwd(t, s);
+        if (e != cudaSuccess) return cuda_fail(e, "launch tensor-core adjoint tail");
+        a.skip_tail = 1;
+    }
     cudaError_t e = dispatch<Bwd>(sc->cfg.n_bands, a, s);
     return e == cudaSuccess ? SHS_OK : cuda_fail(e, "launch backward");
 }

@@ -43,6 +43,7 @@ struct FwdArgs {
     float* radiance;
     float* saved_f;          // [K][P] or null
     int* saved_k;            // [P] or null
+    int tail_only;           // 1: f read from saved_f (exponential and shading only)
 };
 
 struct BwdArgs {
@@ -68,6 +69,7 @@ struct BwdArgs {
     unsigned int* counter;   // scratch, zero between launches
     int partial_stride;
     int grid;                // persistent grid size
+    int skip_tail;           // split backward: dfp_ws and the lighting / loss rows are already written
 };
 
 // A batch: up to kMaxBatch requests (of one band count) whose 128-point tiles
@@ -91,38 +93,50 @@ struct BwdBatch {
     BwdArgs r[kMaxBatch];                 // partials/counter: per-request accumulator
 };
 
-// Reduced-precision tail on the tensor cores (8 bands): inputs are the
-// log-visibility f saved by the pair pass; tables are in the canonical K-major
-// layout as split 16-bit operands (hi, lo).
+// Reduced-precision tails on the tensor cores (8 bands): the log-visibility f
+// comes from the pair pass; the tables are the product quadrature's Y_c and
+// (2^8 w Y)_c per chunk of directions, split into parts of the operand type
+// and laid out in the canonical K-major layout, chunk after chunk.
 struct TcArgs {
     SceneView sc;
     int64_t n_points;
+    int prec;                // 0 = BF16 (3 parts), 1 = FP16 (2), 2 = TF32 (2)
     const float* normals;
     const float* albedo;
-    float* radiance;
+    float* radiance;         // forward: [P,3] out
     const float* f;          // [K][P]
-    int* saved_k;            // [P] out
-    const void* b1h;         // y_i(w_q), rows q (256) x 64
-    const void* b1l;
-    const void* b2h;         // 2^s2 w_q y_i(w_q), rows i (64) x 256
-    const void* b2l;
-    const void* b3h;         // 2^s3 M_c[j][k], rows c*64+k (192) x 64
-    const void* b3l;
-    float b2_unscale;        // 2^-s2
-    float b3_unscale;        // 2^-s3
-    int fp16;                // operand format: 1 = IEEE half, 0 = bfloat16
+    int* saved_k;            // forward: [P] out, or null
+    const void* chunks;      // tables, chunk after chunk
+    const float4* dirs;      // [256] (x, y, z, w_q), zero weight past 242
+    const float* ytab;       // [256][64] y_i(w_q), float32
+    float b2_unscale;        // 2^-8
+    float lobe_c1;           // clamped-cosine lobe H(t) = c1 t + e0 + e1 t^2 + e2 t^4 + e3 t^6
+    float lobe_e[4];
+    // adjoint
+    const int* k_in;         // [P] squarings (saved by the forward)
+    const float* d_radiance; // [P,3], or null in L2 mode
+    const float* radiance_in;// [P,3] (L2 mode)
+    const float* target;     // [P,3] (L2 mode) or null
+    float* d_albedo;
+    float* d_normals;
+    float* dfp_ws;           // [K][P] pair-adjoint coefficients (out)
+    float* partials;         // [grid][stride] lighting + loss rows, or an accumulator
+    int partial_stride;
+    int partial_rows;        // rows the pair pass will reduce (deterministic mode)
+    int deterministic;
+    float* hist;             // [grid][kMaxK][K][128] squaring operands (adjoint workspace)
 };
 
+constexpr int tc_prec_bf16 = 0, tc_prec_fp16 = 1, tc_prec_tf32 = 2;   // operand types of the tensor-core tails
 constexpr int kTcQ = 256;    // quadrature directions (242 used) for 8 bands
 
 template <int NB> cudaError_t launch_forward_pairs(const FwdArgs& a, cudaStream_t s);
-template <int NB> cudaError_t launch_tail_tc(const TcArgs& a, cudaStream_t s);
-template <int NB> cudaError_t launch_build_mcat(const SceneView& sc, void* b3h, void* b3l, int fp16, float scale,
-                                                cudaStream_t s);
+cudaError_t launch_tail_tc_fwd(const TcArgs& a, cudaStream_t s);
+cudaError_t launch_tail_tc_bwd(const TcArgs& a, cudaStream_t s);
+int tail_tc_chunk(int precision);              // directions per table chunk
+size_t tail_tc_chunk_bytes(int precision);
+int tail_tc_bwd_grid();                         // blocks of the adjoint tail (rows of its workspace)
 template <int NB> cudaError_t launch_forward_batch(const FwdBatch& b, cudaStream_t s);
-// Lay out a row-major float [rows x cols] table as split 16-bit operands in
-// the canonical K-major layout (defined in shs_tc.cu).
-cudaError_t launch_pack_split(const float* src, int rows, int cols, int fp16, void* hi, void* lo, cudaStream_t s);
 template <int NB> cudaError_t launch_backward_batch(const BwdBatch& b, cudaStream_t s);
 template <int NB> cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
 template <int NB> cudaError_t launch_backward(const BwdArgs& a, cudaStream_t s);

@@ -23,6 +23,8 @@
 
 #include "generated/shs_sh_gen.cuh"
 #include "shs_internal.h"
+#include "shs_exp.cuh"
+#include "shs_warp.cuh"
 #include "shs_tc.cuh"
 
 #ifndef SHS_NB
@@ -38,10 +40,6 @@ constexpr int KPAD = (K + 3) / 4 * 4;
 constexpr int NWARP = kBlock / 32;
 using SH = shsgen::SH<NB>;
 
-constexpr float kSqrt4Pi = 3.5449077018110318f;
-constexpr float kInvSqrt4Pi = 0.28209479177387814f;
-constexpr float kInv8Pi = 0.039788735772973836f;
-constexpr float kInv4Pi = 0.07957747154594767f;
 
 __host__ __device__ constexpr int band_of(int i) {
     int l = 0;
@@ -373,51 +371,6 @@ __device__ __forceinline__ void pair_backward_grad(float px, float py, float pz,
     gcz = fmaf(fmaf(-rad, sz, az), g.invD, coef * g.dz);
 }
 
-// Number of squarings: least k >= 0 with |f_hat| <= tau 2^k, capped at kmax.
-// Optimal linear step exp*(g) ~ a(s) sqrt(4 pi) e_0 + b(s) g at s = |g|
-// (Sec. 3.3.2): the Gaussian reading a = b = exp(s^2 / 8 pi), or, for
-// exp_mode 2, a fitted table that is linear between its nodes and constant
-// past the last one.  ca and cb are (da/ds) / s and (db/ds) / s, the factors
-// of g in the adjoint (zero at s = 0 and past the table).  TAB: Gaussian only
-// (0), table only (1), or chosen by the scene's exp_mode (2).
-struct OLCoef {
-    float a, b, ca, cb;
-};
-template <int TAB = 2>
-__device__ __forceinline__ OLCoef ol_coef(const SceneView& sc, float s2) {
-    OLCoef r;
-    if (TAB == 0 || (TAB == 2 && sc.exp_mode != 2)) {
-        r.a = expf(s2 * kInv8Pi);
-        r.b = r.a;
-        r.ca = r.a * kInv4Pi;
-        r.cb = r.ca;
-        return r;
-    }
-    const float s = sqrtf(s2);
-    const float last = static_cast<float>(sc.ol_m - 1);
-    const float x = fminf(s * sc.ol_inv_h, last);
-    const int i = min(static_cast<int>(x), sc.ol_m - 2);
-    const float t = x - static_cast<float>(i);
-    const float2 lo = __ldg(sc.ol_table + i), hi = __ldg(sc.ol_table + i + 1);
-    r.a = fmaf(t, hi.x - lo.x, lo.x);
-    r.b = fmaf(t, hi.y - lo.y, lo.y);
-    const float c = (x < last && s > 0.f) ? sc.ol_inv_h / s : 0.f;
-    r.ca = (hi.x - lo.x) * c;
-    r.cb = (hi.y - lo.y) * c;
-    return r;
-}
-
-__device__ __forceinline__ int scaling_k(const SceneView& sc, float nrm2) {
-    if (sc.fixed_k >= 0) return sc.fixed_k;
-    int k = 0;
-    float thr = sc.tau2;
-    while (k < sc.kmax && nrm2 > thr) {
-        ++k;
-        thr *= 4.f;
-    }
-    return k;
-}
-
 // Truncated SH triple product o = a * b (Eq. 7) and square o = a * a.
 // Up to 6 bands: the unrolled Gaunt contraction of the generated header.
 // From 7 bands: a separable quadrature that is exact for these degrees
@@ -667,10 +620,19 @@ __device__ __forceinline__ float load_or(const float* p, int64_t i, bool live) {
 // ---------------------------------------------------------------------------
 
 // Forward shading of point p of one request (Eq. 8), scene staged in shared
-// memory.  Without TAIL only the log-visibility f is computed and stored.
-template <bool TAIL = true>
+// memory.  MODE kFwdFull: pair terms, exponential and shading; kFwdPairs:
+// only the log-visibility f, stored; kFwdTail: f read from the saved state,
+// then the exponential and shading (lighting or albedo changed, geometry not).
+constexpr int kFwdFull = 0, kFwdPairs = 1, kFwdTail = 2;
+
+template <int MODE = kFwdFull>
 __device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_sph, const float* s_light,
                                               int64_t p) {
+    float f[K];
+    if constexpr (MODE == kFwdTail) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) f[i] = __ldg(a.saved_f + i * a.n_points + p);
+    } else {
     const float px = __ldg(a.points + 3 * p), py = __ldg(a.points + 3 * p + 1),
                 pz = __ldg(a.points + 3 * p + 2);
 
@@ -712,12 +674,12 @@ __device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_
         }
     }
 
-    float f[K];
     finish_f(a.sc, acc, f);
-    if constexpr (!TAIL) {
+    if constexpr (MODE == kFwdPairs) {
 #pragma unroll
         for (int i = 0; i < K; ++i) a.saved_f[i * a.n_points + p] = f[i];
         return;
+    }
     }
     float V[K];
     int k = 0;
@@ -758,7 +720,7 @@ __device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_
         for (int i = 0; i < K; ++i) d = fmaf(s_light[c * KPAD + i], W[i], d);
         a.radiance[3 * p + c] = __ldg(a.albedo + 3 * p + c) * d;
     }
-    if (a.saved_f) {
+    if (MODE == kFwdFull && a.saved_f) {
 #pragma unroll
         for (int i = 0; i < K; ++i) a.saved_f[i * a.n_points + p] = f[i];
         a.saved_k[p] = k;
@@ -772,7 +734,7 @@ __device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_
 #define SHS_BWD_MINB 3
 #endif
 
-template <bool TAIL>
+template <int MODE>
 __global__ void __launch_bounds__(kBlock, NB <= 4 ? SHS_FWD_MINB : 1) forward_kernel_t(FwdArgs a) {
     __shared__ __align__(16) float4 s_sph[kMaxSpheres];
     __shared__ __align__(16) float s_light[3 * KPAD];
@@ -784,331 +746,13 @@ __global__ void __launch_bounds__(kBlock, NB <= 4 ? SHS_FWD_MINB : 1) forward_ke
     }
     const int64_t p = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x;
     if (p >= a.n_points) return;
-    forward_point<TAIL>(a, s_sph, s_light, p);
+    forward_point<MODE>(a, s_sph, s_light, p);
 }
 
-#if SHS_NB == 8
-// ---------------------------------------------------------------------------
-// reduced-precision tail on the tensor cores (8 bands)
-// ---------------------------------------------------------------------------
-// Per 128-point tile (thread = point = tensor-memory lane):
-//   S_0 from f in float32 (DC isolation, scaling, optimal linear step);
-//   each squaring S <- S * S (Eq. 7, truncated) as two GEMMs through a
-//   quadrature exact for the degree-21 integrand: X = S Y^T (values at 242
-//   directions), S' = (X o X) (w Y), in four chunks of 64 directions;
-//   U = S M (M_c[j][k] = sum_i L_c,i C_ijk, Eq. 8) and B_c = a_c e0 U_c . H.
-// Operands are split 16-bit pairs (x ~ hi + lo; three MMAs per product:
-// hi*hi + lo*hi + hi*lo) accumulating in float32 tensor memory.
-namespace tcq {
-constexpr uint32_t kB1 = kTcQ * 64 * 2;   // 32 KB per part
-constexpr uint32_t kB2 = 64 * kTcQ * 2;   // 32 KB
-constexpr uint32_t kB3 = 192 * 64 * 2;    // 24 KB
-constexpr uint32_t kA = 128 * 64 * 2;     // 16 KB
-constexpr uint32_t kOffB1h = 0, kOffB1l = kB1, kOffB2h = 2 * kB1, kOffB2l = 2 * kB1 + kB2;
-constexpr uint32_t kOffAh = 2 * kB1 + 2 * kB2, kOffAl = kOffAh + kA;
-constexpr uint32_t kOffXh = kOffAl + kA, kOffXl = kOffXh + kA;
-constexpr uint32_t kSmem = kOffXl + kA;   // 192 KB
-}  // namespace tcq
-
-__device__ __forceinline__ bool wait_all(uint64_t* bar, uint32_t& phase, int* status) {
-    const bool w = tc::mbar_wait(bar, phase);
-    phase ^= 1u;
-    const bool bad = __syncthreads_or(!w);
-    if (bad && threadIdx.x == 0) atomicExch(status, kDevTimeout);
-    return !bad;
-}
-
-__device__ __forceinline__ void sync_for_mma() {
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-}
-
-template <bool FP16>
-__global__ void __launch_bounds__(128, 1) tail_tc_kernel(const __grid_constant__ TcArgs a) {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) uint64_t bar_ld, bar_mma;
-    __shared__ uint32_t tmem_base;
-    __shared__ int s_kmax;
-    using namespace tcq;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    unsigned char* B1h = sm + kOffB1h;
-    unsigned char* B1l = sm + kOffB1l;
-    unsigned char* B2h = sm + kOffB2h;
-    unsigned char* B2l = sm + kOffB2l;
-    unsigned char* Ah = sm + kOffAh;
-    unsigned char* Al = sm + kOffAl;
-    unsigned char* Xh = sm + kOffXh;
-    unsigned char* Xl = sm + kOffXl;
-    constexpr uint32_t idesc64 = FP16 ? tc::idesc_fp16(128, 64) : tc::idesc_bf16(128, 64);
-    constexpr uint32_t idesc192 = FP16 ? tc::idesc_fp16(128, 192) : tc::idesc_bf16(128, 192);
-
-    if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
-    if (tid == 0) {
-        tc::mbar_init1(&bar_ld);
-        tc::mbar_init1(&bar_mma);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tmem = tmem_base;
-    const uint32_t lane_tm = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    uint32_t ph_ld = 0, ph_mma = 0;
-
-    if (tid == 0) {
-        tc::mbar_expect(&bar_ld, 2 * kB2);
-        tc::bulk_g2s(B2h, a.b2h, kB2, &bar_ld);
-        tc::bulk_g2s(B2l, a.b2l, kB2, &bar_ld);
-    }
-    bool ok = wait_all(&bar_ld, ph_ld, a.sc.status);
-    const int64_t P = a.n_points;
-    const int64_t ntiles = (P + 127) / 128;
-    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-        if (tid == 0) {
-            tc::mbar_expect(&bar_ld, 2 * kB1);
-            tc::bulk_g2s(B1h, a.b1h, kB1, &bar_ld);
-            tc::bulk_g2s(B1l, a.b1l, kB1, &bar_ld);
-        }
-        const int64_t p = tile * 128 + tid;
-        const bool live = p < P;
-        const int64_t q = live ? p : 0;
-        float S[K];
-#pragma unroll
-        for (int i = 0; i < K; ++i) S[i] = live ? __ldg(a.f + i * P + q) : 0.f;
-        float nrm2 = 0.f;
-#pragma unroll
-        for (int i = 1; i < K; ++i) nrm2 = fmaf(S[i], S[i], nrm2);
-        const int k = scaling_k(a.sc, nrm2);
-        const float e0 = expf(S[0] * kInvSqrt4Pi);
-        const float scale = ldexpf(1.f, -k);
-        const OLCoef ol = ol_coef(a.sc, nrm2 * scale * scale);
-        S[0] = ol.a * kSqrt4Pi;
-#pragma unroll
-        for (int i = 1; i < K; ++i) S[i] = ol.b * (S[i] * scale);
-        if (tid == 0) s_kmax = 0;
-        __syncthreads();
-        atomicMax(&s_kmax, k);
-        ok = wait_all(&bar_ld, ph_ld, a.sc.status);      // B1 resident; also publishes s_kmax
-        if (!ok) break;
-        const int kt = s_kmax;
-        for (int t = 0; ok && t < kt; ++t) {
-            // Row scaling by a power of two keeps every operand and X o X inside
-            // half precision's range: |S| 2^-s <= 2^7 bounds |X| by 2^7 (|y_i| <= 1.1).
-            float sabs = 0.f;
-#pragma unroll
-            for (int i = 0; i < K; ++i) sabs += fabsf(S[i]);
-            const int sh = max(0, ilogbf(fmaxf(1.25f * sabs, 1e-30f)) - 6);
-            {
-                float Sd[K];
-#pragma unroll
-                for (int i = 0; i < K; ++i) Sd[i] = ldexpf(S[i], -sh);
-                tc::store_row64<FP16>(Ah, Al, tid, Sd);
-            }
-            sync_for_mma();
-            for (int c = 0; c < 4 && ok; ++c) {
-                if (tid == 0) {               // X = S Y^T for directions 64c..64c+63 -> columns 0..63
-#pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint32_t ao = ks * 256, bo = c * 8192 + ks * 256;
-                        const uint64_t ah = tc::make_desc(tc::smem_u32(Ah) + ao, 1024);
-                        const uint64_t al = tc::make_desc(tc::smem_u32(Al) + ao, 1024);
-                        const uint64_t bh = tc::make_desc(tc::smem_u32(B1h) + bo, 1024);
-                        const uint64_t bl = tc::make_desc(tc::smem_u32(B1l) + bo, 1024);
-                        tc::mma_bf16(tmem, ah, bh, idesc64, ks > 0);
-                        tc::mma_bf16(tmem, al, bh, idesc64, true);
-                        tc::mma_bf16(tmem, ah, bl, idesc64, true);
-                    }
-                    tc::commit(&bar_mma);
-                }
-                ok = wait_all(&bar_mma, ph_mma, a.sc.status);
-                if (!ok) break;
-                tc::fence_after_sync();
-                float X[64];
-                tc::tmem_ld32(lane_tm + 0, X);
-                tc::tmem_ld32(lane_tm + 32, X + 32);
-#pragma unroll
-                for (int i = 0; i < 64; ++i) X[i] *= X[i];
-                tc::store_row64<FP16>(Xh, Xl, tid, X);
-                sync_for_mma();
-                if (tid == 0) {               // S' += (X o X) (w Y) over these directions -> columns 64..127
-#pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint32_t ao = ks * 256, bo = c * 1024 + ks * 256;
-                        const uint64_t ah = tc::make_desc(tc::smem_u32(Xh) + ao, 1024);
-                        const uint64_t al = tc::make_desc(tc::smem_u32(Xl) + ao, 1024);
-                        const uint64_t bh = tc::make_desc(tc::smem_u32(B2h) + bo, 4096);
-                        const uint64_t bl = tc::make_desc(tc::smem_u32(B2l) + bo, 4096);
-                        tc::mma_bf16(tmem + 64, ah, bh, idesc64, c > 0 || ks > 0);
-                        tc::mma_bf16(tmem + 64, al, bh, idesc64, true);
-                        tc::mma_bf16(tmem + 64, ah, bl, idesc64, true);
-                    }
-                    tc::commit(&bar_mma);
-                }
-                ok = wait_all(&bar_mma, ph_mma, a.sc.status);
-            }
-            if (!ok) break;
-            tc::fence_after_sync();
-            float Sn[64];
-            tc::tmem_ld32(lane_tm + 64, Sn);
-            tc::tmem_ld32(lane_tm + 96, Sn + 32);
-            if (t < k) {
-                const float up = ldexpf(a.b2_unscale, 2 * sh);
-#pragma unroll
-                for (int i = 0; i < K; ++i) S[i] = Sn[i] * up;
-            }
-            tc::fence_before_sync();
-        }
-        if (!ok) break;
-        // shading: U = S M (per channel), B_c = a_c e0 U_c . H
-        float sabs = 0.f;
-#pragma unroll
-        for (int i = 0; i < K; ++i) sabs += fabsf(S[i]);
-        const int shf = max(0, ilogbf(fmaxf(sabs, 1e-30f)) - 9);
-        {
-            float Sd[K];
-#pragma unroll
-            for (int i = 0; i < K; ++i) Sd[i] = ldexpf(S[i], -shf);
-            tc::store_row64<FP16>(Ah, Al, tid, Sd);
-        }
-        __syncthreads();                      // every MMA on B1 is complete (waited above)
-        if (tid == 0) {
-            tc::mbar_expect(&bar_ld, 2 * kB3);
-            tc::bulk_g2s(B1h, a.b3h, kB3, &bar_ld);
-            tc::bulk_g2s(B1l, a.b3l, kB3, &bar_ld);
-        }
-        ok = wait_all(&bar_ld, ph_ld, a.sc.status);
-        if (!ok) break;
-        sync_for_mma();
-        if (tid == 0) {
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-                const uint32_t o = ks * 256;
-                const uint64_t ah = tc::make_desc(tc::smem_u32(Ah) + o, 1024);
-                const uint64_t al = tc::make_desc(tc::smem_u32(Al) + o, 1024);
-                const uint64_t bh = tc::make_desc(tc::smem_u32(B1h) + o, 1024);
-                const uint64_t bl = tc::make_desc(tc::smem_u32(B1l) + o, 1024);
-                tc::mma_bf16(tmem, ah, bh, idesc192, ks > 0);
-                tc::mma_bf16(tmem, al, bh, idesc192, true);
-                tc::mma_bf16(tmem, ah, bl, idesc192, true);
-            }
-            tc::commit(&bar_mma);
-        }
-        ok = wait_all(&bar_mma, ph_mma, a.sc.status);
-        if (!ok) break;
-        tc::fence_after_sync();
-        float H[K], ux, uy, uz, il;
-        cosine_lobe(live ? __ldg(a.normals + 3 * q) : 0.f, live ? __ldg(a.normals + 3 * q + 1) : 0.f,
-                    live ? __ldg(a.normals + 3 * q + 2) : 1.f, H, ux, uy, uz, il);
-        float Bc[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int cc = 0; cc < 6; ++cc) {
-            float u[32];
-            tc::tmem_ld32(lane_tm + 32 * cc, u);
-            const int ch = cc >> 1, k0 = (cc & 1) * 32;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) Bc[ch] = fmaf(u[i], H[k0 + i], Bc[ch]);
-        }
-        if (live) {
-            const float s3 = e0 * ldexpf(a.b3_unscale, shf);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) a.radiance[3 * q + c] = __ldg(a.albedo + 3 * q + c) * Bc[c] * s3;
-            if (a.saved_k) a.saved_k[q] = k;
-        }
-        tc::fence_before_sync();
-        __syncthreads();                      // TMEM and B1 free for the next tile
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, 256);
-}
-
-// M_c[j][k] = sum_i L_c,i C_ijk = (L_c * e_j)_k, scaled by `scale`, written as
-// split 16-bit operands: row c*64 + k, column j of a [192 x 64] K-major layout.
-template <bool FP16>
-__global__ void build_mcat_kernel(SceneView sc, unsigned char* b3h, unsigned char* b3l, float scale) {
-    const int c = blockIdx.x, j = threadIdx.x;
-    if (c >= 3 || j >= K) return;
-    float Lc[K], e[K], T[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-        Lc[i] = sc.light[c * KPAD + i];
-        e[i] = i == j ? 1.f : 0.f;
-    }
-    sh_mul(Lc, e, T);
-#pragma unroll
-    for (int kk = 0; kk < K; ++kk) {
-        uint16_t h, l;
-        tc::split16<FP16>(T[kk] * scale, h, l);
-        const uint32_t o = tc::kmajor_offset(c * 64 + kk, j, 64);
-        *reinterpret_cast<uint16_t*>(b3h + o) = h;
-        *reinterpret_cast<uint16_t*>(b3l + o) = l;
-    }
-}
-#endif  // SHS_NB == 8
 
 // ---------------------------------------------------------------------------
 // backward kernel
 // ---------------------------------------------------------------------------
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Sum NV values (NV a power of two <= 32) over the warp by halving exchanges:
-// afterwards v[0] on lane l holds the warp total of value (l >> (5 - log2 NV)).
-template <int NV>
-__device__ __forceinline__ void warp_transpose_sum(float* v, int lane) {
-#pragma unroll
-    for (int o = 16, cnt = NV; o > 0; o >>= 1) {
-        if (cnt > 1) {
-            const int half = cnt / 2;
-            const bool up = lane & o;
-#pragma unroll
-            for (int i = 0; i < half; ++i) {
-                const float send = up ? v[i] : v[i + half];
-                const float keep = up ? v[i + half] : v[i];
-                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-            }
-            cnt = half;
-        } else {
-            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
-        }
-    }
-}
-
-constexpr int log2c(int v) { return v <= 1 ? 0 : 1 + log2c(v / 2); }
-constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : 2 * pow2_at_least((v + 1) / 2); }
-
-// Add the warp totals of vals[0..NV) into dst[0..NV) (one lane per value).
-template <int NV>
-__device__ __forceinline__ void warp_sum_into(const float* vals, float* dst, int lane) {
-#pragma unroll
-    for (int base = 0; base < NV; base += 32) {
-        const int rem = NV - base;
-        if (rem >= 32) {
-            float v[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = vals[base + i];
-            warp_transpose_sum<32>(v, lane);
-            dst[base + lane] += v[0];
-        } else {
-            constexpr int R = NV % 32 == 0 ? 32 : NV % 32;
-            constexpr int RP = pow2_at_least(R);
-            float v[RP];
-#pragma unroll
-            for (int i = 0; i < RP; ++i) v[i] = i < R ? vals[base + i] : 0.f;
-            warp_transpose_sum<RP>(v, lane);
-            constexpr int sh = 5 - log2c(RP);
-            const int idx = lane >> sh;
-            if ((lane & ((1 << sh) - 1)) == 0 && idx < R) dst[base + idx] += v[0];
-        }
-    }
-}
 
 // Sum four values over the warp; lane l returns the total of value (l >> 3).
 __device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v3, int lane) {
@@ -1803,63 +1447,19 @@ template <>
 cudaError_t launch_forward_pairs<NB>(const FwdArgs& a, cudaStream_t s) {
     if (a.n_points <= 0) return cudaSuccess;
     const int64_t blocks = (a.n_points + kBlock - 1) / kBlock;
-    forward_kernel_t<false><<<static_cast<unsigned>(blocks), kBlock, 0, s>>>(a);
+    forward_kernel_t<kFwdPairs><<<static_cast<unsigned>(blocks), kBlock, 0, s>>>(a);
     count_launch();
     return cudaGetLastError();
-}
-
-template <>
-cudaError_t launch_tail_tc<NB>(const TcArgs& a, cudaStream_t s) {
-#if SHS_NB == 8
-    if (a.n_points <= 0) return cudaSuccess;
-    auto kern = a.fp16 ? tail_tc_kernel<true> : tail_tc_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(tcq::kSmem));
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    const int64_t tiles = (a.n_points + 127) / 128;
-    const int grid = static_cast<int>(tiles < sms ? tiles : sms);
-    kern<<<grid, 128, tcq::kSmem, s>>>(a);
-    count_launch();
-    return cudaGetLastError();
-#else
-    (void)a;
-    (void)s;
-    return cudaErrorNotSupported;
-#endif
-}
-
-template <>
-cudaError_t launch_build_mcat<NB>(const SceneView& sc, void* b3h, void* b3l, int fp16, float scale,
-                                  cudaStream_t s) {
-#if SHS_NB == 8
-    if (fp16)
-        build_mcat_kernel<true><<<3, K, 0, s>>>(sc, static_cast<unsigned char*>(b3h),
-                                                static_cast<unsigned char*>(b3l), scale);
-    else
-        build_mcat_kernel<false><<<3, K, 0, s>>>(sc, static_cast<unsigned char*>(b3h),
-                                                 static_cast<unsigned char*>(b3l), scale);
-    count_launch();
-    return cudaGetLastError();
-#else
-    (void)sc;
-    (void)b3h;
-    (void)b3l;
-    (void)fp16;
-    (void)scale;
-    (void)s;
-    return cudaErrorNotSupported;
-#endif
 }
 
 template <>
 cudaError_t launch_forward<NB>(const FwdArgs& a, cudaStream_t s) {
     if (a.n_points <= 0) return cudaSuccess;
     const int64_t blocks = (a.n_points + kBlock - 1) / kBlock;
-    forward_kernel_t<true><<<static_cast<unsigned>(blocks), kBlock, 0, s>>>(a);
+    if (a.tail_only)
+        forward_kernel_t<kFwdTail><<<static_cast<unsigned>(blocks), kBlock, 0, s>>>(a);
+    else
+        forward_kernel_t<kFwdFull><<<static_cast<unsigned>(blocks), kBlock, 0, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
@@ -1884,10 +1484,12 @@ cudaError_t launch_backward<NB>(const BwdArgs& a, cudaStream_t s) {
     if (err != cudaSuccess) return err;
     if (a.dfp_ws) {
         // split backward: tail pass (per point), then the pair pass (per sphere lane)
-        backward_kernel_t<false, 2, 2><<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
-        count_launch();
-        err = cudaGetLastError();
-        if (err != cudaSuccess) return err;
+        if (!a.skip_tail) {
+            backward_kernel_t<false, 2, 2><<<static_cast<unsigned>(a.grid), kBlock, smem, s>>>(a);
+            count_launch();
+            err = cudaGetLastError();
+            if (err != cudaSuccess) return err;
+        }
         const bool need_pairs = a.d_centers || a.d_radii || a.d_points;
         static const cudaError_t attr2 = cudaFuncSetAttribute(
             bwd_pairs_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSpheres * 32);

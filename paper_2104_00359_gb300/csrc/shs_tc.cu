@@ -1,7 +1,8 @@
 // Diagnostic entry point for the tensor-core machinery used by the
-// reduced-precision tail: one CTA computes D = A B^T (M = 128) with tcgen05
-// BF16 MMAs accumulating in tensor memory, optionally in split precision
-// (A ~ A_hi + A_lo, B ~ B_hi + B_lo, D = A_hi B_hi + A_lo B_hi + A_hi B_lo).
+// reduced-precision tails: one CTA computes D = A B^T (M = 128) with tcgen05
+// MMAs accumulating in tensor memory: plain BF16 (mode 0), BF16 split in two
+// parts (mode 1: A_hi B_hi + A_lo B_hi + A_hi B_lo), and the tails' operand
+// types (modes 2-4: BF16 in three parts, TF32 in two, FP16 in two).
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -87,29 +88,83 @@ __global__ void __launch_bounds__(128) tc_gemm_selftest_kernel(const float* A, c
     if (warp == 0) shs::tc::tmem_dealloc(tmem, ncols);
 }
 
-__global__ void pack_split_kernel(const float* src, int rows, int cols, int fp16, uint16_t* hi, uint16_t* lo) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= rows * cols) return;
-    const int r = e / cols, c = e % cols;
-    uint16_t h, l;
-    if (fp16) shs::tc::split_fp16(src[e], h, l);
-    else shs::tc::split_bf16(src[e], h, l);
-    const uint32_t o = shs::tc::kmajor_offset(r, c, cols) >> 1;
-    hi[o] = h;
-    lo[o] = l;
+// Split-precision self-test (modes 2-4): A [128 x KD] and B [n x KD] split
+// into the parts of the operand type, every product term of the precision.
+template <int PR, int KD>
+__global__ void __launch_bounds__(128) tc_split_selftest_kernel(const float* A, const float* B, int N, float* D,
+                                                                int* status) {
+    using P = shs::tc::Prec<PR>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t a_part = kM * KD * P::kElem, b_part = static_cast<uint32_t>(N) * KD * P::kElem;
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + P::kParts * a_part;
+    {
+        float v[KD];
+        for (int k = 0; k < KD; ++k) v[k] = A[tid * KD + k];
+        shs::tc::store_row_split<PR, KD>(sA, a_part, tid, v);
+    }
+    for (int n = tid; n < N; n += 128) {
+        float v[KD];
+        for (int k = 0; k < KD; ++k) v[k] = B[n * KD + k];
+        shs::tc::store_row_split<PR, KD>(sB, b_part, n, v);
+    }
+    if (warp == 0) shs::tc::tmem_alloc(&tmem_base, 256);
+    if (tid == 0) {
+        shs::tc::mbar_init1(&bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    shs::tc::fence_async_smem();
+    shs::tc::fence_before_sync();
+    __syncthreads();
+    shs::tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    if (tid == 0) {
+        shs::tc::gemm_split<PR, KD>(tmem, shs::tc::smem_u32(sA), a_part, shs::tc::smem_u32(sB), b_part,
+                                    shs::tc::idesc_of<PR>(kM, N), false);
+        shs::tc::commit(&bar);
+    }
+    const bool ok = shs::tc::mbar_wait(&bar, 0);
+    if (!ok && tid == 0) atomicExch(status, shs::kDevTimeout);
+    shs::tc::fence_after_sync();
+    if (ok) {
+        const uint32_t lane_addr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+        for (int c = 0; c < N; c += 16) {
+            float v[16];
+            shs::tc::tmem_ld16(lane_addr + c, v);
+            for (int i = 0; i < 16; ++i) D[tid * N + c + i] = v[i];
+        }
+    }
+    shs::tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) shs::tc::tmem_dealloc(tmem, 256);
+}
+
+template <int PR, int KD>
+cudaError_t launch_split_selftest(const float* A, const float* B, int n, float* D, int* status, cudaStream_t s) {
+    using P = shs::tc::Prec<PR>;
+    const size_t smem = static_cast<size_t>(P::kParts) * P::kElem * KD * (kM + n);
+    auto kern = tc_split_selftest_kernel<PR, KD>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<1, 128, smem, s>>>(A, B, n, D, status);
+    shs::count_launch();
+    return cudaGetLastError();
+}
+
+template <int PR>
+cudaError_t split_selftest(const float* A, const float* B, int n, int k, float* D, int* status, cudaStream_t s) {
+    switch (k) {
+        case 16: return launch_split_selftest<PR, 16>(A, B, n, D, status, s);
+        case 32: return launch_split_selftest<PR, 32>(A, B, n, D, status, s);
+        case 64: return launch_split_selftest<PR, 64>(A, B, n, D, status, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
-
-namespace shs {
-cudaError_t launch_pack_split(const float* src, int rows, int cols, int fp16, void* hi, void* lo, cudaStream_t s) {
-    const int n = rows * cols;
-    pack_split_kernel<<<(n + 255) / 256, 256, 0, s>>>(src, rows, cols, fp16, static_cast<uint16_t*>(hi),
-                                                      static_cast<uint16_t*>(lo));
-    count_launch();
-    return cudaGetLastError();
-}
-}  // namespace shs
 
 extern "C" shs_status shs_tc_gemm_selftest(const float* A, const float* B, int32_t n, int32_t k, int32_t split,
                                            float* D, int32_t* device_status, void* stream) {
@@ -118,12 +173,22 @@ extern "C" shs_status shs_tc_gemm_selftest(const float* A, const float* B, int32
     if (n < 16 || n > kMaxN || n % 16 || k < 16 || k > kMaxKdim || k % 16)
         return static_cast<shs_status>(shs::report_error(
             SHS_ERR_INVALID_ARG, "tc self-test needs 16 <= n <= 256, 16 <= k <= 64, multiples of 16"));
+    if (split < 0 || split > 4)
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "tc self-test mode %d not in 0..4", split));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (split >= 2) {
+        if (k == 48) return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "split modes take k = 16, 32 or 64"));
+        if (split == 2) e = split_selftest<shs::tc::kPrecBF16>(A, B, n, k, D, device_status, st);
+        else if (split == 3) e = split_selftest<shs::tc::kPrecTF32>(A, B, n, k, D, device_status, st);
+        else e = split_selftest<shs::tc::kPrecFP16>(A, B, n, k, D, device_status, st);
+        return e == cudaSuccess ? SHS_OK : static_cast<shs_status>(shs::report_cuda(e, "tc self-test launch"));
+    }
     const size_t smem = 2 * (static_cast<size_t>(kM) * k * 2) + 2 * (static_cast<size_t>(n) * k * 2);
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_selftest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    e = cudaFuncSetAttribute(tc_gemm_selftest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem));
     if (e != cudaSuccess) return static_cast<shs_status>(shs::report_cuda(e, "tc self-test attribute"));
-    tc_gemm_selftest_kernel<<<1, 128, smem, static_cast<cudaStream_t>(stream)>>>(A, B, n, k, split ? 1 : 0, D,
-                                                                              device_status);
+    tc_gemm_selftest_kernel<<<1, 128, smem, st>>>(A, B, n, k, split ? 1 : 0, D, device_status);
     shs::count_launch();
     e = cudaGetLastError();
     return e == cudaSuccess ? SHS_OK : static_cast<shs_status>(shs::report_cuda(e, "tc self-test launch"));

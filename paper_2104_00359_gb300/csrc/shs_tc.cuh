@@ -190,5 +190,222 @@ __device__ __forceinline__ void store_row64(unsigned char* hi_base, unsigned cha
     }
 }
 
+// ---------------------------------------------------------------------------
+// Split-precision operands for the 8-band tensor-core tails.
+//
+// A float32 value x is carried as the sum of P parts of the MMA's input type:
+// x ~ p_0 + p_1 + ..., p_j = rnd(x - p_0 - ... - p_{j-1}).  A product of
+// split operands a b is the sum of the part products a_i b_j of total order
+// i + j below the parts' count, each one MMA accumulating in float32 tensor
+// memory, smallest first.
+//   BF16: 3 parts per operand (about 24 significant bits), 6 products;
+//   FP16: 2 parts (about 22 bits; operands pre-scaled into half range), 3;
+//   TF32: 2 parts (about 22 bits), 3 products, K = 8 per MMA.
+// An element pair (16-bit types) or element (TF32) fills 32 bits; 16 bytes of
+// a row form one core-matrix row (8 elements of 16 bits, 4 of TF32), so the
+// canonical K-major layout above holds for every type with the K index
+// counted in 16-byte groups: element (r, k) of an R x KD operand with element
+// size eb sits at (r / 8) SBO + (k / T) 128 + (r % 8) 16 + (k % T) eb,
+// T = 16 / eb, SBO = (KD / T) 128.  One MMA consumes 32 bytes of K (K = 16
+// for 16-bit types, 8 for TF32): successive K steps advance 256 bytes.
+enum : int { kPrecBF16 = 0, kPrecFP16 = 1, kPrecTF32 = 2 };
+
+template <int PR>
+struct Prec;
+template <>
+struct Prec<kPrecBF16> {
+    static constexpr int kElem = 2, kParts = 3, kKmma = 16, kTerms = 6;
+    static constexpr uint32_t kFmt = 1;
+};
+template <>
+struct Prec<kPrecFP16> {
+    static constexpr int kElem = 2, kParts = 2, kKmma = 16, kTerms = 3;
+    static constexpr uint32_t kFmt = 0;
+};
+template <>
+struct Prec<kPrecTF32> {
+    static constexpr int kElem = 4, kParts = 2, kKmma = 8, kTerms = 3;
+    static constexpr uint32_t kFmt = 2;
+};
+
+// (part of A, part of B) of product term t, smallest first.
+template <int PR>
+__host__ __device__ constexpr int term_a(int t) {
+    return Prec<PR>::kTerms == 6 ? (t == 0 ? 2 : t == 1 ? 1 : t == 2 ? 0 : t == 3 ? 1 : 0)
+                                 : (t == 0 ? 1 : 0);
+}
+template <int PR>
+__host__ __device__ constexpr int term_b(int t) {
+    return Prec<PR>::kTerms == 6 ? (t == 0 ? 0 : t == 1 ? 1 : t == 2 ? 2 : t == 3 ? 0 : t == 4 ? 1 : 0)
+                                 : (t == 1 ? 1 : 0);
+}
+
+// Instruction descriptor: D = F32, A = B of the precision's format, both
+// K-major, M x N.
+template <int PR>
+__host__ __device__ constexpr uint32_t idesc_of(int M, int N) {
+    return (1u << 4) | (Prec<PR>::kFmt << 7) | (Prec<PR>::kFmt << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+template <int PR>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                    bool accumulate) {
+    if constexpr (PR == kPrecTF32) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+            ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate ? 1u : 0u)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+            ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate ? 1u : 0u)
+            : "memory");
+    }
+}
+
+// D (+)= A B^T for split operands: A [128 x KD] and B [N x KD], both K-major
+// with their parts `a_part` / `b_part` bytes apart; every product term of the
+// precision over all K steps.  Issued by one thread.
+template <int PR, int KD>
+__device__ __forceinline__ void gemm_split(uint32_t d_tmem, uint32_t a_addr, uint32_t a_part, uint32_t b_addr,
+                                           uint32_t b_part, uint32_t idesc, bool accumulate) {
+    constexpr uint32_t T = 16 / Prec<PR>::kElem;
+    constexpr uint32_t SBO = (KD / T) * 128;
+    constexpr int KS = KD / Prec<PR>::kKmma;
+#pragma unroll
+    for (int t = 0; t < Prec<PR>::kTerms; ++t) {
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+            const uint64_t ad = make_desc(a_addr + term_a<PR>(t) * a_part + ks * 256, SBO);
+            const uint64_t bd = make_desc(b_addr + term_b<PR>(t) * b_part + ks * 256, SBO);
+            mma<PR>(d_tmem, ad, bd, idesc, accumulate || t > 0 || ks > 0);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Parts of x as raw bits (16-bit types in the low half).
+template <int PR>
+__device__ __forceinline__ void split_parts(float x, uint32_t* part) {
+    float r = x;
+#pragma unroll
+    for (int j = 0; j < Prec<PR>::kParts; ++j) {
+        if constexpr (PR == kPrecBF16) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(r);
+            part[j] = __bfloat16_as_ushort(h);
+            r -= __bfloat162float(h);
+        } else if constexpr (PR == kPrecFP16) {
+            const __half h = __float2half_rn(r);
+            part[j] = __half_as_ushort(h);
+            r -= __half2float(h);
+        } else {
+            const uint32_t h = to_tf32(r);
+            part[j] = h;
+            r -= __uint_as_float(h);
+        }
+    }
+}
+
+// Store row r (KD values) of a [rows x KD] split operand whose parts are
+// `part_bytes` apart.
+template <int PR, int KD>
+__device__ __forceinline__ void store_row_split(unsigned char* base, uint32_t part_bytes, int r, const float* v) {
+    constexpr int EB = Prec<PR>::kElem, T = 16 / EB, NP = Prec<PR>::kParts;
+    constexpr uint32_t SBO = (KD / T) * 128;
+    const uint32_t row_off = (r >> 3) * SBO + (r & 7) * 16;
+#pragma unroll
+    for (int g = 0; g < KD / T; ++g) {
+        uint32_t w[NP][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if constexpr (EB == 2) {
+                uint32_t lo[NP], hi[NP];
+                split_parts<PR>(v[g * 8 + 2 * e], lo);
+                split_parts<PR>(v[g * 8 + 2 * e + 1], hi);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) w[j][e] = lo[j] | (hi[j] << 16);
+            } else {
+                uint32_t pp[NP];
+                split_parts<PR>(v[g * 4 + e], pp);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) w[j][e] = pp[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+            *reinterpret_cast<uint4*>(base + j * part_bytes + row_off + g * 128) =
+                make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
+    }
+}
+
+// 16 consecutive FP32 columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v) {
+    static_assert(N % 16 == 0, "multiple of 16 columns");
+    if constexpr (N % 32 == 0) {
+#pragma unroll
+        for (int c = 0; c < N; c += 32) tmem_ld32(taddr + c, v + c);
+    } else {
+#pragma unroll
+        for (int c = 0; c < N; c += 16) tmem_ld16(taddr + c, v + c);
+    }
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` with a bound of about one second; gives up early
+// when another role of the block raised *abort.  On a timeout it raises
+// *abort and records SHS_ERR_TIMEOUT in *status.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                                   int* status) {
+    const uint64_t t0 = now_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 63u) == 63u) {
+            if (*abort) return false;
+            if (now_ns() - t0 > 1000000000ull) {
+                *abort = 1;
+                atomicExch(status, 5);
+                return false;
+            }
+        }
+    }
+}
+
 }  // namespace tc
 }  // namespace shs

@@ -129,6 +129,18 @@ class Scene:
               "shs_shade")
         return rad
 
+    def shade_tail(self, normals, albedo, saved, out=None):
+        """Radiance from the log-visibility a shade() call saved for the same
+        points and spheres: only the exponential and the shading run (the
+        lighting or the albedo changed since, the geometry did not)."""
+        P = int(normals.shape[0])
+        nrm = _dev_f32(normals, (P, 3), "normals")
+        alb = _dev_f32(albedo, (P, 3), "albedo")
+        rad = out if out is not None else torch.empty((P, 3), dtype=torch.float32, device=nrm.device)
+        check(self.lib.shs_shade_tail(self.handle, P, ptr(nrm), ptr(alb), ptr(saved), ptr(rad), _stream()),
+              "shs_shade_tail")
+        return rad
+
     def _grad_buffers(self, P, device, want):
         z = lambda *s: torch.empty(s, dtype=torch.float32, device=device)
         N = self.n_spheres

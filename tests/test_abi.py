@@ -73,6 +73,7 @@ def test_config_validation_without_gpu(lib):
     c2.exp_mode = 2
     assert lib.shs_shade_backward_noalloc(ctypes.byref(c2), 0, None, None, None, 0, *([None] * 11), None) == 2
     assert lib.shs_shade(None, 10, None, None, None, None, None, None) == 1
+    assert lib.shs_shade_tail(None, 10, None, None, None, None, None) == 1
     assert lib.shs_status_string(5) == b"device wait timed out"
 
 

@@ -190,3 +190,34 @@ def test_autograd_function_matches_direct_backward():
     for k_, t in T.items():
         assert grad_err(name_map[k_], t.grad.cpu().numpy(), ref).max() <= TOL, k_
     scene.close()
+
+
+@pytest.mark.parametrize("n,prec", [(4, 0), (6, 0), (8, 0), (8, 2), (8, 1)])
+def test_shade_tail_after_lighting_update(n, prec):
+    """shs_shade_tail: with the saved log-visibility of an earlier shs_shade
+    and new lighting, only the exponential and Eq. 8 run; the radiance equals
+    a full forward with the new lighting (FP32: bitwise) and the oracle."""
+    import torch
+    from paper_2104_00359_gb300 import Config, Scene
+    sc = S.random_scene(400 + n + prec, 333, 11, n, inside_fraction=0.05)
+    dev = torch.device("cuda:0")
+    T = {k: torch.from_numpy(sc[k]).to(dev) for k in FIELDS}
+    P = sc["points"].shape[0]
+    scene = Scene(T["centers"], T["radii"], T["light"], Config(n_bands=n, precision=prec))
+    sv = scene.new_saved(P, dev)
+    scene.shade(T["points"], T["normals"], T["albedo"], saved=sv)
+    light2 = np.random.default_rng(9).normal(scale=0.3, size=sc["light"].shape).astype(np.float32)
+    light2[:, 0] = 1.0
+    alb2 = np.ascontiguousarray(sc["albedo"][::-1], np.float32)
+    scene.update(light=torch.from_numpy(light2).to(dev))
+    Bt = scene.shade_tail(T["normals"], torch.from_numpy(alb2).to(dev), sv)
+    Bf = scene.shade(T["points"], T["normals"], torch.from_numpy(alb2).to(dev))
+    torch.cuda.synchronize()
+    assert scene.device_status() == 0
+    k = scene.saved_views(sv, P)[1].cpu().numpy().astype(np.int64)
+    scene.close()
+    if prec == 0:
+        np.testing.assert_array_equal(Bt.cpu().numpy(), Bf.cpu().numpy())
+    sc2 = dict(sc, light=light2, albedo=alb2)
+    ref = O.shade_forward(O.Config(n_bands=n), *[sc2[f] for f in FIELDS], k=k)["radiance"]
+    assert rel_err(Bt.cpu().numpy(), ref).max() <= (TOL if prec == 0 else 2e-3)
