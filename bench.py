@@ -681,6 +681,22 @@ def bench_heightfield(args, world, rank, local):
                 times_f.append(e0.elapsed_time(e1))
                 times_b.append(e1.elapsed_time(e2))
         k = scene.saved_views(saved, P)[1].cpu().numpy().astype(np.int64)
+        # the exponential and shading alone (shs_shade_tail), and the adjoint
+        # without the pair terms (only lighting, albedo and normal gradients)
+        tail_f, tail_b = [], []
+        Bt = torch.empty_like(B)
+        for it in range(args.warmup + args.steps):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            scene.shade_tail(T["normals"], T["albedo"], saved, out=Bt)
+            e1.record()
+            scene.backward(T["points"], T["normals"], T["albedo"], dB, saved=saved,
+                           want=("light", "albedo", "normals"))
+            e2.record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                tail_f.append(e0.elapsed_time(e1))
+                tail_b.append(e1.elapsed_time(e2))
         # every output on the sample: shading and adjoint of the 256 sampled points
         svs = scene.new_saved(len(sel), dev)
         Bs = scene.shade(Ts["points"], Ts["normals"], Ts["albedo"], saved=svs)
@@ -702,7 +718,11 @@ def bench_heightfield(args, world, rank, local):
                           "max_rel_err_vs_fp64": errs,
                           "full_size_radiance_matches_sample": bool(np.allclose(got_full, Bs.cpu().numpy(), rtol=0,
                                                                                 atol=1e-6 * np.abs(got_full).max())),
-                          "k_mean": float(k.mean())}
+                          "k_mean": float(k.mean()),
+                          "tail_fwd_ms": statistics.fmean(tail_f), "tail_bwd_ms": statistics.fmean(tail_b)}
+        if prec != 0:
+            out[prec_name]["roofline_tail"] = _tc_tail_roofline(prec, k, statistics.fmean(tail_f),
+                                                                statistics.fmean(tail_b))
         if mode in (1, 2):
             # accuracy of the exponential methods (FP64) against the projection of
             # exp(f) by a fine rule (64 x 128 nodes) on the same sample
@@ -724,6 +744,35 @@ def bench_heightfield(args, world, rank, local):
                 config={"workload": f"height field {args.hf_res}x{args.hf_res} points, 300 spheres, n_bands=8 (64 SH coeffs)",
                         "points": P, "spheres": N, "error_sample_points": int(len(sel))},
                 precisions=out)
+
+
+def _tc_tail_roofline(prec, k, fwd_ms, bwd_ms):
+    """Tensor-core tails against the measured dense peak of their operand type.
+    Work = the MMAs the method issues: per 128-point tile (kt = the tile's
+    largest k) and pass over the 256 quadrature directions, the evaluation
+    GEMM X = S Y^T and the projection GEMM (X o X)(w Y) are 2 x 128 x 256 x 64
+    flop each, times the product terms of the split operands (BF16: 6, TF32 /
+    FP16: 3).  Forward: kt squaring passes (2 GEMMs) and a shading pass (1).
+    Adjoint: kt recomputed squarings (2), the shading adjoint (1 + 2) and kt
+    squaring adjoints (2 evaluations + 1 projection): 5 kt + 3."""
+    peaks = load_peaks()
+    bf16 = peaks.get("bf16_tflops") or 1900.0
+    terms = 6 if prec == 2 else 3
+    # TF32 at the recipe's nominal ratio to BF16 (1.1 / 2.25 PFLOP/s dense)
+    peak = bf16 * (1.1 / 2.25) if prec == 1 else bf16
+    P = k.shape[0]
+    kt = np.array([k[i:i + 128].max() for i in range(0, P, 128)], np.int64)
+    gemm = 2.0 * 128 * 256 * 64 * terms
+    f_fwd = gemm * float(np.sum(2 * kt + 1))
+    f_bwd = gemm * float(np.sum(5 * kt + 3))
+    a_f = f_fwd / (fwd_ms * 1e-3) / 1e12
+    a_b = f_bwd / (bwd_ms * 1e-3) / 1e12
+    return {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
+            "peak_source": "MEASURED_PEAKS bf16_tflops (burst)" + (" x 1.1/2.25 (TF32 nominal ratio)" if prec == 1 else ""),
+            "forward": {"achieved": a_f, "frac": a_f / peak, "flop": f_fwd, "ms": fwd_ms},
+            "adjoint": {"achieved": a_b, "frac": a_b / peak, "flop": f_bwd, "ms": bwd_ms,
+                        "note": "includes the fixed-order lighting reduction launch"},
+            "terms": terms, "tiles": int(kt.shape[0]), "kt_mean": float(kt.mean())}
 
 
 def _norm_err(got, ref, abs_terms=None):

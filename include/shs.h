@@ -374,7 +374,9 @@ shs_status shs_fp32_fma_probe(int32_t blocks, int64_t iters, float* out, void* s
  * inner size k on the tensor cores (tcgen05, FP32 accumulation in tensor
  * memory).  split selects the operand type: 0 = BF16; 1 = BF16 split in two
  * parts (three MMAs); 2 = BF16 in three parts (six MMAs); 3 = TF32 in two
- * parts (three MMAs); 4 = FP16 in two parts.  This checks the tensor-core
+ * parts (three MMAs); 4 = FP16 in two parts; 5-7 = as 2-4 with A held in
+ * tensor memory (written there by tcgen05.st, read by the MMA) instead of
+ * shared memory.  This checks the tensor-core
  * operand layouts and descriptors of the reduced-precision tails (the paper's
  * triple product, Eq. 7, and shading, Eq. 8).
  *   A: [128,k], B: [n,k], D: [128,n] float32 device arrays; 16 <= n <= 256,

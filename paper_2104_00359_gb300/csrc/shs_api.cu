@@ -82,7 +82,7 @@ struct shs_scene_s {
     int64_t fwork_points;
     float* bwork;          // [K][P] adjoint coefficients of the split backward (>= 6 bands)
     int64_t bwork_points;
-    float* hwork;          // tensor-core adjoint: squaring operands per block [grid][kMaxK][K][128]
+    float* hwork;          // tensor-core adjoint: squaring operands per block [grid][kMaxK][K + 2][128]
     float2* ol_table;      // exp_mode 2: (a, b) per node
     int ol_m;
     float ol_inv_h;
@@ -270,7 +270,7 @@ struct TcTables {
     float4* dirs = nullptr;
     float* ytab = nullptr;
 };
-TcTables g_tc_tables[64][3];
+TcTables g_tc_tables[64][3][2];   // device, operand type, forward / adjoint chunking
 std::mutex g_tc_mutex;
 
 // x rounded to the operand type (round to nearest even).
@@ -317,20 +317,20 @@ void store_elem(unsigned char* base, size_t off, uint32_t bits, int eb) {
     }
 }
 
-shs_status tc_tables(int prec, TcTables* out) {
+shs_status tc_tables(int prec, int adjoint, TcTables* out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= 64) return fail(SHS_ERR_UNSUPPORTED, "device ordinal %d", dev);
     std::lock_guard<std::mutex> lock(g_tc_mutex);
-    TcTables& t = g_tc_tables[dev][prec];
+    TcTables& t = g_tc_tables[dev][prec][adjoint ? 1 : 0];
     if (!t.chunks) {
         const int Q = shs::kTcQ, K = 64, NZ = 11, NP = 22;
-        const int CQ = shs::tail_tc_chunk(prec), NCH = Q / CQ;
+        const int CQ = shs::tail_tc_chunk(prec, adjoint), NCH = Q / CQ;
         const int eb = prec == shs::tc_prec_tf32 ? 4 : 2;
         const int parts = prec == shs::tc_prec_bf16 ? 3 : 2;
         const size_t tb = static_cast<size_t>(CQ) * K * eb, chunk = 2 * parts * tb;
-        if (chunk != shs::tail_tc_chunk_bytes(prec)) return fail(SHS_ERR_UNSUPPORTED, "tensor-core chunk size");
+        if (chunk != shs::tail_tc_chunk_bytes(prec, adjoint)) return fail(SHS_ERR_UNSUPPORTED, "tensor-core chunk size");
         std::vector<double> Y(static_cast<size_t>(Q) * K, 0.0), w(Q, 0.0);
         std::vector<float4> dirs(Q, make_float4(0.f, 0.f, 0.f, 0.f));
         double zx[NZ], zw[NZ], y[64];
@@ -629,7 +629,7 @@ shs_status shs_shade(shs_scene_t sc, int64_t n_points, const float* points, cons
             a.saved_f = sc->fwork;
         }
         TcTables tt;
-        shs_status ts = tc_tables(tc_prec(sc->cfg), &tt);
+        shs_status ts = tc_tables(tc_prec(sc->cfg), 0, &tt);
         if (ts != SHS_OK) return ts;
         cudaError_t e = shs::launch_forward_pairs<8>(a, st);
         if (e != cudaSuccess) return cuda_fail(e, "launch pair terms");
@@ -668,7 +668,7 @@ shs_status shs_shade_tail(shs_scene_t sc, int64_t n_points, const float* normals
     split_saved(sc, n_points, const_cast<void*>(saved), &sf, &sk);
     if (tensor_core_precision(sc->cfg)) {
         TcTables tt;
-        shs_status ts = tc_tables(tc_prec(sc->cfg), &tt);
+        shs_status ts = tc_tables(tc_prec(sc->cfg), 0, &tt);
         if (ts != SHS_OK) return ts;
         shs::TcArgs t{};
         t.sc = view_of(sc);
@@ -765,13 +765,13 @@ static shs_status backward_common(shs_scene_t sc, int64_t n_points, const float*
         // the exponential's and the shading's adjoint on the tensor cores, then
         // the float32 pair pass of the split backward
         TcTables tt;
-        shs_status ts = tc_tables(tc_prec(sc->cfg), &tt);
+        shs_status ts = tc_tables(tc_prec(sc->cfg), 1, &tt);
         if (ts != SHS_OK) return ts;
         const int hgrid = shs::tail_tc_bwd_grid();
         if (!sc->hwork) {
             cudaError_t e = cudaStreamSynchronize(s);
             if (e == cudaSuccess)
-                e = cudaMalloc(&sc->hwork, sizeof(float) * static_cast<size_t>(hgrid) * shs::kMaxK * sc->K * 128);
+                e = cudaMalloc(&sc->hwork, sizeof(float) * static_cast<size_t>(hgrid) * shs::kMaxK * (sc->K + 2) * 128);
             if (e != cudaSuccess) return cuda_fail(e, "allocate tensor-core adjoint workspace");
         }
         const float* f = sf;

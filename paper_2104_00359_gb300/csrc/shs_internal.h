@@ -124,7 +124,7 @@ struct TcArgs {
     int partial_stride;
     int partial_rows;        // rows the pair pass will reduce (deterministic mode)
     int deterministic;
-    float* hist;             // [grid][kMaxK][K][128] squaring operands (adjoint workspace)
+    float* hist;             // [grid][kMaxK][K + 2][128] squaring operands and row shifts (adjoint workspace)
 };
 
 constexpr int tc_prec_bf16 = 0, tc_prec_fp16 = 1, tc_prec_tf32 = 2;   // operand types of the tensor-core tails
@@ -133,8 +133,8 @@ constexpr int kTcQ = 256;    // quadrature directions (242 used) for 8 bands
 template <int NB> cudaError_t launch_forward_pairs(const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_tail_tc_fwd(const TcArgs& a, cudaStream_t s);
 cudaError_t launch_tail_tc_bwd(const TcArgs& a, cudaStream_t s);
-int tail_tc_chunk(int precision);              // directions per table chunk
-size_t tail_tc_chunk_bytes(int precision);
+int tail_tc_chunk(int precision, int adjoint);            // directions per table chunk
+size_t tail_tc_chunk_bytes(int precision, int adjoint);
 int tail_tc_bwd_grid();                         // blocks of the adjoint tail (rows of its workspace)
 template <int NB> cudaError_t launch_forward_batch(const FwdBatch& b, cudaStream_t s);
 template <int NB> cudaError_t launch_backward_batch(const BwdBatch& b, cudaStream_t s);

@@ -20,10 +20,13 @@
 // l >= 3).  X_S comes from the tensor cores; the sum over directions runs on
 // the CUDA cores.
 //
-// Roles in a block of 160 threads: warps 0-3 are the compute warps (thread
-// = point = tensor-memory lane): exponent set-up, squaring and splitting the
-// GEMM outputs, the direction sums.  Lane 0 of warp 4 issues the MMAs and the
-// table copies.  Hand-offs go through mbarriers; every wait is bounded (about
+// Roles in a block of 288 threads: warps 0-7 are the compute warps, two
+// threads per point (tensor-memory lane): warps w and w + 4 read lanes
+// 32 (w % 4) .. + 31 and take the two halves of each chunk's columns and of
+// each per-point operand row; both keep the point's full exponent state.  They
+// set up the exponent, square and split the GEMM outputs and run the
+// direction sums (the first half alone).  Lane 0 of warp 8 issues the MMAs
+// and the table copies.  Hand-offs go through mbarriers; every wait is bounded (about
 // one second) and a timeout makes every role stop, drain its copies and MMAs
 // and return with SHS_ERR_TIMEOUT in the status word.
 
@@ -46,36 +49,18 @@ namespace {
 constexpr int K = 64;
 constexpr int KPAD = 64;
 constexpr int kQ = kTcQ;          // 256 directions (242 with weight)
-constexpr int kCompute = 128;     // compute threads
-constexpr int kThreads = 160;     // + the MMA / copy warp
+constexpr int kCompute = 256;     // compute threads: two per point (one per half of each chunk)
+constexpr int kThreads = 288;     // + the MMA / copy warp
+constexpr int kMmaWarp = kCompute / 32;
 constexpr int kSmemBudget = 227 * 1024;
 using SH = shsgen::SH<8>;
 
-// Shared-memory plan of one tail kernel: per-point split operands (A: S, and
-// for the adjoint A2: dS), double-buffered chunk operands Xs, the table ring,
-// and the direction table.
-template <int PR, int CQ, bool BWD>
-struct Plan {
-    using P = tc::Prec<PR>;
-    static constexpr int EB = P::kElem, NP = P::kParts;
-    static constexpr int NCH = kQ / CQ;
-    static constexpr uint32_t kA = 128u * 64 * EB;      // one part of a [128 x 64] operand
-    static constexpr uint32_t kXs = 128u * CQ * EB;     // one part of a [128 x CQ] operand
-    static constexpr uint32_t kTb = CQ * 64u * EB;      // one part of Y_c or (wY)_c
-    static constexpr uint32_t kChunk = 2u * NP * kTb;   // Y_c parts, then (wY)_c parts
-    static constexpr uint32_t kOffA = 0;
-    static constexpr uint32_t kOffA2 = kOffA + NP * kA;
-    static constexpr uint32_t kOffXs = kOffA2 + (BWD ? NP * kA : 0);
-    static constexpr uint32_t kOffDir = kOffXs + 2 * NP * kXs;
-    static constexpr uint32_t kOffRing = kOffDir + kQ * 28;   // float4 dir, 3 floats of light
-    static constexpr int kStatic = 4096;                       // barriers, flags, per-warp sums
-    static constexpr int R0 = static_cast<int>((kSmemBudget - kStatic - kOffRing) / kChunk);
-    static constexpr int R = R0 > 4 ? 4 : R0;
-    static_assert(R >= 2, "table ring needs two stages");
-    static constexpr uint32_t kBytes = kOffRing + R * kChunk;
-    static constexpr uint32_t kIdescX = tc::idesc_of<PR>(128, CQ);   // X_c = A Y_c^T
-    static constexpr uint32_t kIdescS = tc::idesc_of<PR>(128, 64);   // S' += Xs (wY)_c
-};
+// Directions per table chunk: the forward streams wider chunks (its operands
+// live in tensor memory), the adjoint narrower ones (two operand rows and the
+// chunk operands share shared memory with the ring).
+constexpr int kCqFwdBF16 = 64, kCqFwdFP16 = 64, kCqFwdTF32 = 32;
+constexpr int kCqBwdBF16 = 32, kCqBwdFP16 = 32, kCqBwdTF32 = 16;
+
 
 // Lobe H(t) = c1 t + e0 + e1 t^2 + e2 t^4 + e3 t^6 and its derivative.
 struct Lobe {
@@ -99,15 +84,6 @@ __device__ __forceinline__ int row_shift(const float* S) {
     for (int i = 0; i < K; ++i) sabs += fabsf(S[i]);
     if (!(sabs > 1e-30f)) return 0;
     return min(64, max(-64, ilogbf(1.25f * sabs) - 6));
-}
-
-template <int PR>
-__device__ __forceinline__ void store_operand64(unsigned char* base, uint32_t part_bytes, int row, const float* S,
-                                                int sh) {
-    float Sd[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) Sd[i] = ldexpf(S[i], -sh);
-    tc::store_row_split<PR, 64>(base, part_bytes, row, Sd);
 }
 
 // Direction table: s_dir[q] = (x, y, z, w_q), s_lc[c][q] = L_c(w_q).
@@ -136,7 +112,7 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
 }
 
 __device__ __forceinline__ void named_sync_compute() {
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, 256;" ::: "memory");
 }
 
 // Exponent set-up of one point (DC isolation, scaling, optimal linear step):
@@ -170,11 +146,16 @@ __device__ __forceinline__ ExpState exp_setup(const SceneView& sc, const float* 
 // seq - 2 (whose MMAs it committed a step earlier) with chunk seq - 2 + R.
 template <int R, int NCH, uint32_t CHUNK>
 struct Ring {
+    // With as many stages as chunks the tables stay resident: each chunk is
+    // copied once and its stage's barrier completes once (phase 0).
+    static constexpr bool kResident = R >= NCH;
     uint64_t* full;
     uint64_t* empty;
     unsigned char* base;
     const unsigned char* src;
     uint32_t issued = 0;
+
+    __device__ static uint32_t full_parity(uint32_t s) { return kResident ? 0u : (s / R) & 1u; }
 
     __device__ void load(uint32_t s) {
         const uint32_t st = s % R;
@@ -198,6 +179,7 @@ struct Ring {
     }
     // Before consuming chunk seq: make sure its copy was issued.
     __device__ bool ensure(uint32_t seq, volatile int* abort, int* status) {
+        if (kResident) return true;
         while (issued <= seq)
             if (!load_next(abort, status)) return false;
         return true;
@@ -205,12 +187,16 @@ struct Ring {
     // After step seq committed the release of chunk seq - 1: refill the stage
     // released a step earlier (chunk seq - 2), if not done yet.
     __device__ bool refill(uint32_t seq, volatile int* abort, int* status) {
-        if (seq < 2 || issued > seq - 2 + R) return true;
+        if (kResident || seq < 2 || issued > seq - 2 + R) return true;
         return load_next(abort, status);
     }
     __device__ unsigned char* stage(uint32_t s) const { return base + (s % R) * CHUNK; }
     // Wait (bounded, ignoring aborts) for every copy still in flight.
     __device__ void drain(uint32_t consumed) {
+        if (kResident) {
+            for (uint32_t s = 0; s < static_cast<uint32_t>(R); ++s) (void)tc::mbar_wait(&full[s], 0u);
+            return;
+        }
         for (uint32_t s = consumed; s < issued; ++s) (void)tc::mbar_wait(&full[s % R], (s / R) & 1u);
     }
 };
@@ -218,24 +204,54 @@ struct Ring {
 // ---------------------------------------------------------------------------
 // forward tail
 // ---------------------------------------------------------------------------
+// The per-point operands live in tensor memory (the MMAs read A from there):
+// shared memory holds only the tables, resident for BF16 / FP16 (all chunks)
+// and streamed through a ring for TF32.  Tensor-memory columns: the split S
+// (kTmS), two fp32 buffers of X = S Y_c^T (kTmX), two split (X o X) operands
+// (kTmXs), the accumulator S' (kTmAcc).
+template <int PR, int CQ>
+struct PlanF {
+    using P = tc::Prec<PR>;
+    static constexpr int EB = P::kElem, NP = P::kParts;
+    static constexpr int NCH = kQ / CQ;
+    static constexpr uint32_t kTb = CQ * 64u * EB;       // one part of Y_c or (wY)_c
+    static constexpr uint32_t kChunk = 2u * NP * kTb;
+    static constexpr uint32_t kOffDir = 0;
+    static constexpr uint32_t kOffRing = kQ * 28;         // float4 dir, 3 floats of light
+    static constexpr int kStatic = 4096;
+    static constexpr int R0 = static_cast<int>((kSmemBudget - kStatic - kOffRing) / kChunk);
+    static constexpr int R = R0 >= NCH ? NCH : (R0 > 6 ? 6 : R0);
+    static_assert(R >= 3, "table ring needs three stages");
+    static constexpr uint32_t kBytes = kOffRing + R * kChunk;
+    static constexpr uint32_t kColsS = tc::tmem_cols<PR>(64);      // one part of S
+    static constexpr uint32_t kColsX = tc::tmem_cols<PR>(CQ);      // one part of an (X o X) chunk
+    static constexpr uint32_t kTmS = 0;
+    static constexpr uint32_t kTmX = kTmS + NP * kColsS;
+    static constexpr uint32_t kTmXs = kTmX + 2 * CQ;
+    static constexpr uint32_t kTmAcc = kTmXs + 2 * NP * kColsX;
+    static_assert(kTmAcc + 64 <= 512, "tensor memory plan");
+    static constexpr uint32_t kIdescX = tc::idesc_of<PR>(128, CQ);
+    static constexpr uint32_t kIdescS = tc::idesc_of<PR>(128, 64);
+};
+
 template <int PR, int CQ>
 __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_constant__ TcArgs a) {
-    using PL = Plan<PR, CQ, false>;
-    constexpr int NCH = PL::NCH, R = PL::R;
+    using PL = PlanF<PR, CQ>;
+    constexpr int NCH = PL::NCH, R = PL::R, NP = PL::NP;
+    constexpr int HQ = CQ / 2;   // each of a point's two threads takes half of a chunk's columns
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) uint64_t full[R], empty[R], xr[2], xs[2], g2[2], ar, sp, fin;
+    __shared__ __align__(8) uint64_t full[R], empty[R], xr[2], xs[2], g2[2], ar, sp, fin, hb, hb2;
     __shared__ uint32_t tmem_base;
     __shared__ int s_kt;
     __shared__ int s_abort;
+    __shared__ float s_bx[128][3];
     const int tid = threadIdx.x, warp = tid >> 5;
-    unsigned char* sA = sm + PL::kOffA;
-    unsigned char* sXs = sm + PL::kOffXs;
     float4* s_dir = reinterpret_cast<float4*>(sm + PL::kOffDir);
     float (*s_lc)[kQ] = reinterpret_cast<float (*)[kQ]>(s_dir + kQ);
     unsigned char* sRing = sm + PL::kOffRing;
     volatile int* abort = &s_abort;
 
-    if (warp == 0) tc::tmem_alloc(&tmem_base, 128);
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
     if (tid == 0) {
         for (int i = 0; i < R; ++i) {
             tc::mbar_init(&full[i], 1);
@@ -249,6 +265,8 @@ __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_c
         tc::mbar_init(&ar, kCompute);
         tc::mbar_init(&sp, 1);
         tc::mbar_init(&fin, 1);
+        tc::mbar_init(&hb, 128);
+        tc::mbar_init(&hb2, 128);
         s_kt = 0;
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -260,15 +278,14 @@ __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_c
     const int64_t P = a.n_points;
     const int64_t ntiles = (P + 127) / 128;
 
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
         if ((tid & 31) == 0) {
             // ---------------- MMA / copy issuer
             Ring<R, NCH, PL::kChunk> ring{full, empty, sRing, static_cast<const unsigned char*>(a.chunks)};
             ring.prime();
-            uint32_t seq = 0, arc = 0, xsc[2] = {0u, 0u};
+            uint32_t seq = 0, arc = 0, xn = 0;   // xn: xs waits so far (buffer xn & 1)
             bool ok = true;
-            const uint32_t aA = tc::smem_u32(sA), aXs = tc::smem_u32(sXs);
-            for (int64_t tile = blockIdx.x, it = 0; ok && tile < ntiles; tile += gridDim.x, ++it) {
+            for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
                 int kt = 0;
                 for (int pass = 0; ok; ++pass) {
                     ok = tc::mbar_wait_or_abort(&ar, arc & 1u, abort, a.sc.status);
@@ -277,44 +294,37 @@ __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_c
                     tc::fence_after_sync();
                     if (pass == 0) kt = s_kt & 31;
                     const bool shading = pass == kt;
-                    for (int c = 0; ok && c < NCH; ++c, ++seq) {
-                        ok = ring.ensure(seq, abort, a.sc.status) &&
-                             tc::mbar_wait_or_abort(&full[seq % R], (seq / R) & 1u, abort, a.sc.status);
-                        if (!ok) break;
-                        const uint32_t st = tc::smem_u32(ring.stage(seq));
-                        tc::gemm_split<PR, 64>(tmem + (c & 1) * 32, aA, PL::kA, st, PL::kTb, PL::kIdescX, false);
-                        tc::commit(&xr[c & 1]);
+                    for (int c = 0; ok && c <= NCH; ++c) {
+                        if (c < NCH) {
+                            ok = ring.ensure(seq, abort, a.sc.status) &&
+                                 tc::mbar_wait_or_abort(&full[seq % R], ring.full_parity(seq), abort, a.sc.status);
+                            if (!ok) break;
+                            tc::gemm_split_ts<PR, 64, PL::kColsS, PL::kTb>(tmem + PL::kTmX + (c & 1) * CQ,
+                                                                          tmem + PL::kTmS,
+                                                                          tc::smem_u32(ring.stage(seq)), PL::kIdescX,
+                                                                          false);
+                            tc::commit(&xr[c & 1]);
+                        }
                         if (c >= 1) {
                             const int b = (c - 1) & 1;
-                            ok = tc::mbar_wait_or_abort(&xs[b], xsc[b] & 1u, abort, a.sc.status);
-                            ++xsc[b];
+                            ok = tc::mbar_wait_or_abort(&xs[b], (xn >> 1) & 1u, abort, a.sc.status);
+                            ++xn;
                             if (!ok) break;
                             tc::fence_after_sync();
                             if (!shading) {
-                                const uint32_t stp = tc::smem_u32(ring.stage(seq - 1));
-                                tc::gemm_split<PR, CQ>(tmem + 64, aXs + b * PL::NP * PL::kXs, PL::kXs,
-                                                       stp + PL::NP * PL::kTb, PL::kTb, PL::kIdescS, c - 1 > 0);
+                                tc::gemm_split_ts<PR, CQ, PL::kColsX, PL::kTb>(
+                                    tmem + PL::kTmAcc, tmem + PL::kTmXs + b * NP * PL::kColsX,
+                                    tc::smem_u32(ring.stage(seq - 1)) + NP * PL::kTb, PL::kIdescS, c - 1 > 0);
                                 tc::commit(&g2[b]);
                             }
-                            tc::commit(&empty[(seq - 1) % R]);
+                            if (!ring.kResident) tc::commit(&empty[(seq - 1) % R]);
+                            if (c == NCH && !shading) tc::commit(&sp);
                         }
-                        ok = ring.refill(seq, abort, a.sc.status);
+                        if (c < NCH) {
+                            ok = ring.refill(seq, abort, a.sc.status);
+                            ++seq;
+                        }
                     }
-                    if (!ok) break;
-                    // last chunk of the pass
-                    const int b = (NCH - 1) & 1;
-                    ok = tc::mbar_wait_or_abort(&xs[b], xsc[b] & 1u, abort, a.sc.status);
-                    ++xsc[b];
-                    if (!ok) break;
-                    tc::fence_after_sync();
-                    if (!shading) {
-                        const uint32_t stp = tc::smem_u32(ring.stage(seq - 1));
-                        tc::gemm_split<PR, CQ>(tmem + 64, aXs + b * PL::NP * PL::kXs, PL::kXs,
-                                               stp + PL::NP * PL::kTb, PL::kTb, PL::kIdescS, NCH > 1);
-                        tc::commit(&g2[b]);
-                    }
-                    tc::commit(&empty[(seq - 1) % R]);
-                    if (!shading) tc::commit(&sp);
                     if (shading) break;
                 }
             }
@@ -326,12 +336,13 @@ __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_c
         // ---------------- compute warps
         load_directions(a, s_dir, s_lc);
         named_sync_compute();
-        const uint32_t lane_tm = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+        const int row = tid & 127, half = tid >> 7;
+        const uint32_t lane_tm = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
         const Lobe hl{a.lobe_c1, a.lobe_e[0], a.lobe_e[1], a.lobe_e[2], a.lobe_e[3]};
-        uint32_t xrc[2] = {0u, 0u}, g2c[2] = {0u, 0u}, spc = 0, arc = 0;
+        uint32_t cn = 0, g2n = 0, spc = 0, arc = 0;   // chunks seen, chunks sent to the projection GEMM
         bool ok = true;
         for (int64_t tile = blockIdx.x, it = 0; ok && tile < ntiles; tile += gridDim.x, ++it) {
-            const int64_t p = tile * 128 + tid;
+            const int64_t p = tile * 128 + row;
             const bool live = p < P;
             const int64_t q = live ? p : 0;
             float S[K];
@@ -352,9 +363,20 @@ __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_c
             float B0 = 0.f, B1 = 0.f, B2 = 0.f;
             int kt = 0, sh = 0;
             for (int pass = 0; ok; ++pass) {
+                // this thread's half of the split S (scaled by 2^-sh) into tensor memory
                 sh = row_shift(S);
-                store_operand64<PR>(sA, PL::kA, tid, S, sh);
-                tc::fence_async_smem();
+                {
+                    float Sd[32];
+                    if (half) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) Sd[i] = ldexpf(S[32 + i], -sh);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) Sd[i] = ldexpf(S[i], -sh);
+                    }
+                    tc::tmem_store_split<PR, 32>(lane_tm + PL::kTmS, PL::kColsS, 32 * half, Sd);
+                    tc::tmem_wait_st();
+                }
                 tc::fence_before_sync();
                 tc::mbar_arrive(&ar);
                 if (pass == 0) {
@@ -366,67 +388,88 @@ __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_c
                 const bool shading = pass == kt;
                 for (int c = 0; ok && c < NCH; ++c) {
                     const int b = c & 1;
-                    ok = warp_wait(&xr[b], xrc[b] & 1u, abort, a.sc.status);
-                    ++xrc[b];
+                    ok = warp_wait(&xr[b], (cn >> 1) & 1u, abort, a.sc.status);
+                    ++cn;
                     if (!ok) break;
                     tc::fence_after_sync();
-                    float X[CQ];
-                    tc::tmem_ld<CQ>(lane_tm + b * 32, X);
+                    float X[HQ];
+                    tc::tmem_ld<HQ>(lane_tm + PL::kTmX + b * CQ + half * HQ, X);
                     if (!shading) {
 #pragma unroll
-                        for (int i = 0; i < CQ; ++i) X[i] *= X[i];
+                        for (int i = 0; i < HQ; ++i) X[i] *= X[i];
                         if (c >= 2) {
-                            ok = warp_wait(&g2[b], (g2c[b] - 1) & 1u, abort, a.sc.status);
+                            ok = warp_wait(&g2[b], ((g2n - 2) >> 1) & 1u, abort, a.sc.status);
                             if (!ok) break;
                         }
-                        tc::store_row_split<PR, CQ>(sXs + b * PL::NP * PL::kXs, PL::kXs, tid, X);
-                        tc::fence_async_smem();
-                        tc::fence_before_sync();
-                        tc::mbar_arrive(&xs[b]);
-                        ++g2c[b];
+                        tc::tmem_store_split<PR, HQ>(lane_tm + PL::kTmXs + b * NP * PL::kColsX, PL::kColsX,
+                                                      half * HQ, X);
+                        tc::tmem_wait_st();
+                        ++g2n;
                     } else {
-#pragma unroll 4
-                        for (int i = 0; i < CQ; ++i) {
-                            const int qd = c * CQ + i;
-                            const float4 d = s_dir[qd];
+                        const int q0 = c * CQ + half * HQ;
+#pragma unroll
+                        for (int i = 0; i < HQ; ++i) {
+                            const float4 d = s_dir[q0 + i];
                             const float t = fmaf(ux, d.x, fmaf(uy, d.y, uz * d.z));
                             const float xw = X[i] * lobe(hl, t) * d.w;
-                            B0 = fmaf(xw, s_lc[0][qd], B0);
-                            B1 = fmaf(xw, s_lc[1][qd], B1);
-                            B2 = fmaf(xw, s_lc[2][qd], B2);
+                            B0 = fmaf(xw, s_lc[0][q0 + i], B0);
+                            B1 = fmaf(xw, s_lc[1][q0 + i], B1);
+                            B2 = fmaf(xw, s_lc[2][q0 + i], B2);
                         }
-                        tc::fence_before_sync();
-                        tc::mbar_arrive(&xs[b]);
                     }
+                    tc::fence_before_sync();
+                    tc::mbar_arrive(&xs[b]);
                 }
                 if (!ok || shading) break;
                 ok = warp_wait(&sp, spc & 1u, abort, a.sc.status);
                 ++spc;
                 if (!ok) break;
                 tc::fence_after_sync();
-                float Sn[K];
-                tc::tmem_ld<64>(lane_tm + 64, Sn);
-                tc::fence_before_sync();
-                if (pass < ex.k) {
-                    const float up = ldexpf(a.b2_unscale, 2 * sh);
+                // tensor-memory loads are warp-collective: every lane loads, then
+                // only points that take part in this squaring keep the result
+                const bool take = pass < ex.k;
+                const float up = ldexpf(a.b2_unscale, 2 * sh);
 #pragma unroll
-                    for (int i = 0; i < K; ++i) S[i] = Sn[i] * up;
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    float Sn[32];
+                    tc::tmem_ld<32>(lane_tm + PL::kTmAcc + 32 * h2, Sn);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) S[32 * h2 + i] = take ? Sn[i] * up : S[32 * h2 + i];
                 }
+                tc::fence_before_sync();
             }
             if (!ok) break;
-            if (live) {
-                const float s3 = ex.e0 * ldexpf(1.f, sh);
-                a.radiance[3 * q] = __ldg(a.albedo + 3 * q) * B0 * s3;
-                a.radiance[3 * q + 1] = __ldg(a.albedo + 3 * q + 1) * B1 * s3;
-                a.radiance[3 * q + 2] = __ldg(a.albedo + 3 * q + 2) * B2 * s3;
-                if (a.saved_k) a.saved_k[q] = ex.k;
+            // the two halves' direction sums meet in shared memory
+            if (half) {
+                if (it > 0) {
+                    ok = warp_wait(&hb2, (it - 1) & 1, abort, a.sc.status);
+                    if (!ok) break;
+                }
+                s_bx[row][0] = B0;
+                s_bx[row][1] = B1;
+                s_bx[row][2] = B2;
+                tc::mbar_arrive(&hb);
+            } else {
+                ok = warp_wait(&hb, it & 1, abort, a.sc.status);
+                if (!ok) break;
+                B0 += s_bx[row][0];
+                B1 += s_bx[row][1];
+                B2 += s_bx[row][2];
+                tc::mbar_arrive(&hb2);
+                if (live) {
+                    const float s3 = ex.e0 * ldexpf(1.f, sh);
+                    a.radiance[3 * q] = __ldg(a.albedo + 3 * q) * B0 * s3;
+                    a.radiance[3 * q + 1] = __ldg(a.albedo + 3 * q + 1) * B1 * s3;
+                    a.radiance[3 * q + 2] = __ldg(a.albedo + 3 * q + 2) * B2 * s3;
+                    if (a.saved_k) a.saved_k[q] = ex.k;
+                }
             }
         }
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
 // ---------------------------------------------------------------------------
@@ -448,27 +491,59 @@ __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_c
 //                   projecting with w Y is evaluating with Y, and back).
 // Then the optimal-linear step and the scaling in float32 (as the CUDA-core
 // adjoint) give df, stored for the pair pass.
+// Operands in tensor memory as in the forward: A (S_t) and A2 (dS_{t+1}, or
+// in the shading pass the second projected operand X_S H), two fp32 buffers
+// each of X = A Y_c^T and G = A2 Y_c^T, two split chunk operands Z, and the
+// accumulators (the second, W, shares G's columns where they suffice).
+template <int PR, int CQ>
+struct PlanB {
+    using P = tc::Prec<PR>;
+    static constexpr int EB = P::kElem, NP = P::kParts;
+    static constexpr int NCH = kQ / CQ;
+    static constexpr uint32_t kTb = CQ * 64u * EB;
+    static constexpr uint32_t kChunk = 2u * NP * kTb;
+    static constexpr uint32_t kOffDir = 0;
+    static constexpr uint32_t kOffRing = kQ * 28;
+    static constexpr int kStatic = 8192;
+    static constexpr int R0 = static_cast<int>((kSmemBudget - kStatic - kOffRing) / kChunk);
+    static constexpr int R = R0 >= NCH ? NCH : (R0 > 6 ? 6 : R0);
+    static_assert(R >= 3, "table ring needs three stages");
+    static constexpr uint32_t kBytes = kOffRing + R * kChunk;
+    static constexpr uint32_t kColsS = tc::tmem_cols<PR>(64);
+    static constexpr uint32_t kColsX = tc::tmem_cols<PR>(CQ);
+    static constexpr uint32_t kTmA = 0;
+    static constexpr uint32_t kTmA2 = kTmA + NP * kColsS;
+    static constexpr uint32_t kTmX = kTmA2 + NP * kColsS;
+    static constexpr uint32_t kTmG = kTmX + 2 * CQ;
+    static constexpr uint32_t kTmZ = kTmG + 2 * CQ;
+    static constexpr uint32_t kTmAcc = kTmZ + 2 * NP * kColsX;
+    static constexpr uint32_t kTmW = 2 * CQ >= 64 ? kTmG : kTmAcc + 64;
+    static_assert((2 * CQ >= 64 ? kTmAcc + 64 : kTmW + 64) <= 512, "tensor memory plan");
+    static_assert(2 * NP * kColsX <= NP * kColsS, "shading operands fit in A2's columns");
+    static constexpr uint32_t kIdescX = tc::idesc_of<PR>(128, CQ);
+    static constexpr uint32_t kIdescS = tc::idesc_of<PR>(128, 64);
+};
+
 template <int PR, int CQ>
 __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_constant__ TcArgs a) {
-    using PL = Plan<PR, CQ, true>;
+    using PL = PlanB<PR, CQ>;
     constexpr int NCH = PL::NCH, R = PL::R, NP = PL::NP;
+    constexpr int HQ = CQ / 2;
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) uint64_t full[R], empty[R], xr[2], xs[2], g2[2], ar, sp, fin;
+    __shared__ __align__(8) uint64_t full[R], empty[R], xr[2], xs[2], g2[2], ar, sp, fin, hb, hb2;
     __shared__ uint32_t tmem_base;
     __shared__ int s_kt;
     __shared__ int s_abort;
     __shared__ float s_dl[4][3 * K + 1];
     __shared__ float s_lsum[3];
+    __shared__ float s_bx[128][7];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    unsigned char* sA = sm + PL::kOffA;
-    unsigned char* sA2 = sm + PL::kOffA2;
-    unsigned char* sXs = sm + PL::kOffXs;
     float4* s_dir = reinterpret_cast<float4*>(sm + PL::kOffDir);
     float (*s_lc)[kQ] = reinterpret_cast<float (*)[kQ]>(s_dir + kQ);
     unsigned char* sRing = sm + PL::kOffRing;
     volatile int* abort = &s_abort;
 
-    if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
     if (tid == 0) {
         for (int i = 0; i < R; ++i) {
             tc::mbar_init(&full[i], 1);
@@ -482,11 +557,13 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
         tc::mbar_init(&ar, kCompute);
         tc::mbar_init(&sp, 1);
         tc::mbar_init(&fin, 1);
+        tc::mbar_init(&hb, 128);
+        tc::mbar_init(&hb2, 128);
         s_kt = 0;
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int e = tid; e < 4 * (3 * K + 1); e += kThreads) (&s_dl[0][0])[e] = 0.f;
+    for (int e = tid; e < 4 * (3 * K + 1); e += kThreads) (&s_dl[0][0])[e] = 0.f;   // per lane group
     if (tid < 3) {
         float t = 0.f;
         for (int i = 0; i < K; ++i) t += fabsf(__ldg(a.sc.light + tid * KPAD + i));
@@ -499,15 +576,14 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
     const int64_t P = a.n_points;
     const int64_t ntiles = (P + 127) / 128;
 
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
         if (lane == 0) {
             // ---------------- MMA / copy issuer
             Ring<R, NCH, PL::kChunk> ring{full, empty, sRing, static_cast<const unsigned char*>(a.chunks)};
             ring.prime();
-            uint32_t seq = 0, arc = 0, xsc[2] = {0u, 0u};
+            uint32_t seq = 0, arc = 0, xn = 0;
             bool ok = true;
-            const uint32_t aA = tc::smem_u32(sA), aA2 = tc::smem_u32(sA2), aXs = tc::smem_u32(sXs);
-            for (int64_t tile = blockIdx.x, it = 0; ok && tile < ntiles; tile += gridDim.x, ++it) {
+            for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
                 int kt = 0;
                 for (int pass = 0; ok && pass <= 2 * kt; ++pass) {
                     ok = tc::mbar_wait_or_abort(&ar, arc & 1u, abort, a.sc.status);
@@ -519,29 +595,32 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
                     for (int c = 0; ok && c <= NCH; ++c) {
                         if (c < NCH) {
                             ok = ring.ensure(seq, abort, a.sc.status) &&
-                                 tc::mbar_wait_or_abort(&full[seq % R], (seq / R) & 1u, abort, a.sc.status);
+                                 tc::mbar_wait_or_abort(&full[seq % R], ring.full_parity(seq), abort, a.sc.status);
                             if (!ok) break;
                             const uint32_t st = tc::smem_u32(ring.stage(seq));
-                            tc::gemm_split<PR, 64>(tmem + (c & 1) * 32, aA, PL::kA, st, PL::kTb, PL::kIdescX, false);
+                            tc::gemm_split_ts<PR, 64, PL::kColsS, PL::kTb>(tmem + PL::kTmX + (c & 1) * CQ,
+                                                                          tmem + PL::kTmA, st, PL::kIdescX, false);
                             if (adj)
-                                tc::gemm_split<PR, 64>(tmem + 64 + (c & 1) * 32, aA2, PL::kA, st, PL::kTb, PL::kIdescX,
-                                                       false);
+                                tc::gemm_split_ts<PR, 64, PL::kColsS, PL::kTb>(tmem + PL::kTmG + (c & 1) * CQ,
+                                                                              tmem + PL::kTmA2, st, PL::kIdescX,
+                                                                              false);
                             tc::commit(&xr[c & 1]);
                         }
                         if (c >= 1) {
                             const int b = (c - 1) & 1;
-                            ok = tc::mbar_wait_or_abort(&xs[b], xsc[b] & 1u, abort, a.sc.status);
-                            ++xsc[b];
+                            ok = tc::mbar_wait_or_abort(&xs[b], (xn >> 1) & 1u, abort, a.sc.status);
+                            ++xn;
                             if (!ok) break;
                             tc::fence_after_sync();
                             const uint32_t wy = tc::smem_u32(ring.stage(seq - 1)) + NP * PL::kTb;
-                            tc::gemm_split<PR, CQ>(tmem + 128, aXs + b * NP * PL::kXs, PL::kXs, wy, PL::kTb,
-                                                   PL::kIdescS, c - 1 > 0);
+                            tc::gemm_split_ts<PR, CQ, PL::kColsX, PL::kTb>(
+                                tmem + PL::kTmAcc, tmem + PL::kTmZ + b * NP * PL::kColsX, wy, PL::kIdescS, c - 1 > 0);
                             if (shade)
-                                tc::gemm_split<PR, CQ>(tmem + 192, aA2 + b * NP * PL::kXs, PL::kXs, wy, PL::kTb,
-                                                       PL::kIdescS, c - 1 > 0);
+                                tc::gemm_split_ts<PR, CQ, PL::kColsX, PL::kTb>(
+                                    tmem + PL::kTmW, tmem + PL::kTmA2 + b * NP * PL::kColsX, wy, PL::kIdescS,
+                                    c - 1 > 0);
                             tc::commit(&g2[b]);
-                            tc::commit(&empty[(seq - 1) % R]);
+                            if (!ring.kResident) tc::commit(&empty[(seq - 1) % R]);
                             if (c == NCH) tc::commit(&sp);
                         }
                         if (c < NCH) {
@@ -559,14 +638,16 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
         // ---------------- compute warps
         load_directions(a, s_dir, s_lc);
         named_sync_compute();
-        const uint32_t lane_tm = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+        const int row = tid & 127, half = tid >> 7, lg = warp & 3;
+        const uint32_t lane_tm = tmem + (static_cast<uint32_t>(lg * 32) << 16);
         const Lobe hl{a.lobe_c1, a.lobe_e[0], a.lobe_e[1], a.lobe_e[2], a.lobe_e[3]};
-        float* hist = a.hist + static_cast<size_t>(blockIdx.x) * (kMaxK * K * 128);
-        uint32_t xrc[2] = {0u, 0u}, g2c[2] = {0u, 0u}, spc = 0, arc = 0;
+        // per block: [kMaxK][K + 2][128] -- S_t by coefficient, then each half's row shift
+        float* hist = a.hist + static_cast<size_t>(blockIdx.x) * (kMaxK * (K + 2) * 128);
+        uint32_t cn = 0, g2n = 0, spc = 0, arc = 0;   // chunks seen, chunks sent to the projection GEMM
         float loss_acc = 0.f;
         bool ok = true;
         for (int64_t tile = blockIdx.x, it = 0; ok && tile < ntiles; tile += gridDim.x, ++it) {
-            const int64_t p = tile * 128 + tid;
+            const int64_t p = tile * 128 + row;
             const bool live = p < P;
             const int64_t q = live ? p : 0;
             float V[K];      // S (forward passes), then dS (adjoint passes)
@@ -584,7 +665,7 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
             for (int i = 1; i < K; ++i) V[i] = ol.b * (V[i] * scale);
             atomicMax(&s_kt, static_cast<int>((it << 5) | k));
             float ux = 0.f, uy = 0.f, uz = 1.f, il = 0.f;
-            float dB[3] = {0.f, 0.f, 0.f}, u[3] = {0.f, 0.f, 0.f}, alb[3] = {0.f, 0.f, 0.f};
+            float dB[3] = {0.f, 0.f, 0.f}, u[3] = {0.f, 0.f, 0.f};
             if (live) {
                 const float nx = __ldg(a.normals + 3 * q), ny = __ldg(a.normals + 3 * q + 1),
                             nz = __ldg(a.normals + 3 * q + 2);
@@ -595,14 +676,13 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
                 uz = nz * il;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    alb[c] = __ldg(a.albedo + 3 * q + c);
                     if (a.target) {
                         dB[c] = __ldg(a.radiance_in + 3 * q + c) - __ldg(a.target + 3 * q + c);
-                        loss_acc = fmaf(0.5f * dB[c], dB[c], loss_acc);
+                        if (half == 0) loss_acc = fmaf(0.5f * dB[c], dB[c], loss_acc);
                     } else {
                         dB[c] = __ldg(a.d_radiance + 3 * q + c);
                     }
-                    u[c] = alb[c] * dB[c];
+                    u[c] = __ldg(a.albedo + 3 * q + c) * dB[c];
                 }
             }
             // scale of D H (the shading adjoint's projected operand): |L_c(w)| <= 1.1 sum |L_c,i|, |H| <= 1.1
@@ -610,31 +690,56 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
                 const float zb = 1.25f * (fabsf(u[0]) * s_lsum[0] + fabsf(u[1]) * s_lsum[1] + fabsf(u[2]) * s_lsum[2]);
                 return zb > 1e-30f ? min(64, max(-64, ilogbf(zb) - 6)) : 0;
             }();
-            float acc[3] = {0.f, 0.f, 0.f}, gn[3] = {0.f, 0.f, 0.f}, de0s = 0.f;
+            // direction sums of the shading adjoint: dB_c / (a_c e0 2^sh), dL/de0, dL/dn (unprojected)
+            float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float de0 = 0.f;
             int kt = 0, sh = 0, shg = 0;
             for (int pass = 0; ok && pass <= 2 * kt; ++pass) {
                 // operands of this pass (kt is still 0 before pass 0's barrier)
-                if (pass <= kt) {
-                    // forward passes and the shading pass: A = S_pass
-                    sh = row_shift(V);
-                    store_operand64<PR>(sA, PL::kA, tid, V, sh);
-                    if (pass == 0 || pass < kt) {
-                        // keep S_t for the adjoint (read back for t < kt only)
-#pragma unroll 8
-                        for (int i = 0; i < K; ++i) hist[(static_cast<size_t>(pass) * K + i) * 128 + tid] = V[i];
+                {
+                    float Sd[32];
+                    if (pass <= kt) {
+                        // forward passes and the shading pass: A = S_pass
+                        sh = row_shift(V);
+                        if (pass == 0 || pass < kt) {
+                            // keep this half of S_t and its row shift for the adjoint
+                            float* h = hist + static_cast<size_t>(pass) * (K + 2) * 128;
+                            if (half) {
+#pragma unroll
+                                for (int i = 32; i < 64; ++i) h[i * 128 + row] = V[i];
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 32; ++i) h[i * 128 + row] = V[i];
+                            }
+                            h[(K + half) * 128 + row] = __int_as_float(sh);
+                        }
+                        if (half) {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) Sd[i] = ldexpf(V[32 + i], -sh);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) Sd[i] = ldexpf(V[i], -sh);
+                        }
+                        tc::tmem_store_split<PR, 32>(lane_tm + PL::kTmA, PL::kColsS, 32 * half, Sd);
+                    } else {
+                        const int t = 2 * kt - pass;
+                        const float* h = hist + static_cast<size_t>(t) * (K + 2) * 128;
+                        sh = __float_as_int(h[(K + half) * 128 + row]);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) Sd[i] = ldexpf(h[(32 * half + i) * 128 + row], -sh);
+                        tc::tmem_store_split<PR, 32>(lane_tm + PL::kTmA, PL::kColsS, 32 * half, Sd);
+                        shg = row_shift(V);
+                        if (half) {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) Sd[i] = ldexpf(V[32 + i], -shg);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) Sd[i] = ldexpf(V[i], -shg);
+                        }
+                        tc::tmem_store_split<PR, 32>(lane_tm + PL::kTmA2, PL::kColsS, 32 * half, Sd);
                     }
-                } else {
-                    const int t = 2 * kt - pass;
-                    float Sh[K];
-#pragma unroll 8
-                    for (int i = 0; i < K; ++i) Sh[i] = hist[(static_cast<size_t>(t) * K + i) * 128 + tid];
-                    sh = row_shift(Sh);
-                    store_operand64<PR>(sA, PL::kA, tid, Sh, sh);
-                    shg = row_shift(V);
-                    store_operand64<PR>(sA2, PL::kA, tid, V, shg);
+                    tc::tmem_wait_st();
                 }
-                tc::fence_async_smem();
                 tc::fence_before_sync();
                 tc::mbar_arrive(&ar);
                 if (pass == 0) {
@@ -646,131 +751,137 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
                 const bool shade = pass == kt, adj = pass > kt;
                 for (int c = 0; ok && c < NCH; ++c) {
                     const int b = c & 1;
-                    ok = warp_wait(&xr[b], xrc[b] & 1u, abort, a.sc.status);
-                    ++xrc[b];
+                    ok = warp_wait(&xr[b], (cn >> 1) & 1u, abort, a.sc.status);
+                    ++cn;
                     if (!ok) break;
                     tc::fence_after_sync();
-                    float X[CQ];
-                    tc::tmem_ld<CQ>(lane_tm + b * 32, X);
+                    float X[HQ];
+                    tc::tmem_ld<HQ>(lane_tm + PL::kTmX + b * CQ + half * HQ, X);
+                    float Z2[HQ];
                     if (adj) {
-                        float G[CQ];
-                        tc::tmem_ld<CQ>(lane_tm + 64 + b * 32, G);
+                        float G[HQ];
+                        tc::tmem_ld<HQ>(lane_tm + PL::kTmG + b * CQ + half * HQ, G);
 #pragma unroll
-                        for (int i = 0; i < CQ; ++i) X[i] = 2.f * X[i] * G[i];
+                        for (int i = 0; i < HQ; ++i) X[i] = 2.f * X[i] * G[i];
                     } else if (!shade) {
 #pragma unroll
-                        for (int i = 0; i < CQ; ++i) X[i] *= X[i];
+                        for (int i = 0; i < HQ; ++i) X[i] *= X[i];
                     } else {
-                        float Z[CQ];
-#pragma unroll 4
-                        for (int i = 0; i < CQ; ++i) {
-                            const int qd = c * CQ + i;
-                            const float4 d = s_dir[qd];
-                            const float4 l = make_float4(s_lc[0][qd], s_lc[1][qd], s_lc[2][qd], 0.f);
+                        // this half's directions: the sums, Z = D H (scaled 2^-sz), Z2 = X H
+                        const int q0 = c * CQ + half * HQ;
+#pragma unroll
+                        for (int i = 0; i < HQ; ++i) {
+                            const float4 d = s_dir[q0 + i];
+                            const float l0 = s_lc[0][q0 + i], l1 = s_lc[1][q0 + i], l2 = s_lc[2][q0 + i];
                             const float t = fmaf(ux, d.x, fmaf(uy, d.y, uz * d.z));
-                            const float h = lobe(hl, t), hd = lobe_d(hl, t);
-                            const float D = fmaf(u[0], l.x, fmaf(u[1], l.y, u[2] * l.z));
+                            const float hv = lobe(hl, t), hd = lobe_d(hl, t);
+                            const float D = fmaf(u[0], l0, fmaf(u[1], l1, u[2] * l2));
                             const float wx = d.w * X[i];
-                            const float wxh = wx * h;
-                            acc[0] = fmaf(wxh, l.x, acc[0]);
-                            acc[1] = fmaf(wxh, l.y, acc[1]);
-                            acc[2] = fmaf(wxh, l.z, acc[2]);
-                            de0s = fmaf(wxh, D, de0s);
+                            const float wxh = wx * hv;
+                            acc[0] = fmaf(wxh, l0, acc[0]);
+                            acc[1] = fmaf(wxh, l1, acc[1]);
+                            acc[2] = fmaf(wxh, l2, acc[2]);
+                            acc[3] = fmaf(wxh, D, acc[3]);
                             const float gd = wx * D * hd;
-                            gn[0] = fmaf(gd, d.x, gn[0]);
-                            gn[1] = fmaf(gd, d.y, gn[1]);
-                            gn[2] = fmaf(gd, d.z, gn[2]);
-                            Z[i] = ldexpf(D * h, -sz);
-                            X[i] *= h;
+                            acc[4] = fmaf(gd, d.x, acc[4]);
+                            acc[5] = fmaf(gd, d.y, acc[5]);
+                            acc[6] = fmaf(gd, d.z, acc[6]);
+                            Z2[i] = X[i] * hv;
+                            X[i] = ldexpf(D * hv, -sz);
                         }
-                        if (c >= 2) {
-                            ok = warp_wait(&g2[b], (g2c[b] - 1) & 1u, abort, a.sc.status);
-                            if (!ok) break;
-                        }
-                        tc::store_row_split<PR, CQ>(sXs + b * NP * PL::kXs, PL::kXs, tid, Z);
-                        tc::store_row_split<PR, CQ>(sA2 + b * NP * PL::kXs, PL::kXs, tid, X);
-                        tc::fence_async_smem();
-                        tc::fence_before_sync();
-                        tc::mbar_arrive(&xs[b]);
-                        ++g2c[b];
-                        continue;
                     }
                     if (c >= 2) {
-                        ok = warp_wait(&g2[b], (g2c[b] - 1) & 1u, abort, a.sc.status);
+                        ok = warp_wait(&g2[b], ((g2n - 2) >> 1) & 1u, abort, a.sc.status);
                         if (!ok) break;
                     }
-                    tc::store_row_split<PR, CQ>(sXs + b * NP * PL::kXs, PL::kXs, tid, X);
-                    tc::fence_async_smem();
+                    tc::tmem_store_split<PR, HQ>(lane_tm + PL::kTmZ + b * NP * PL::kColsX, PL::kColsX, half * HQ, X);
+                    if (shade)
+                        tc::tmem_store_split<PR, HQ>(lane_tm + PL::kTmA2 + b * NP * PL::kColsX, PL::kColsX, half * HQ,
+                                                      Z2);
+                    tc::tmem_wait_st();
                     tc::fence_before_sync();
                     tc::mbar_arrive(&xs[b]);
-                    ++g2c[b];
+                    ++g2n;
                 }
                 if (!ok) break;
                 ok = warp_wait(&sp, spc & 1u, abort, a.sc.status);
                 ++spc;
                 if (!ok) break;
                 tc::fence_after_sync();
-                float Sn[K];
-                tc::tmem_ld<64>(lane_tm + 128, Sn);
-                if (pass < kt) {
-                    tc::fence_before_sync();
-                    if (pass < k) {
-                        const float up = ldexpf(a.b2_unscale, 2 * sh);
+                // the pass's accumulator (S', dV or dS') replaces V where the point takes part
+                const bool take = pass < kt ? pass < k : pass == kt ? true : 2 * kt - pass < k;
+                const float up = pass < kt ? ldexpf(a.b2_unscale, 2 * sh)
+                                           : pass == kt ? e0 * ldexpf(a.b2_unscale, sz)
+                                                        : ldexpf(a.b2_unscale, sh + shg);
 #pragma unroll
-                        for (int i = 0; i < K; ++i) V[i] = Sn[i] * up;
-                    }
-                } else if (shade) {
-                    // dS_k = e0 dV, W = e0 2^sh P[X H]; d_light += u_c W over the points
-                    float Wv[K];
-                    tc::tmem_ld<64>(lane_tm + 192, Wv);
-                    tc::fence_before_sync();
-                    const float dvs = e0 * ldexpf(a.b2_unscale, sz);
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    float Sn[32];
+                    tc::tmem_ld<32>(lane_tm + PL::kTmAcc + 32 * h2, Sn);
 #pragma unroll
-                    for (int i = 0; i < K; ++i) V[i] = Sn[i] * dvs;
+                    for (int i = 0; i < 32; ++i) V[32 * h2 + i] = take ? Sn[i] * up : V[32 * h2 + i];
+                }
+                if (shade) {
+                    // W = e0 2^sh P[X H]; d_light += u_c W over the points (this half's coefficients)
+                    float Wv[32];
+                    tc::tmem_ld<32>(lane_tm + PL::kTmW + 32 * half, Wv);
+                    tc::fence_before_sync();
                     const float ws = e0 * ldexpf(a.b2_unscale, sh);
 #pragma unroll
                     for (int c3 = 0; c3 < 3; ++c3) {
-                        float dl[K];
+                        float dl[32];
                         const float uc = live ? u[c3] * ws : 0.f;
 #pragma unroll
-                        for (int i = 0; i < K; ++i) dl[i] = uc * Wv[i];
-                        warp_sum_into<K>(dl, &s_dl[warp][c3 * K], lane);
+                        for (int i = 0; i < 32; ++i) dl[i] = uc * Wv[i];
+                        warp_sum_into<32>(dl, &s_dl[lg][c3 * K + 32 * half], lane);
                     }
-                    const float s2 = ldexpf(1.f, sh);
-                    de0 = de0s * s2;
-                    if (live) {
-                        if (a.d_albedo) {
-#pragma unroll
-                            for (int c3 = 0; c3 < 3; ++c3) a.d_albedo[3 * q + c3] = dB[c3] * e0 * s2 * acc[c3];
+                    // the halves' direction sums meet in shared memory
+                    if (half) {
+                        if (it > 0) {
+                            ok = warp_wait(&hb2, (it - 1) & 1, abort, a.sc.status);
+                            if (!ok) break;
                         }
-                        if (a.d_normals) {
-                            const float gx = e0 * s2 * gn[0], gy = e0 * s2 * gn[1], gz = e0 * s2 * gn[2];
-                            const float ug = ux * gx + uy * gy + uz * gz;
-                            a.d_normals[3 * q] = (gx - ux * ug) * il;
-                            a.d_normals[3 * q + 1] = (gy - uy * ug) * il;
-                            a.d_normals[3 * q + 2] = (gz - uz * ug) * il;
+#pragma unroll
+                        for (int j = 0; j < 7; ++j) s_bx[row][j] = acc[j];
+                        tc::mbar_arrive(&hb);
+                    } else {
+                        ok = warp_wait(&hb, it & 1, abort, a.sc.status);
+                        if (!ok) break;
+#pragma unroll
+                        for (int j = 0; j < 7; ++j) acc[j] += s_bx[row][j];
+                        tc::mbar_arrive(&hb2);
+                        const float s2 = ldexpf(1.f, sh);
+                        de0 = acc[3] * s2;
+                        if (live) {
+                            if (a.d_albedo) {
+#pragma unroll
+                                for (int c3 = 0; c3 < 3; ++c3) a.d_albedo[3 * q + c3] = dB[c3] * e0 * s2 * acc[c3];
+                            }
+                            if (a.d_normals) {
+                                const float gx = e0 * s2 * acc[4], gy = e0 * s2 * acc[5], gz = e0 * s2 * acc[6];
+                                const float ug = ux * gx + uy * gy + uz * gz;
+                                a.d_normals[3 * q] = (gx - ux * ug) * il;
+                                a.d_normals[3 * q + 1] = (gy - uy * ug) * il;
+                                a.d_normals[3 * q + 2] = (gz - uz * ug) * il;
+                            }
                         }
                     }
                 } else {
                     tc::fence_before_sync();
-                    if (2 * kt - pass < k) {
-                        const float up = ldexpf(a.b2_unscale, sh + shg);
-#pragma unroll
-                        for (int i = 0; i < K; ++i) V[i] = Sn[i] * up;
-                    }
                 }
             }
             if (!ok) break;
-            // optimal linear step and scaling: S_0 = a(s) sqrt(4 pi), S_i = b(s) g_i, g = f^ 2^-k
+            // optimal linear step and scaling: S_0 = a(s) sqrt(4 pi), S_i = b(s) g_i, g = f^ 2^-k;
+            // each half writes its 32 coefficients of df
             if (live) {
                 float dBs = 0.f;
 #pragma unroll
                 for (int i = 1; i < K; ++i) dBs = fmaf(V[i], __ldg(a.f + i * P + q) * scale, dBs);
                 const float dA = V[0] * kSqrt4Pi;
                 const float cg = fmaf(dA, ol.ca, dBs * ol.cb);
-                a.dfp_ws[q] = de0 * e0 * kInvSqrt4Pi * a.sc.neg_2pi_eps * SH::norm(0);
+                if (half == 0) a.dfp_ws[q] = de0 * e0 * kInvSqrt4Pi * a.sc.neg_2pi_eps * SH::norm(0);
 #pragma unroll
                 for (int i = 1; i < K; ++i) {
+                    if ((i >> 5) != half) continue;
                     const float gi = __ldg(a.f + i * P + q) * scale;
                     a.dfp_ws[i * P + q] = fmaf(ol.b, V[i], cg * gi) * scale * a.sc.neg_2pi_eps * SH::norm(i);
                 }
@@ -778,13 +889,13 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
         }
         if (a.target) {
             const float v = warp_sum(loss_acc);
-            if (lane == 0) s_dl[warp][3 * K] += v;
+            if (lane == 0) atomicAdd(&s_dl[lg][3 * K], v);
         }
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
     if (s_abort) return;
     // block partial row of the lighting gradient and loss
     for (int e = tid; e <= 3 * K; e += kThreads) {
@@ -801,7 +912,7 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
 
 template <int PR, int CQ>
 cudaError_t launch_fwd_t(const TcArgs& a, cudaStream_t s) {
-    using PL = Plan<PR, CQ, false>;
+    using PL = PlanF<PR, CQ>;
     auto kern = tail_fwd_tc_kernel<PR, CQ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(PL::kBytes));
@@ -819,7 +930,7 @@ cudaError_t launch_fwd_t(const TcArgs& a, cudaStream_t s) {
 
 template <int PR, int CQ>
 cudaError_t launch_bwd_t(const TcArgs& a, cudaStream_t s) {
-    using PL = Plan<PR, CQ, true>;
+    using PL = PlanB<PR, CQ>;
     auto kern = tail_bwd_tc_kernel<PR, CQ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(PL::kBytes));
@@ -844,20 +955,29 @@ int tail_tc_bwd_grid() {
 cudaError_t launch_tail_tc_bwd(const TcArgs& a, cudaStream_t s) {
     if (a.n_points <= 0) return cudaSuccess;
     switch (a.prec) {
-        case tc::kPrecBF16: return launch_bwd_t<tc::kPrecBF16, 32>(a, s);
-        case tc::kPrecFP16: return launch_bwd_t<tc::kPrecFP16, 32>(a, s);
-        case tc::kPrecTF32: return launch_bwd_t<tc::kPrecTF32, 16>(a, s);
+        case tc::kPrecBF16: return launch_bwd_t<tc::kPrecBF16, kCqBwdBF16>(a, s);
+        case tc::kPrecFP16: return launch_bwd_t<tc::kPrecFP16, kCqBwdFP16>(a, s);
+        case tc::kPrecTF32: return launch_bwd_t<tc::kPrecTF32, kCqBwdTF32>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-int tail_tc_chunk(int precision) { return precision == tc::kPrecTF32 ? 16 : 32; }
-
-size_t tail_tc_chunk_bytes(int precision) {
+int tail_tc_chunk(int precision, int adjoint) {
     switch (precision) {
-        case tc::kPrecBF16: return Plan<tc::kPrecBF16, 32, false>::kChunk;
-        case tc::kPrecFP16: return Plan<tc::kPrecFP16, 32, false>::kChunk;
-        case tc::kPrecTF32: return Plan<tc::kPrecTF32, 16, false>::kChunk;
+        case tc::kPrecBF16: return adjoint ? kCqBwdBF16 : kCqFwdBF16;
+        case tc::kPrecFP16: return adjoint ? kCqBwdFP16 : kCqFwdFP16;
+        default: return adjoint ? kCqBwdTF32 : kCqFwdTF32;
+    }
+}
+
+size_t tail_tc_chunk_bytes(int precision, int adjoint) {
+    switch (precision) {
+        case tc::kPrecBF16:
+            return adjoint ? PlanB<tc::kPrecBF16, kCqBwdBF16>::kChunk : PlanF<tc::kPrecBF16, kCqFwdBF16>::kChunk;
+        case tc::kPrecFP16:
+            return adjoint ? PlanB<tc::kPrecFP16, kCqBwdFP16>::kChunk : PlanF<tc::kPrecFP16, kCqFwdFP16>::kChunk;
+        case tc::kPrecTF32:
+            return adjoint ? PlanB<tc::kPrecTF32, kCqBwdTF32>::kChunk : PlanF<tc::kPrecTF32, kCqFwdTF32>::kChunk;
         default: return 0;
     }
 }
@@ -865,9 +985,9 @@ size_t tail_tc_chunk_bytes(int precision) {
 cudaError_t launch_tail_tc_fwd(const TcArgs& a, cudaStream_t s) {
     if (a.n_points <= 0) return cudaSuccess;
     switch (a.prec) {
-        case tc::kPrecBF16: return launch_fwd_t<tc::kPrecBF16, 32>(a, s);
-        case tc::kPrecFP16: return launch_fwd_t<tc::kPrecFP16, 32>(a, s);
-        case tc::kPrecTF32: return launch_fwd_t<tc::kPrecTF32, 16>(a, s);
+        case tc::kPrecBF16: return launch_fwd_t<tc::kPrecBF16, kCqFwdBF16>(a, s);
+        case tc::kPrecFP16: return launch_fwd_t<tc::kPrecFP16, kCqFwdFP16>(a, s);
+        case tc::kPrecTF32: return launch_fwd_t<tc::kPrecTF32, kCqFwdTF32>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

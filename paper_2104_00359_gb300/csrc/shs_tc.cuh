@@ -269,22 +269,86 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b
 // D (+)= A B^T for split operands: A [128 x KD] and B [N x KD], both K-major
 // with their parts `a_part` / `b_part` bytes apart; every product term of the
 // precision over all K steps.  Issued by one thread.
-template <int PR, int KD>
-__device__ __forceinline__ void gemm_split(uint32_t d_tmem, uint32_t a_addr, uint32_t a_part, uint32_t b_addr,
-                                           uint32_t b_part, uint32_t idesc, bool accumulate) {
+// The descriptors of one GEMM differ only in their start address (the low
+// 14-bit field, in 16-byte units): each is the first one plus a compile-time
+// offset.  Shared-memory addresses stay below 256 KB, so the sum never
+// carries out of the field.
+template <int PR, int KD, uint32_t A_PART, uint32_t B_PART>
+__device__ __forceinline__ void gemm_split(uint32_t d_tmem, uint32_t a_addr, uint32_t b_addr, uint32_t idesc,
+                                           bool accumulate) {
     constexpr uint32_t T = 16 / Prec<PR>::kElem;
     constexpr uint32_t SBO = (KD / T) * 128;
     constexpr int KS = KD / Prec<PR>::kKmma;
+    const uint64_t a0 = make_desc(a_addr, SBO), b0 = make_desc(b_addr, SBO);
 #pragma unroll
     for (int t = 0; t < Prec<PR>::kTerms; ++t) {
 #pragma unroll
         for (int ks = 0; ks < KS; ++ks) {
-            const uint64_t ad = make_desc(a_addr + term_a<PR>(t) * a_part + ks * 256, SBO);
-            const uint64_t bd = make_desc(b_addr + term_b<PR>(t) * b_part + ks * 256, SBO);
+            const uint64_t ad = a0 + ((term_a<PR>(t) * A_PART + ks * 256u) >> 4);
+            const uint64_t bd = b0 + ((term_b<PR>(t) * B_PART + ks * 256u) >> 4);
             mma<PR>(d_tmem, ad, bd, idesc, accumulate || t > 0 || ks > 0);
         }
     }
 }
+
+// D (+)= A B^T with A [128 x K] in tensor memory (lane = row; 16-bit types
+// two elements per 32-bit column, TF32 one), B from shared memory.
+template <int PR>
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                       bool accumulate) {
+    if constexpr (PR == kPrecTF32) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+            ::"r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate ? 1u : 0u)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+            ::"r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate ? 1u : 0u)
+            : "memory");
+    }
+}
+
+// Tensor-memory columns one part of a [128 x KD] operand takes.
+template <int PR>
+__host__ __device__ constexpr uint32_t tmem_cols(int KD) {
+    return static_cast<uint32_t>(KD * Prec<PR>::kElem / 4);
+}
+
+// As gemm_split with the split A in tensor memory: part j of A starts at
+// column a_tmem + j * A_COLS; one K step (32 bytes of K) takes 8 columns.
+template <int PR, int KD, uint32_t A_COLS, uint32_t B_PART>
+__device__ __forceinline__ void gemm_split_ts(uint32_t d_tmem, uint32_t a_tmem, uint32_t b_addr, uint32_t idesc,
+                                              bool accumulate) {
+    constexpr uint32_t T = 16 / Prec<PR>::kElem;
+    constexpr uint32_t SBO = (KD / T) * 128;
+    constexpr int KS = KD / Prec<PR>::kKmma;
+    const uint64_t b0 = make_desc(b_addr, SBO);
+#pragma unroll
+    for (int t = 0; t < Prec<PR>::kTerms; ++t) {
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+            const uint64_t bd = b0 + ((term_b<PR>(t) * B_PART + ks * 256u) >> 4);
+            mma_ts<PR>(d_tmem, a_tmem + term_a<PR>(t) * A_COLS + ks * 8u, bd, idesc, accumulate || t > 0 || ks > 0);
+        }
+    }
+}
+
+// Store 8 / 16 consecutive 32-bit columns of this thread's lane.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+                   "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
@@ -292,37 +356,42 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
     return r;
 }
 
-// Parts of x as raw bits (16-bit types in the low half).
+// Parts of x as raw bits (16-bit types in the low half).  BF16 and TF32
+// parts are taken by truncation: p_0 keeps the leading 8 (BF16) or 11 (TF32)
+// significant bits of x, and x - p_0 is exact in float32, so three BF16 parts
+// hold x exactly; FP16 parts are rounded (a format conversion is needed).
 template <int PR>
 __device__ __forceinline__ void split_parts(float x, uint32_t* part) {
     float r = x;
 #pragma unroll
     for (int j = 0; j < Prec<PR>::kParts; ++j) {
         if constexpr (PR == kPrecBF16) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(r);
-            part[j] = __bfloat16_as_ushort(h);
-            r -= __bfloat162float(h);
+            const uint32_t u = __float_as_uint(r);
+            part[j] = u >> 16;
+            r -= __uint_as_float(u & 0xFFFF0000u);
         } else if constexpr (PR == kPrecFP16) {
             const __half h = __float2half_rn(r);
             part[j] = __half_as_ushort(h);
             r -= __half2float(h);
         } else {
-            const uint32_t h = to_tf32(r);
-            part[j] = h;
-            r -= __uint_as_float(h);
+            const uint32_t u = __float_as_uint(r) & 0xFFFFE000u;
+            part[j] = u;
+            r -= __uint_as_float(u);
         }
     }
 }
 
-// Store row r (KD values) of a [rows x KD] split operand whose parts are
-// `part_bytes` apart.
-template <int PR, int KD>
-__device__ __forceinline__ void store_row_split(unsigned char* base, uint32_t part_bytes, int r, const float* v) {
+// Store columns c0 .. c0 + NC - 1 (values v[0 .. NC)) of row r of a
+// [rows x KD] split operand whose parts are `part_bytes` apart; c0 and NC are
+// multiples of 16 bytes' worth of elements.
+template <int PR, int KD, int NC>
+__device__ __forceinline__ void store_cols_split(unsigned char* base, uint32_t part_bytes, int r, int c0,
+                                                 const float* v) {
     constexpr int EB = Prec<PR>::kElem, T = 16 / EB, NP = Prec<PR>::kParts;
     constexpr uint32_t SBO = (KD / T) * 128;
-    const uint32_t row_off = (r >> 3) * SBO + (r & 7) * 16;
+    const uint32_t row_off = (r >> 3) * SBO + (r & 7) * 16 + (c0 / T) * 128;
 #pragma unroll
-    for (int g = 0; g < KD / T; ++g) {
+    for (int g = 0; g < NC / T; ++g) {
         uint32_t w[NP][4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -346,6 +415,48 @@ __device__ __forceinline__ void store_row_split(unsigned char* base, uint32_t pa
     }
 }
 
+// Write NC values (this thread's row, from column c0 of the operand) of a
+// split operand held in tensor memory: part j at column base + j * part_cols;
+// NC * eb / 4 is a multiple of 8 columns.  Warp-collective; the caller waits
+// (tmem_wait_st) before handing the operand to the MMA issuer.
+template <int PR, int NC>
+__device__ __forceinline__ void tmem_store_split(uint32_t lane_base, uint32_t part_cols, int c0, const float* v) {
+    constexpr int EB = Prec<PR>::kElem, NP = Prec<PR>::kParts;
+    constexpr int NW = NC * EB / 4;                 // 32-bit words per part
+    static_assert(NW % 8 == 0, "whole 8-column stores");
+    uint32_t w[NP][NW];
+#pragma unroll
+    for (int e = 0; e < NW; ++e) {
+        if constexpr (EB == 2) {
+            uint32_t lo[NP], hi[NP];
+            split_parts<PR>(v[2 * e], lo);
+            split_parts<PR>(v[2 * e + 1], hi);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) w[j][e] = lo[j] | (hi[j] << 16);
+        } else {
+            uint32_t pp[NP];
+            split_parts<PR>(v[e], pp);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) w[j][e] = pp[j];
+        }
+    }
+    const uint32_t col0 = static_cast<uint32_t>(c0 * EB / 4);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+#pragma unroll
+        for (int q = 0; q < NW; q += 16) {
+            if (NW - q >= 16) tmem_st16(lane_base + j * part_cols + col0 + q, &w[j][q]);
+            else tmem_st8(lane_base + j * part_cols + col0 + q, &w[j][q]);
+        }
+    }
+}
+
+// Store row r (KD values) of a [rows x KD] split operand.
+template <int PR, int KD>
+__device__ __forceinline__ void store_row_split(unsigned char* base, uint32_t part_bytes, int r, const float* v) {
+    store_cols_split<PR, KD, KD>(base, part_bytes, r, 0, v);
+}
+
 // 16 consecutive FP32 columns of this thread's lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     uint32_t r[16];
@@ -361,15 +472,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 8 consecutive FP32 columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 template <int N>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v) {
-    static_assert(N % 16 == 0, "multiple of 16 columns");
+    static_assert(N % 8 == 0, "multiple of 8 columns");
     if constexpr (N % 32 == 0) {
 #pragma unroll
         for (int c = 0; c < N; c += 32) tmem_ld32(taddr + c, v + c);
-    } else {
+    } else if constexpr (N % 16 == 0) {
 #pragma unroll
         for (int c = 0; c < N; c += 16) tmem_ld16(taddr + c, v + c);
+    } else {
+#pragma unroll
+        for (int c = 0; c < N; c += 8) tmem_ld8(taddr + c, v + c);
     }
 }
 
