@@ -839,27 +839,37 @@ def bench_chain(args, world, rank, local):
     poses = T["poses"].clone().requires_grad_(True)
     cfg = Config(n_bands=m["n_bands"])
     scenes = chain.make_view_scenes(V, T["c0"], T["radii"], T["light"], cfg)
+    views = chain.ViewBatch(V, M, T["c0"], T["radii"], T["light"], cfg)
     W = torch.randn((V, M, 3), device=dev)
     steps = max(3, min(args.steps, 20))
-    launches0 = None
-    times = []
-    with ClockSampler(local) as clk:
+
+    def run_steps(batched):
+        times, launches = [], 0
         for it in range(args.warmup + steps):
-            if it == args.warmup:
-                launches0 = lib.shs_launch_count()
+            l0 = lib.shs_launch_count()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             pp.grad = None
             poses.grad = None
             e0.record(stream)
-            B = chain.render_views(pp, poses, T, T["radii"], T["light"], T["albedo"], scenes)
+            if batched:
+                B = chain.render_views_batched(pp, poses, T, T["radii"], T["light"], T["albedo"], views)
+            else:
+                B = chain.render_views(pp, poses, T, T["radii"], T["light"], T["albedo"], scenes)
             (B * W).sum().backward()
             e1.record(stream)
             torch.cuda.synchronize()
             if it >= args.warmup:
                 times.append(e0.elapsed_time(e1))
+                launches += lib.shs_launch_count() - l0
+        return statistics.fmean(times), launches
+
+    # the step as one batched launch per pass (all views), and view by view
+    with ClockSampler(local) as clk:
+        step_ms, launches = run_steps(True)
+    per_view_ms, per_view_launches = run_steps(False)
     for sc in scenes:
         sc.close()
-    step_ms = statistics.fmean(times)
+    views.close()
     hbm = load_peaks().get("hbm_gbs")
     ach = chain_bytes / (fwd_ms * 1e-3) / 1e9
     cpu = None
@@ -880,12 +890,13 @@ def bench_chain(args, world, rank, local):
         config={"workload": f"mesh deformation {V} views x {M} vertices, {N} spheres, {D} parameters, n_bands=4",
                 "views": V, "vertices": M, "spheres": N, "params": D, "l2_flush_between_chain_launches": True},
         chain_kernels={"fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "bytes_per_launch": chain_bytes},
+        step={"batched_views_ms": step_ms, "launches_per_step": launches / steps,
+              "per_view_calls_ms": per_view_ms, "per_view_launches_per_step": per_view_launches / steps},
         roofline={"bound": "hbm", "kernel": "chain_forward_kernel (vertices)", "achieved": ach, "peak": hbm,
                   "unit": "GB/s", "frac": ach / hbm if hbm else None, "traffic": None,
                   "backward": {"achieved": chain_bytes / (bwd_ms * 1e-3) / 1e9,
                                "frac": chain_bytes / (bwd_ms * 1e-3) / 1e9 / hbm if hbm else None}},
-        gpu_launches=(lib.shs_launch_count() - launches0) if launches0 is not None else None,
-        clocks=clk.summary(), cpu_baseline=cpu)
+        gpu_launches=int(launches), clocks=clk.summary(), cpu_baseline=cpu)
 
 
 def bench_envmap(args, world, rank, local):

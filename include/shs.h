@@ -264,6 +264,9 @@ typedef struct {
     float* d_radii;
     float* d_points;
     float* d_normals;
+    const float* d_radiance;/* [P,3]; with target NULL: adjoint of sum(d_radiance  */
+                            /* * B) (as shs_shade_backward); radiance may then be  */
+                            /* NULL, which skips the forward (saved must hold it)  */
 } shs_request;
 
 /* A batch context holds the device work counters of one in-flight batch call;
@@ -271,7 +274,9 @@ typedef struct {
 shs_status shs_batch_create(shs_batch_t* out);
 shs_status shs_batch_destroy(shs_batch_t batch);
 
-/* Enqueues the batch on `stream`.  Requests with a target need `saved`.  Two
+/* Enqueues the batch on `stream`.  Requests with a target or d_radiance need
+ * `saved`; a request with radiance NULL and d_radiance set runs only the
+ * adjoint, from the state an earlier call saved.  Two
  * requests may not share a scene (its accumulator is per call).  Scene-level
  * sums are accumulated with atomics (run-to-run rounding differences).
  * Returns SHS_ERR_INVALID_ARG for more than 32 requests. */
@@ -361,6 +366,24 @@ size_t shs_chain_workspace_bytes(int64_t n_rows, int32_t n_params);
 shs_status shs_chain_backward(const float* base, const float* basis, int64_t n_rows, int32_t n_params,
                               const float* p, const float* pose, int32_t direction, const float* d_x,
                               float* d_p, float* d_pose, void* workspace, size_t workspace_bytes, void* stream);
+
+/* The same chain for n_views rigid poses at once (the views of one mesh in a
+ * multi-view optimisation): the deformation x_rest is computed once per row,
+ * then each view's pose applied.  1 <= n_views <= SHS_CHAIN_MAX_VIEWS.
+ *   poses [n_views][6]; x [n_views][n_rows][3] (view-major).
+ * The adjoint takes d_x [n_views][n_rows][3] and writes d_p [n_params] (the
+ * sum over views) and d_poses [n_views][6]; its workspace is
+ * shs_chain_views_workspace_bytes(n_rows, n_params, n_views) bytes.  With
+ * n_views = 1 these equal shs_chain_forward / shs_chain_backward. */
+#define SHS_CHAIN_MAX_VIEWS 32
+size_t shs_chain_views_workspace_bytes(int64_t n_rows, int32_t n_params, int32_t n_views);
+shs_status shs_chain_forward_views(const float* base, const float* basis, int64_t n_rows, int32_t n_params,
+                                   const float* p, const float* poses, int32_t n_views, int32_t direction,
+                                   float* x_rest, float* x, void* stream);
+shs_status shs_chain_backward_views(const float* base, const float* basis, int64_t n_rows, int32_t n_params,
+                                    const float* p, const float* poses, int32_t n_views, int32_t direction,
+                                    const float* d_x, float* d_p, float* d_poses, void* workspace,
+                                    size_t workspace_bytes, void* stream);
 
 /* Diagnostic: FP32 FMA throughput probe.  Launches `blocks` blocks of 256
  * threads; each thread runs 8 independent fused multiply-add chains of

@@ -38,7 +38,8 @@ class ShsRequest(ctypes.Structure):
     """Mirror of ``shs_request`` (one job's request in a batch call)."""
     _fields_ = [("scene", c_void_p), ("n_points", c_int64)] + [
         (n, c_void_p) for n in ("points", "normals", "albedo", "radiance", "saved", "target", "loss",
-                                "d_light", "d_albedo", "d_centers", "d_radii", "d_points", "d_normals")]
+                                "d_light", "d_albedo", "d_centers", "d_radii", "d_points", "d_normals",
+                                "d_radiance")]
 
 
 class ShsError(RuntimeError):
@@ -82,6 +83,11 @@ _SIGS = {
     "shs_chain_forward": (c_int32, [c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int32, c_void_p,
                                     c_void_p, c_void_p]),
     "shs_chain_workspace_bytes": (c_size_t, [c_int64, c_int32]),
+    "shs_chain_views_workspace_bytes": (c_size_t, [c_int64, c_int32, c_int32]),
+    "shs_chain_forward_views": (c_int32, [c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int32, c_int32,
+                                          c_void_p, c_void_p, c_void_p]),
+    "shs_chain_backward_views": (c_int32, [c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int32,
+                                           c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "shs_chain_backward": (c_int32, [c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int32, c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "shs_fp32_fma_probe": (c_int32, [c_int32, c_int64, c_void_p, c_void_p]),

@@ -882,9 +882,13 @@ shs_status shs_shade_batch(shs_batch_t batch, const shs_request* reqs, int32_t n
         if (!r.scene) return fail(SHS_ERR_INVALID_ARG, "request %d: scene is NULL", i);
         if (!table_ready(r.scene)) return fail(SHS_ERR_INVALID_ARG, "request %d: exp_mode 2 without a table", i);
         if (r.n_points < 0) return fail(SHS_ERR_INVALID_ARG, "request %d: n_points < 0", i);
-        if (r.n_points > 0 && (!r.points || !r.normals || !r.albedo || !r.radiance))
+        const bool bwd_only = !r.radiance && r.d_radiance && !r.target;
+        if (r.n_points > 0 && (!r.points || !r.normals || !r.albedo || (!r.radiance && !bwd_only)))
             return fail(SHS_ERR_INVALID_ARG, "request %d: NULL input/output array", i);
-        if (r.target && !r.saved) return fail(SHS_ERR_INVALID_ARG, "request %d: backward needs saved", i);
+        if (r.target && r.d_radiance)
+            return fail(SHS_ERR_INVALID_ARG, "request %d: target and d_radiance are exclusive", i);
+        if ((r.target || r.d_radiance) && !r.saved)
+            return fail(SHS_ERR_INVALID_ARG, "request %d: backward needs saved", i);
         if (r.saved && (reinterpret_cast<uintptr_t>(r.saved) & 15u))
             return fail(SHS_ERR_INVALID_ARG, "request %d: saved not 16-byte aligned", i);
         for (int j = 0; j < i; ++j)
@@ -901,8 +905,9 @@ shs_status shs_shade_batch(shs_batch_t batch, const shs_request* reqs, int32_t n
         fb.queue = batch->queues + (nb - 1);
         for (int i = 0; i < n_reqs; ++i) {
             const shs_request& r = reqs[i];
-            if (r.scene->cfg.n_bands != nb || r.n_points == 0) continue;
+            if (r.scene->cfg.n_bands != nb || r.n_points == 0 || !r.radiance) continue;
             shs::FwdArgs& a = fb.r[fb.n];
+            a = shs::FwdArgs{};
             a.sc = view_of(r.scene);
             a.n_points = r.n_points;
             a.points = r.points;
@@ -926,7 +931,7 @@ shs_status shs_shade_batch(shs_batch_t batch, const shs_request* reqs, int32_t n
         for (int i = 0; i < n_reqs && e == cudaSuccess; ++i) {
             const shs_request& r = reqs[i];
             shs_scene_s* sc = r.scene;
-            if (sc->cfg.n_bands != nb || !r.target) continue;
+            if (sc->cfg.n_bands != nb || (!r.target && !r.d_radiance)) continue;
             if (r.n_points == 0) {
                 if (r.d_light) e = cudaMemsetAsync(r.d_light, 0, sizeof(float) * 3 * sc->K, s);
                 if (e == cudaSuccess && r.d_centers && sc->n_spheres) e = cudaMemsetAsync(r.d_centers, 0, sizeof(float) * 3 * sc->n_spheres, s);
@@ -948,7 +953,8 @@ shs_status shs_shade_batch(shs_batch_t batch, const shs_request* reqs, int32_t n
             a.saved_k = sk;
             a.radiance = r.radiance;
             a.target = r.target;
-            a.loss = r.loss;
+            a.d_radiance = r.d_radiance;
+            a.loss = r.target ? r.loss : nullptr;
             a.d_light = r.d_light;
             a.d_albedo = r.d_albedo;
             a.d_centers = sc->n_spheres ? r.d_centers : nullptr;

@@ -1,10 +1,11 @@
 // Scene chain above the shading path (Sec. 3.3.1, Sec. 3.5): per array of M
-// rows (vertices, normals or sphere centres) a linear deformation model and a
-// rigid pose,
-//   x_rest[m] = base[m] + basis[m] p   (basis[m]: 3 x D, row-major [M][3][D])
-//   x[m]      = R(w) x_rest[m] + t     (t dropped for directions)
-// with R(w) = exp([w]x) (Rodrigues' formula), and the adjoint to p and to the
-// pose (w, t).
+// rows (vertices, normals or sphere centres) a linear deformation model and
+// the rigid pose of each of V views,
+//   x_rest[m]  = base[m] + basis[m] p        (basis[m]: 3 x D, row-major [M][3][D])
+//   x[v][m]    = R(w_v) x_rest[m] + t_v      (t dropped for directions)
+// with R(w) = exp([w]x) (Rodrigues' formula), and the adjoint to p and to
+// every view's pose (w_v, t_v).  The deformation is computed once per row for
+// all views; lane v of the row's warp applies view v.
 //
 // The basis is the only large operand (M * 3 * D floats), read once per pass:
 // one warp per row, lanes striding the D parameters, so each row's 3 D floats
@@ -26,7 +27,8 @@ constexpr int kChainWarps = 8;                  // 256-thread blocks
 constexpr int kChainThreads = 32 * kChainWarps;
 constexpr int kChainMaxD = SHS_CHAIN_MAX_PARAMS;
 constexpr int kChainMaxBlocks = 152 * 4;
-constexpr int kChainExtra = 12;                 // dL/dR (9, row-major) and dL/dt (3)
+constexpr int kChainExtra = 12;                 // per view: dL/dR (9, row-major) and dL/dt (3)
+constexpr int kChainMaxViews = SHS_CHAIN_MAX_VIEWS;
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -78,20 +80,26 @@ __device__ __forceinline__ void rotation(const float* pose, float* R) {
 constexpr int kChainRowsPerStep = SHS_CHAIN_ROWS;
 
 // PL: parameters per lane (D <= 32 PL).  Loads beyond D or M read nothing and
-// count as zero.
+// count as zero.  poses: [V][6]; x: [V][M][3].
 template <int PL>
 __global__ void SHS_CHAIN_BOUNDS chain_forward_kernel(const float* base, const float* basis, int64_t M,
-                                                                      int D, const float* p, const float* pose,
-                                                                      int direction, float* x_rest, float* x) {
+                                                      int D, const float* p, const float* poses, int V,
+                                                      int direction, float* x_rest, float* x) {
     constexpr int RW = kChainRowsPerStep;
     __shared__ float s_p[32 * PL];
+    __shared__ float s_rt[kChainMaxViews][12];      // R (9) and t (3) per view
     for (int d = threadIdx.x; d < 32 * PL; d += kChainThreads) s_p[d] = d < D ? __ldg(p + d) : 0.f;
+    if (threadIdx.x < V) {
+        const float* pose = poses + 6 * threadIdx.x;
+        rotation(pose, s_rt[threadIdx.x]);
+        for (int c = 0; c < 3; ++c) s_rt[threadIdx.x][9 + c] = direction ? 0.f : __ldg(pose + 3 + c);
+    }
     __syncthreads();
-    float R[9];
-    rotation(pose, R);
-    const float tx = direction ? 0.f : __ldg(pose + 3), ty = direction ? 0.f : __ldg(pose + 4),
-                tz = direction ? 0.f : __ldg(pose + 5);
     const int lane = threadIdx.x & 31;
+    // lane v applies view v (V <= 32)
+    float R[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) R[i] = lane < V ? s_rt[lane][i] : 0.f;
     const int64_t step = static_cast<int64_t>(gridDim.x) * kChainWarps * RW;
     for (int64_t m0 = (static_cast<int64_t>(blockIdx.x) * kChainWarps + (threadIdx.x >> 5)) * RW; m0 < M;
          m0 += step) {
@@ -119,41 +127,48 @@ __global__ void SHS_CHAIN_BOUNDS chain_forward_kernel(const float* base, const f
                 acc[r][c] = warp_sum(t);
             }
         }
-        if (lane < RW) {
-            // lane r writes row m0 + r (register arrays indexed by a compile-time r)
 #pragma unroll
-            for (int r = 0; r < RW; ++r) {
-                const int64_t m = m0 + r;
-                if (lane != r || m >= M) continue;
-                const float a0 = acc[r][0] + __ldg(base + 3 * m), a1 = acc[r][1] + __ldg(base + 3 * m + 1),
-                            a2 = acc[r][2] + __ldg(base + 3 * m + 2);
-                if (x_rest) {
-                    x_rest[3 * m] = a0;
-                    x_rest[3 * m + 1] = a1;
-                    x_rest[3 * m + 2] = a2;
-                }
-                x[3 * m] = fmaf(R[0], a0, fmaf(R[1], a1, fmaf(R[2], a2, tx)));
-                x[3 * m + 1] = fmaf(R[3], a0, fmaf(R[4], a1, fmaf(R[5], a2, ty)));
-                x[3 * m + 2] = fmaf(R[6], a0, fmaf(R[7], a1, fmaf(R[8], a2, tz)));
+        for (int r = 0; r < RW; ++r) {
+            const int64_t m = m0 + r;
+            if (m >= M) continue;
+            const float a0 = acc[r][0] + __ldg(base + 3 * m), a1 = acc[r][1] + __ldg(base + 3 * m + 1),
+                        a2 = acc[r][2] + __ldg(base + 3 * m + 2);
+            if (x_rest && lane == 0) {
+                x_rest[3 * m] = a0;
+                x_rest[3 * m + 1] = a1;
+                x_rest[3 * m + 2] = a2;
+            }
+            if (lane < V) {
+                float* xo = x + (static_cast<int64_t>(lane) * M + m) * 3;
+                xo[0] = fmaf(R[0], a0, fmaf(R[1], a1, fmaf(R[2], a2, R[9])));
+                xo[1] = fmaf(R[3], a0, fmaf(R[4], a1, fmaf(R[5], a2, R[10])));
+                xo[2] = fmaf(R[6], a0, fmaf(R[7], a1, fmaf(R[8], a2, R[11])));
             }
         }
     }
 }
 
-// Partial sums of one block: [0, D) dL/dp, then dL/dR (9), dL/dt (3).
+// Partial sums of one block: [0, D) dL/dp, then per view dL/dR (9), dL/dt (3).
+// d_x: [V][M][3].  Lane v takes view v's gradient of the row: it adds
+// R_v^T g_v to the rest-frame gradient (summed over the warp's lanes) and
+// accumulates view v's dL/dR and dL/dt.
 template <int PL>
 __global__ void SHS_CHAIN_BOUNDS chain_backward_kernel(const float* base, const float* basis, int64_t M,
-                                                                       int D, const float* p, const float* pose,
-                                                                       int direction, const float* g, float* partials) {
+                                                       int D, const float* p, const float* poses, int V,
+                                                       int direction, const float* g, float* partials) {
     constexpr int RW = kChainRowsPerStep;
     __shared__ float s_p[32 * PL];
     __shared__ float s_dp[kChainWarps][32 * PL];
-    __shared__ float s_ex[kChainWarps][kChainExtra];
+    __shared__ float s_ex[kChainWarps][kChainMaxViews][kChainExtra];
+    __shared__ float s_r[kChainMaxViews][9];
     for (int d = threadIdx.x; d < 32 * PL; d += kChainThreads) s_p[d] = d < D ? __ldg(p + d) : 0.f;
+    if (threadIdx.x < V) rotation(poses + 6 * threadIdx.x, s_r[threadIdx.x]);
     __syncthreads();
-    float R[9];
-    rotation(pose, R);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool view = lane < V;
+    float R[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) R[i] = view ? s_r[lane][i] : 0.f;
     float dp[PL];
 #pragma unroll
     for (int j = 0; j < PL; ++j) dp[j] = 0.f;
@@ -168,7 +183,7 @@ __global__ void SHS_CHAIN_BOUNDS chain_backward_kernel(const float* base, const 
             const int64_t m = m0 + r;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                gg[r][c] = m < M ? __ldg(g + 3 * m + c) : 0.f;
+                gg[r][c] = (m < M && view) ? __ldg(g + (static_cast<int64_t>(lane) * M + m) * 3 + c) : 0.f;
 #pragma unroll
                 for (int j = 0; j < PL; ++j) {
                     const int d = lane + 32 * j;
@@ -178,10 +193,10 @@ __global__ void SHS_CHAIN_BOUNDS chain_backward_kernel(const float* base, const 
         }
 #pragma unroll
         for (int r = 0; r < RW; ++r) {
-            // R^T g: the gradient in the rest frame
-            const float r0 = fmaf(R[0], gg[r][0], fmaf(R[3], gg[r][1], R[6] * gg[r][2]));
-            const float r1 = fmaf(R[1], gg[r][0], fmaf(R[4], gg[r][1], R[7] * gg[r][2]));
-            const float r2 = fmaf(R[2], gg[r][0], fmaf(R[5], gg[r][1], R[8] * gg[r][2]));
+            // sum over views of R_v^T g_v: the gradient in the rest frame
+            const float r0 = warp_sum(fmaf(R[0], gg[r][0], fmaf(R[3], gg[r][1], R[6] * gg[r][2])));
+            const float r1 = warp_sum(fmaf(R[1], gg[r][0], fmaf(R[4], gg[r][1], R[7] * gg[r][2])));
+            const float r2 = warp_sum(fmaf(R[2], gg[r][0], fmaf(R[5], gg[r][1], R[8] * gg[r][2])));
             float xr[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -207,26 +222,31 @@ __global__ void SHS_CHAIN_BOUNDS chain_backward_kernel(const float* base, const 
     }
 #pragma unroll
     for (int j = 0; j < PL; ++j) s_dp[warp][lane + 32 * j] = dp[j];
-    if (lane == 0) {
+    if (view) {
 #pragma unroll
-        for (int i = 0; i < kChainExtra; ++i) s_ex[warp][i] = ex[i];
+        for (int i = 0; i < kChainExtra; ++i) s_ex[warp][lane][i] = ex[i];
     }
     __syncthreads();
-    const int E = D + kChainExtra;
+    const int E = D + kChainExtra * V;
     for (int i = threadIdx.x; i < E; i += kChainThreads) {
         float t = 0.f;
-        for (int w = 0; w < kChainWarps; ++w) t += i < D ? s_dp[w][i] : s_ex[w][i - D];
+        if (i < D) {
+            for (int w = 0; w < kChainWarps; ++w) t += s_dp[w][i];
+        } else {
+            const int v = (i - D) / kChainExtra, k = (i - D) % kChainExtra;
+            for (int w = 0; w < kChainWarps; ++w) t += s_ex[w][v][k];
+        }
         partials[static_cast<int64_t>(blockIdx.x) * E + i] = t;
     }
 }
 
-// Fixed-order sum of the blocks' partial rows; thread 0 then maps dL/dR to
-// dL/dw in double precision:
+// Fixed-order sum of the blocks' partial rows; thread v then maps view v's
+// dL/dR to dL/dw_v in double precision:
 // dR/dw_a = A K_a + B (K_a K + K K_a) + (A'/th) w_a K + (B'/th) w_a K^2.
-__global__ void __launch_bounds__(kChainThreads) chain_reduce_kernel(const float* partials, int nblk, int D,
-                                                                     const float* pose, float* d_p, float* d_pose) {
-    __shared__ float s_ex[kChainExtra];
-    const int E = D + kChainExtra;
+__global__ void __launch_bounds__(kChainThreads) chain_reduce_kernel(const float* partials, int nblk, int D, int V,
+                                                                     const float* poses, float* d_p, float* d_poses) {
+    __shared__ float s_ex[kChainMaxViews * kChainExtra];
+    const int E = D + kChainExtra * V;
     for (int i = threadIdx.x; i < E; i += kChainThreads) {
         float t = 0.f;
         for (int b = 0; b < nblk; ++b) t += partials[static_cast<int64_t>(b) * E + i];
@@ -234,7 +254,11 @@ __global__ void __launch_bounds__(kChainThreads) chain_reduce_kernel(const float
         else s_ex[i - D] = t;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
+    const int v = threadIdx.x;
+    if (v >= V) return;
+    const float* ex = s_ex + kChainExtra * v;
+    const float* pose = poses + 6 * v;
+    float* d_pose = d_poses + 6 * v;
     const double w[3] = {pose[0], pose[1], pose[2]};
     const double t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
     double A, B, dA, dB;
@@ -268,11 +292,11 @@ __global__ void __launch_bounds__(kChainThreads) chain_reduce_kernel(const float
                 double kk = 0.0;
                 for (int q = 0; q < 3; ++q) kk += Ka[3 * r + q] * K[3 * q + c] + K[3 * r + q] * Ka[3 * q + c];
                 const double G = A * Ka[3 * r + c] + B * kk + dA * w[a] * K[3 * r + c] + dB * w[a] * K2[3 * r + c];
-                acc += G * s_ex[3 * r + c];
+                acc += G * ex[3 * r + c];
             }
         d_pose[a] = static_cast<float>(acc);
     }
-    for (int a = 0; a < 3; ++a) d_pose[3 + a] = s_ex[9 + a];
+    for (int a = 0; a < 3; ++a) d_pose[3 + a] = ex[9 + a];
 }
 
 int chain_grid(int64_t M) {
@@ -309,88 +333,127 @@ int clamp_grid(int64_t need, int resident) {
 
 template <int PL> struct Fwd {
     static void go(int64_t need, cudaStream_t s, const float* base, const float* basis, int64_t M, int D,
-                   const float* p, const float* pose, int dir, float* xr, float* x) {
+                   const float* p, const float* poses, int V, int dir, float* xr, float* x) {
         static const int resident = resident_blocks(chain_forward_kernel<PL>);
-        chain_forward_kernel<PL><<<clamp_grid(need, resident), kChainThreads, 0, s>>>(base, basis, M, D, p, pose, dir,
-                                                                                       xr, x);
+        chain_forward_kernel<PL><<<clamp_grid(need, resident), kChainThreads, 0, s>>>(base, basis, M, D, p, poses, V,
+                                                                                       dir, xr, x);
     }
 };
 template <int PL> struct Bwd {
     static void go(int64_t need, cudaStream_t s, const float* base, const float* basis, int64_t M, int D,
-                   const float* p, const float* pose, int dir, const float* g, float* partials, int* nblk) {
+                   const float* p, const float* poses, int V, int dir, const float* g, float* partials, int* nblk) {
         static const int resident = resident_blocks(chain_backward_kernel<PL>);
         *nblk = clamp_grid(need < kChainMaxBlocks ? need : kChainMaxBlocks, resident);
-        chain_backward_kernel<PL><<<*nblk, kChainThreads, 0, s>>>(base, basis, M, D, p, pose, dir, g, partials);
+        chain_backward_kernel<PL><<<*nblk, kChainThreads, 0, s>>>(base, basis, M, D, p, poses, V, dir, g, partials);
     }
 };
 
 shs_status check_chain(const float* base, const float* basis, int64_t M, int32_t D, const float* p,
-                       const float* pose) {
+                       const float* poses, int32_t V, int32_t direction) {
     if (M < 0) return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "M < 0"));
     if (D < 1 || D > kChainMaxD)
         return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "D %d not in 1..%d", D, kChainMaxD));
-    if (M > (int64_t(1) << 40) / (3 * static_cast<int64_t>(D)))
+    if (V < 1 || V > kChainMaxViews)
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "n_views %d not in 1..%d", V,
+                                                         kChainMaxViews));
+    if (M > (int64_t(1) << 40) / (3 * static_cast<int64_t>(D) * V))
         return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "M x 3 x D too large"));
-    if (!p || !pose) return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL p or pose"));
+    if (!p || !poses) return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL p or pose"));
     if (M > 0 && (!base || !basis))
         return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL base or basis"));
+    if (direction != 0 && direction != 1)
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "direction must be 0 or 1"));
     return SHS_OK;
+}
+
+size_t views_workspace_bytes(int64_t n_rows, int32_t n_params, int32_t n_views) {
+    if (n_rows < 0 || n_params < 1 || n_params > kChainMaxD || n_views < 1 || n_views > kChainMaxViews) return 0;
+    return sizeof(float) * static_cast<size_t>(chain_grid(n_rows)) * (n_params + kChainExtra * n_views);
+}
+
+shs_status forward_views(const float* base, const float* basis, int64_t n_rows, int32_t n_params, const float* p,
+                         const float* poses, int32_t n_views, int32_t direction, float* x_rest, float* x,
+                         void* stream) {
+    shs_status st = check_chain(base, basis, n_rows, n_params, p, poses, n_views, direction);
+    if (st != SHS_OK) return st;
+    if (n_rows == 0) return SHS_OK;
+    if (!x) return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL x"));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t per = static_cast<int64_t>(kChainWarps) * kChainRowsPerStep;
+    by_lanes<Fwd>(n_params, (n_rows + per - 1) / per, s, base, basis, n_rows, n_params, p, poses, n_views, direction,
+                  x_rest, x);
+    shs::count_launch();
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SHS_OK : static_cast<shs_status>(shs::report_cuda(e, "chain forward"));
+}
+
+shs_status backward_views(const float* base, const float* basis, int64_t n_rows, int32_t n_params, const float* p,
+                          const float* poses, int32_t n_views, int32_t direction, const float* d_x, float* d_p,
+                          float* d_poses, void* workspace, size_t workspace_bytes, void* stream) {
+    shs_status st = check_chain(base, basis, n_rows, n_params, p, poses, n_views, direction);
+    if (st != SHS_OK) return st;
+    if (!d_p || !d_poses || !workspace)
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL d_p, d_pose or workspace"));
+    if (n_rows > 0 && !d_x) return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL d_x"));
+    if (reinterpret_cast<uintptr_t>(workspace) & 15u)
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "workspace not 16-byte aligned"));
+    const size_t need = views_workspace_bytes(n_rows, n_params, n_views);
+    if (workspace_bytes < need)
+        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "workspace of %zu bytes < %zu needed",
+                                                         workspace_bytes, need));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float* partials = static_cast<float*>(workspace);
+    int nblk = 0;
+    if (n_rows > 0) {
+        const int64_t per = static_cast<int64_t>(kChainWarps) * kChainRowsPerStep;
+        by_lanes<Bwd>(n_params, (n_rows + per - 1) / per, s, base, basis, n_rows, n_params, p, poses, n_views,
+                      direction, d_x, partials, &nblk);
+        shs::count_launch();
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return static_cast<shs_status>(shs::report_cuda(e, "chain backward"));
+    }
+    chain_reduce_kernel<<<1, kChainThreads, 0, s>>>(partials, nblk, n_params, n_views, poses, d_p, d_poses);
+    shs::count_launch();
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SHS_OK : static_cast<shs_status>(shs::report_cuda(e, "chain reduce"));
 }
 
 }  // namespace
 
 extern "C" size_t shs_chain_workspace_bytes(int64_t n_rows, int32_t n_params) {
-    if (n_rows < 0 || n_params < 1 || n_params > kChainMaxD) return 0;
-    return sizeof(float) * static_cast<size_t>(chain_grid(n_rows)) * (n_params + kChainExtra);
+    return views_workspace_bytes(n_rows, n_params, 1);
+}
+
+extern "C" size_t shs_chain_views_workspace_bytes(int64_t n_rows, int32_t n_params, int32_t n_views) {
+    return views_workspace_bytes(n_rows, n_params, n_views);
 }
 
 extern "C" shs_status shs_chain_forward(const float* base, const float* basis, int64_t n_rows, int32_t n_params,
                                         const float* p, const float* pose, int32_t direction, float* x_rest,
                                         float* x, void* stream) {
-    shs_status st = check_chain(base, basis, n_rows, n_params, p, pose);
-    if (st != SHS_OK) return st;
-    if (direction != 0 && direction != 1)
-        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "direction must be 0 or 1"));
-    if (n_rows == 0) return SHS_OK;
-    if (!x) return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL x"));
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int64_t per = static_cast<int64_t>(kChainWarps) * kChainRowsPerStep;
-    by_lanes<Fwd>(n_params, (n_rows + per - 1) / per, s, base, basis, n_rows, n_params, p, pose, direction, x_rest, x);
-    shs::count_launch();
-    const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? SHS_OK : static_cast<shs_status>(shs::report_cuda(e, "chain forward"));
+    return forward_views(base, basis, n_rows, n_params, p, pose, 1, direction, x_rest, x, stream);
+}
+
+extern "C" shs_status shs_chain_forward_views(const float* base, const float* basis, int64_t n_rows,
+                                              int32_t n_params, const float* p, const float* poses,
+                                              int32_t n_views, int32_t direction, float* x_rest, float* x,
+                                              void* stream) {
+    return forward_views(base, basis, n_rows, n_params, p, poses, n_views, direction, x_rest, x, stream);
 }
 
 extern "C" shs_status shs_chain_backward(const float* base, const float* basis, int64_t n_rows, int32_t n_params,
                                          const float* p, const float* pose, int32_t direction, const float* d_x,
                                          float* d_p, float* d_pose, void* workspace, size_t workspace_bytes,
                                          void* stream) {
-    shs_status st = check_chain(base, basis, n_rows, n_params, p, pose);
-    if (st != SHS_OK) return st;
-    if (direction != 0 && direction != 1)
-        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "direction must be 0 or 1"));
-    if (!d_p || !d_pose || !workspace)
-        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL d_p, d_pose or workspace"));
-    if (n_rows > 0 && !d_x) return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "NULL d_x"));
-    if (reinterpret_cast<uintptr_t>(workspace) & 15u)
-        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "workspace not 16-byte aligned"));
-    if (workspace_bytes < shs_chain_workspace_bytes(n_rows, n_params))
-        return static_cast<shs_status>(shs::report_error(SHS_ERR_INVALID_ARG, "workspace of %zu bytes < %zu needed",
-                                                         workspace_bytes,
-                                                         shs_chain_workspace_bytes(n_rows, n_params)));
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    float* partials = static_cast<float*>(workspace);
-    int nblk = 0;
-    if (n_rows > 0) {
-        const int64_t per = static_cast<int64_t>(kChainWarps) * kChainRowsPerStep;
-        by_lanes<Bwd>(n_params, (n_rows + per - 1) / per, s, base, basis, n_rows, n_params, p, pose, direction, d_x,
-                      partials, &nblk);
-        shs::count_launch();
-        const cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return static_cast<shs_status>(shs::report_cuda(e, "chain backward"));
-    }
-    chain_reduce_kernel<<<1, kChainThreads, 0, s>>>(partials, nblk, n_params, pose, d_p, d_pose);
-    shs::count_launch();
-    const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? SHS_OK : static_cast<shs_status>(shs::report_cuda(e, "chain reduce"));
+    return backward_views(base, basis, n_rows, n_params, p, pose, 1, direction, d_x, d_p, d_pose, workspace,
+                          workspace_bytes, stream);
+}
+
+extern "C" shs_status shs_chain_backward_views(const float* base, const float* basis, int64_t n_rows,
+                                               int32_t n_params, const float* p, const float* poses,
+                                               int32_t n_views, int32_t direction, const float* d_x, float* d_p,
+                                               float* d_poses, void* workspace, size_t workspace_bytes,
+                                               void* stream) {
+    return backward_views(base, basis, n_rows, n_params, p, poses, n_views, direction, d_x, d_p, d_poses, workspace,
+                          workspace_bytes, stream);
 }

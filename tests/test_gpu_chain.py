@@ -66,7 +66,10 @@ def _view_grad(args):
     return dp, adp, np.concatenate([dw, dt]), np.concatenate([adw, adt])
 
 
-def _gpu(m, p0, poses0, wts, cfg_kw):
+def _gpu(m, p0, poses0, wts, cfg_kw, batched=False):
+    """Gradients to p and the poses through the library: one chain and one
+    shading call per view, or (batched) all views in one chain launch per
+    array and one shading launch per pass."""
     import torch
     from paper_2104_00359_gb300 import Config, chain
     dev = torch.device("cuda:0")
@@ -76,9 +79,18 @@ def _gpu(m, p0, poses0, wts, cfg_kw):
     cfg = Config(n_bands=m["n_bands"], **cfg_kw)
     c0 = chain.affine_deform(T["c0"], T["A_c"], p.detach())
     scenes = chain.make_view_scenes(poses.shape[0], c0, T["radii"], T["light"], cfg)
-    B = chain.render_views(p, poses, T, T["radii"], T["light"], T["albedo"], scenes)
     W = torch.from_numpy(wts.astype(np.float32)).to(dev)
-    (B * W).sum().backward()
+    if batched:
+        views = chain.ViewBatch(poses.shape[0], T["v0"].shape[0], c0, T["radii"], T["light"], cfg)
+        B = chain.render_views_batched(p, poses, T, T["radii"], T["light"], T["albedo"], views)
+        (B * W).sum().backward()
+        torch.cuda.synchronize()
+        for sc in views.scenes:
+            assert sc.device_status() == 0
+        views.close()
+    else:
+        B = chain.render_views(p, poses, T, T["radii"], T["light"], T["albedo"], scenes)
+        (B * W).sum().backward()
     # per-point squaring counts of every view, for the oracle
     ks = []
     with torch.no_grad():
@@ -103,7 +115,8 @@ def _check(got, ref, aref, name):
     assert err.max() <= TOL, f"{name}: {err.max():.3e}"
 
 
-def test_chain_reduced_against_finite_differences():
+@pytest.mark.parametrize("batched", [False, True])
+def test_chain_reduced_against_finite_differences(batched):
     m = S.mesh_deformation_scene(seed=5, n_theta=30, n_phi=20, n_spheres=30, n_params=8, n_views=2)
     rng = np.random.default_rng(6)
     p0 = rng.normal(0, 0.5, 8)
@@ -136,7 +149,7 @@ def test_chain_reduced_against_finite_differences():
             fd = (loss(p0, poses0 + e) - loss(p0, poses0 - e)) / (2 * h)
             assert abs(fd - dpose[i, d]) <= 1e-6 * max(1.0, abs(fd)), (i, d, fd, dpose[i, d])
     # the CUDA path against the reference
-    gp, gpose, _ = _gpu(m, p0, poses0, wts, dict(fixed_k=3))
+    gp, gpose, _ = _gpu(m, p0, poses0, wts, dict(fixed_k=3), batched=batched)
     _check(gp, dp, sum(x[1] for x in parts), "d_p")
     _check(gpose, dpose, np.stack([x[3] for x in parts]), "d_pose")
 
@@ -153,6 +166,7 @@ def test_chain_full_size_16_views():
     pool = ctx.Pool(processes=max(1, min(16, os.cpu_count() or 1)))
     try:
         gp, gpose, ks = _gpu(m, p0, poses0, wts, {})
+        gpb, gposeb, _ = _gpu(m, p0, poses0, wts, {}, batched=True)
         cfg = O.Config(n_bands=4)
         chunks = np.array_split(np.arange(M), 4)
         tasks = [(m, p0, poses0[i], wts[i], ks[i], c, cfg) for i in range(V) for c in chunks]
@@ -166,3 +180,5 @@ def test_chain_full_size_16_views():
     adpose = np.stack([sum(parts[i * 4 + c][3] for c in range(4)) for i in range(V)])
     _check(gp, dp, adp, "d_p")
     _check(gpose, dpose, adpose, "d_pose")
+    _check(gpb, dp, adp, "d_p (batched views)")
+    _check(gposeb, dpose, adpose, "d_pose (batched views)")

@@ -108,3 +108,45 @@ def test_autograd_function_matches_oracle():
     ref = C.deform_pose_backward(base, basis, p, pose, g)
     assert _sum_err(tp.grad.cpu().numpy(), ref["d_p"], ref["abs_d_p"]) <= 1e-4
     assert _sum_err(tq.grad.cpu().numpy(), ref["d_pose"], ref["abs_d_pose"]) <= 1e-4
+
+
+@pytest.mark.parametrize("M,D,V", [(1, 3, 1), (333, 17, 5), (50000, 60, 16), (2000, 100, 32)])
+@pytest.mark.parametrize("direction", [False, True])
+def test_chain_views_match_oracle_per_view(M, D, V, direction):
+    """shs_chain_forward_views / shs_chain_backward_views: every view against
+    the oracle's single-pose chain; d_p is the sum over views of the oracle's,
+    d_poses[v] view v's."""
+    import torch
+    from paper_2104_00359_gb300 import _lib
+    from paper_2104_00359_gb300._lib import check, ptr
+    rng = np.random.default_rng(M + 7 * V)
+    base, basis, p, _, _ = _case(M, D, 0.0, seed=M + D + V)
+    poses = np.concatenate([rng.normal(0.0, 0.8, (V, 3)), rng.normal(0.0, 0.2, (V, 3))], 1).astype(np.float32)
+    g = rng.normal(size=(V, M, 3)).astype(np.float32)
+    lib = _lib.load()
+    dev = torch.device("cuda:0")
+    T = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (base, basis, p, poses, g)]
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    x = torch.full((V, M, 3), np.nan, dtype=torch.float32, device=dev)
+    check(lib.shs_chain_forward_views(ptr(T[0]), ptr(T[1]), M, D, ptr(T[2]), ptr(T[3]), V, int(direction), None,
+                                      ptr(x), s), "forward views")
+    nbytes = lib.shs_chain_views_workspace_bytes(M, D, V)
+    ws = torch.empty(max(nbytes, 16) // 4, dtype=torch.float32, device=dev)
+    d_p = torch.full((D,), np.nan, dtype=torch.float32, device=dev)
+    d_poses = torch.full((V, 6), np.nan, dtype=torch.float32, device=dev)
+    check(lib.shs_chain_backward_views(ptr(T[0]), ptr(T[1]), M, D, ptr(T[2]), ptr(T[3]), V, int(direction), ptr(T[4]),
+                                       ptr(d_p), ptr(d_poses), ptr(ws), ws.numel() * 4, s), "backward views")
+    torch.cuda.synchronize()
+    x, d_p, d_poses = x.cpu().numpy(), d_p.cpu().numpy(), d_poses.cpu().numpy()
+    ref_dp, abs_dp = np.zeros(D), np.zeros(D)
+    for v in range(V):
+        rx, _ = C.deform_pose(base, basis, p, poses[v], direction)
+        assert np.abs(x[v] - rx).max() <= 1e-5 * max(np.abs(rx).max(), 1e-30), v
+        ref = C.deform_pose_backward(base, basis, p, poses[v], g[v], direction)
+        assert _sum_err(d_poses[v], ref["d_pose"], ref["abs_d_pose"]) <= 1e-4, v
+        ref_dp += ref["d_p"]
+        abs_dp += ref["abs_d_p"]
+    assert _sum_err(d_p, ref_dp, abs_dp) <= 1e-4
+    # more views than the limit: refused before any launch
+    assert lib.shs_chain_forward_views(ptr(T[0]), ptr(T[1]), M, D, ptr(T[2]), ptr(T[3]), 33, 0, None, ptr(T[4]),
+                                       s) == 1
