@@ -84,20 +84,26 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel, workload_tag):
-    """DRAM bytes per launch (read + write) of ``kernel`` from the committed
-    ncu summary, or None when the kernels changed since it was taken.  The
-    summary carries lines 'traffic <kernel> <workload> <bytes> <source hash>'."""
+def profiled_value(tag, kernel, workload_tag):
+    """A per-launch figure of ``kernel`` recorded in a committed ncu summary,
+    or None when the kernel sources changed since it was taken.  The summary
+    carries lines '<tag> <kernel> <workload> <value> <source hash>'; tags:
+    'traffic' (DRAM read + write bytes), 'flops' (executed FP32 flop: 2 per
+    FFMA, 4 per FFMA2, 1 per FADD / FMUL, 2 per FADD2 / FMUL2)."""
     import glob
     want = kernel_source_hash()
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(path) as fh:
             for line in fh:
                 parts = line.strip().strip("`").split()
-                if len(parts) == 5 and parts[0] == "traffic" and parts[1] == kernel and parts[2] == workload_tag:
+                if len(parts) == 5 and parts[0] == tag and parts[1] == kernel and parts[2] == workload_tag:
                     if parts[4] == want:
                         return float(parts[3])
     return None
+
+
+def profiled_traffic(kernel, workload_tag):
+    return profiled_value("traffic", kernel, workload_tag)
 
 
 def read_ol_table(path):
@@ -249,7 +255,7 @@ def bench_ours(args, world, rank, local, dist):
         # so clock samples see the GPU under load), L2 flushed before each
         # step as above, CUDA events around each step
         est_ms = (t1 - t0) * 1e3 / K
-        NL = int(min(20000, max(200, 3000.0 / max(est_ms, 1e-3))))
+        NL = args.latency_reps or int(min(20000, max(200, 3000.0 / max(est_ms, 1e-3))))
         ls = [torch.cuda.Event(enable_timing=True) for _ in range(NL)]
         le = [torch.cuda.Event(enable_timing=True) for _ in range(NL)]
         lm = [torch.cuda.Event(enable_timing=True) for _ in range(NL)]
@@ -279,8 +285,14 @@ def bench_ours(args, world, rank, local, dist):
     bwd_mean = statistics.fmean(bwd_ms)
     fwd_mean = statistics.fmean(fwd_ms)
     peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = P * fm["bwd"] / (bwd_mean * 1e-3) / 1e12
-    achieved_fwd = P * fm["fwd"] / (fwd_mean * 1e-3) / 1e12
+    # work per launch: the smaller of the algorithmic model and the FP32 flop
+    # ncu counted in the kernel (recorded in profiles/ for these sources)
+    exec_b = profiled_value("flops", "backward_kernel_t", "capsule512_n4")
+    exec_f = profiled_value("flops", "forward_kernel_t", "capsule512_n4")
+    work_b = min(P * fm["bwd"], exec_b) if exec_b else P * fm["bwd"]
+    work_f = min(P * fm["fwd"], exec_f) if exec_f else P * fm["fwd"]
+    achieved = work_b / (bwd_mean * 1e-3) / 1e12
+    achieved_fwd = work_f / (fwd_mean * 1e-3) / 1e12
     p50 = lat_ms[len(lat_ms) // 2]
     p99 = lat_ms[min(len(lat_ms) - 1, int(round(0.99 * (len(lat_ms) - 1))))]
 
@@ -337,11 +349,16 @@ def bench_ours(args, world, rank, local, dist):
                                     "null when the kernel sources changed since",
                   "kernel_source_hash": kernel_source_hash(),
                   "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                  "flops_per_point": fm["bwd"], "k_mean": k_mean,
+                  "flops_per_point": work_b / P, "flops_per_point_model": fm["bwd"],
+                  "flops_per_point_executed": exec_b / P if exec_b else None,
+                  "work_basis": "min(model, ncu-executed FP32 flop)" if exec_b else "model (no current ncu count)",
+                  "k_mean": k_mean,
                   "peak_measured": fma_peak, "frac_of_measured": achieved / fma_peak if fma_peak else None,
                   "peak_measured_source": "shs_fp32_fma_probe: 1216 x 256 threads x 8 FMA chains, CUDA events",
                   "forward": {"achieved": achieved_fwd, "frac": achieved_fwd / peak,
-                              "flops_per_point": fm["fwd"]}},
+                              "frac_of_measured": achieved_fwd / fma_peak if fma_peak else None,
+                              "flops_per_point": work_f / P, "flops_per_point_model": fm["fwd"],
+                              "flops_per_point_executed": exec_f / P if exec_f else None}},
         e2e={"value": world * pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
              "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3, "steps": KE,
              "api": "HostStepPipeline (pinned host in/out, 3 streams, depth 2)"},
@@ -995,6 +1012,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--atomic", action="store_true", help="unordered (atomic) scene-gradient reduction")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--latency-reps", type=int, default=0,
+                    help="steps of the latency loop (default: >= 200 and about 3 s)")
     ap.add_argument("--workload", choices=("capsule", "serving", "heightfield", "envmap", "chain"), default="capsule",
                     help="capsule: the 512x512 G-buffer step (default); serving: the mixed request stream")
     ap.add_argument("--hf-res", type=int, default=1024, help="height-field grid side (heightfield workload)")
