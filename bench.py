@@ -543,7 +543,8 @@ def bench_serving(args, world, rank, local):
     torch.cuda.set_device(local)
     rng = np.random.default_rng(4 + 1000 * rank)
     n_jobs, n_req = args.serve_jobs, args.serve_requests
-    srv = serve.Server(hbm_budget_bytes=80e9, n_slots=3, max_batch=32)
+    srv = serve.Server(hbm_budget_bytes=80e9, n_slots=3, max_batch=32, chunk_points=args.serve_chunk,
+                       batch_work=args.serve_batch_work)
     for j in range(n_jobs):
         P = int(np.exp(rng.uniform(np.log(16384), np.log(1048576))))
         N = int(rng.integers(20, 501))
@@ -607,8 +608,14 @@ def bench_serving(args, world, rank, local):
         lat = [r.latency * 1e3 for r in reqs]
         span = max(r.done for r in reqs) - t0
         pairs = sum(r.pairs for r in reqs)
-        return {"value": pairs / span, "p50_ms": serve.percentile(lat, 0.5), "p99_ms": serve.percentile(lat, 0.99),
-                "span_s": span, "requests": len(reqs)}
+        out = {"value": pairs / span, "p50_ms": serve.percentile(lat, 0.5), "p99_ms": serve.percentile(lat, 0.99),
+               "span_s": span, "requests": len(reqs)}
+        # latency by request size: jobs under 100k points, and the rest
+        for name, test in (("under_100k_points", lambda P: P < 100_000), ("100k_points_and_up", lambda P: P >= 100_000)):
+            sel = [r.latency * 1e3 for r in reqs if test(srv.jobs[r.job_id].P)]
+            out[name] = {"requests": len(sel), "p50_ms": serve.percentile(sel, 0.5),
+                         "p99_ms": serve.percentile(sel, 0.99)}
+        return out
 
     from collections import deque
     pc_reqs, pc_t0 = run_percall()
@@ -636,10 +643,15 @@ def bench_serving(args, world, rank, local):
                                     "at 80% of per-call capacity, 80 GB HBM budget",
                         "jobs": n_jobs, "requests": n_req, "rate_per_s": rate,
                         "mean_per_call_service_ms": mean_service * 1e3, "slots": 3, "max_batch": 32},
-                latency_ms={"p50": sv["p50_ms"], "p99": sv["p99_ms"]},
-                batches=srv.batches, max_batches_in_flight=srv.max_inflight,
+                latency_ms={"p50": sv["p50_ms"], "p99": sv["p99_ms"],
+                            "under_100k_points": sv["under_100k_points"],
+                            "100k_points_and_up": sv["100k_points_and_up"]},
+                batches=srv.batches, max_batches_in_flight=srv.max_inflight, chunk_points=srv.chunk_points,
+                batch_work=srv.batch_work,
                 per_call_baseline={"value": pc["value"], "unit": "pairs/s",
-                                   "latency_ms": {"p50": pc["p50_ms"], "p99": pc["p99_ms"]}},
+                                   "latency_ms": {"p50": pc["p50_ms"], "p99": pc["p99_ms"],
+                                                  "under_100k_points": pc["under_100k_points"],
+                                                  "100k_points_and_up": pc["100k_points_and_up"]}},
                 span_s={"server": sv["span_s"], "per_call": pc["span_s"]},
                 saturated={"server": {"value": svs["value"], "span_s": svs["span_s"]},
                            "per_call": {"value": pcs["value"], "span_s": pcs["span_s"]},
@@ -1022,6 +1034,10 @@ def main():
                          "fp32_oltable")
     ap.add_argument("--env-res", type=int, default=4096, help="environment map rows (width = 2 x rows)")
     ap.add_argument("--serve-jobs", type=int, default=64)
+    ap.add_argument("--serve-batch-work", type=float, default=3.0e8,
+                    help="serving: estimated work one batch may carry (serve.task_work units)")
+    ap.add_argument("--serve-chunk", type=int, default=1 << 40,
+                    help="serving: largest chunk of a request in one launch (points)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

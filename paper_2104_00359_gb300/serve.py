@@ -12,6 +12,15 @@ that slot's stream.  Batches in different slots overlap on the device, and
 requests that arrive while batches run join the next free slot -- continuous
 batching, not a queue in front of one call at a time.
 
+A large job can be split into chunks of at most ``chunk_points`` points, each with
+its own resident scene (the same spheres and lighting), saved state and
+scene-gradient buffers; its request becomes one task per chunk, and a batch
+takes at most one task of a request.  So no launch carries more than a chunk
+of any request, and a small request waits behind at most a chunk of a large
+one instead of its whole service time (the persistent batch kernels hold
+every SM until their work list drains).  The chunks' scene gradients and
+losses are summed when the request's last chunk completes.
+
 The per-call baseline (``PerCallRunner``) serves the same stream of requests
 one at a time with ``shs_shade`` / ``shs_shade_backward_l2`` on one stream.
 """
@@ -35,13 +44,30 @@ def _load():
 
 
 MAX_BATCH = 32
+# Chunking is off by default: measured on the serving mix it lengthened the
+# tails (the host loop handles many more, smaller batches); a cap on a
+# batch's work bounds the wait for SMs instead.
+CHUNK_POINTS = 1 << 40
+# Estimated work a batch may carry (task_work units; about 3 ms on a GB300):
+# the persistent batch kernels hold every SM until their work list drains,
+# so this bounds how long a newly arrived request waits for SMs.
+BATCH_WORK = 3.0e8
+
+
+def task_work(points, spheres, n_bands, op):
+    """Work estimate of one task: point-sphere pairs weighted by the band
+    count's cost per pair (relative to 4 bands), the adjoint counted as
+    forward + 2.5 x forward."""
+    per_pair = (n_bands * n_bands + 4.0) / 20.0
+    return points * max(spheres, 1) * per_pair * (3.5 if op == "fwdbwd" else 1.0)
 
 
 class Job:
-    """A job's resident device state."""
+    """A job's resident device state (and, for a job of more than
+    ``chunk_points`` points, that of its chunks)."""
 
     def __init__(self, job_id, points, normals, albedo, centers, radii, light, config: Config, target=None,
-                 device="cuda"):
+                 device="cuda", chunk_points=CHUNK_POINTS):
         self.job_id = job_id
         self.config = config
         dev = torch.device(device)
@@ -57,35 +83,72 @@ class Job:
         self.grads = self.scene._grad_buffers(self.P, dev, ("light", "albedo", "centers", "radii"))
         self.loss = torch.zeros((), dtype=torch.float32, device=dev)
         self.busy = False
+        self.active = None           # the request the job serves now
+        # chunks: [p0, p1) point ranges; a chunked job gets per-chunk scenes,
+        # saved state and scene-gradient buffers
+        nch = max(1, -(-self.P // int(chunk_points)))
+        bounds = [round(i * self.P / nch) for i in range(nch + 1)]
+        self.ranges = [(bounds[i], bounds[i + 1]) for i in range(nch)]
+        self.chunks = []
+        if nch > 1:
+            K = config.n_bands ** 2
+            for p0, p1 in self.ranges:
+                sc = Scene(self.centers if self.N else None, self.radii if self.N else None, self.light, config)
+                z = lambda *sh: torch.zeros(sh, dtype=torch.float32, device=dev)
+                self.chunks.append(dict(scene=sc, saved=sc.new_saved(p1 - p0, dev), d_light=z(3, K),
+                                        d_centers=z(max(self.N, 1), 3), d_radii=z(max(self.N, 1)), loss=z()))
 
     @staticmethod
-    def device_bytes(P, N, n_bands, with_target=True):
-        """Bytes a job holds on the device (inputs, outputs, saved state, scene)."""
+    def device_bytes(P, N, n_bands, with_target=True, chunk_points=CHUNK_POINTS):
+        """Bytes a job holds on the device (inputs, outputs, saved state,
+        scene, and for a chunked job the chunks' scenes and saved state)."""
         K = n_bands * n_bands
         per_point = 4 * (9 + 3 + (3 if with_target else 0) + 3 + K + 1)
         scene = 16 * N + 4 * (3 * K + 4) + 4 * 2 * (3 * K + 1 + 4 * N) + 4 * (3 * K + 4 * N)
-        return P * per_point + scene + 4096
+        nch = max(1, -(-P // int(chunk_points)))
+        chunked = 0 if nch == 1 else P * 4 * (K + 1) + nch * (scene + 4 * (3 * K + 4 * N + 1) + 4096)
+        return P * per_point + scene + chunked + 4096
 
     def bytes(self):
-        return self.device_bytes(self.P, self.N, self.config.n_bands, self.target is not None)
+        return self.device_bytes(self.P, self.N, self.config.n_bands, self.target is not None,
+                                 self.ranges[0][1] if len(self.ranges) > 1 else CHUNK_POINTS)
 
-    def request_struct(self, op):
+    def request_struct(self, op, chunk=0):
+        """The shs_request of chunk `chunk` (the whole job when unchunked)."""
         r = ShsRequest()
-        r.scene = self.scene.handle.value
-        r.n_points = self.P
-        r.points, r.normals, r.albedo = (t.data_ptr() for t in (self.points, self.normals, self.albedo))
-        r.radiance = self.radiance.data_ptr()
-        r.saved = self.saved.data_ptr()
+        p0, p1 = self.ranges[chunk]
+        c = self.chunks[chunk] if self.chunks else None
+        r.scene = (c["scene"] if c else self.scene).handle.value
+        r.n_points = p1 - p0
+        r.points, r.normals, r.albedo = (t[p0:p1].data_ptr() for t in (self.points, self.normals, self.albedo))
+        r.radiance = self.radiance[p0:p1].data_ptr()
+        r.saved = (c["saved"] if c else self.saved).data_ptr()
         if op == "fwdbwd":
-            r.target = self.target.data_ptr()
-            r.loss = self.loss.data_ptr()
-            for k in ("d_light", "d_albedo", "d_centers", "d_radii"):
+            r.target = self.target[p0:p1].data_ptr()
+            r.loss = (c["loss"] if c else self.loss).data_ptr()
+            r.d_albedo = self.grads["d_albedo"][p0:p1].data_ptr()
+            for k in ("d_light", "d_centers", "d_radii"):
                 v = self.grads[k]
-                setattr(r, k, v.data_ptr() if v is not None else None)
+                if v is None:
+                    continue
+                setattr(r, k, (c[k] if c else v).data_ptr())
         return r
+
+    def finish(self, op):
+        """After the last chunk of a request: the chunks' scene sums."""
+        if op != "fwdbwd" or not self.chunks:
+            return
+        self.loss.copy_(torch.stack([c["loss"] for c in self.chunks]).sum(0))
+        self.grads["d_light"].copy_(torch.stack([c["d_light"] for c in self.chunks]).sum(0))
+        if self.N:
+            self.grads["d_centers"].copy_(torch.stack([c["d_centers"][:self.N] for c in self.chunks]).sum(0))
+            self.grads["d_radii"].copy_(torch.stack([c["d_radii"][:self.N] for c in self.chunks]).sum(0))
+        torch.cuda.current_stream().synchronize()
 
     def close(self):
         self.scene.close()
+        for c in self.chunks:
+            c["scene"].close()
 
 
 @dataclass
@@ -99,6 +162,7 @@ class Request:
     batch: int = -1
     pairs: int = 0
     on_done: object = None
+    left: int = 0                # chunk tasks not yet completed
 
     @property
     def latency(self):
@@ -116,11 +180,16 @@ class _Slot:
 class Server:
     """Continuous-batching request loop (see module docstring)."""
 
-    def __init__(self, hbm_budget_bytes=80e9, n_slots=3, max_batch=MAX_BATCH, device="cuda"):
+    def __init__(self, hbm_budget_bytes=80e9, n_slots=3, max_batch=MAX_BATCH, device="cuda",
+                 chunk_points=CHUNK_POINTS, batch_work=BATCH_WORK):
         if not 1 <= max_batch <= MAX_BATCH:
             raise ValueError(f"max_batch must be in 1..{MAX_BATCH}")
+        if chunk_points < 128:
+            raise ValueError("chunk_points must be at least one 128-point tile")
         self.lib = _load()
         self.device = device
+        self.chunk_points = int(chunk_points)
+        self.batch_work = float(batch_work)
         self.budget = float(hbm_budget_bytes)
         self.max_batch = max_batch
         self.jobs = {}
@@ -143,7 +212,7 @@ class Server:
         Returns True when admitted now."""
         kw = dict(points=points, normals=normals, albedo=albedo, centers=centers, radii=radii, light=light,
                   config=config, target=target)
-        need = Job.device_bytes(len(points), len(centers), config.n_bands, target is not None)
+        need = Job.device_bytes(len(points), len(centers), config.n_bands, target is not None, self.chunk_points)
         if need > self.budget:
             raise ValueError(f"job {job_id} needs {need} bytes, more than the whole budget")
         if self.used + need <= self.budget and not self.waiting_jobs:
@@ -153,7 +222,7 @@ class Server:
         return False
 
     def _admit(self, job_id, kw):
-        job = Job(job_id, device=self.device, **kw)
+        job = Job(job_id, device=self.device, chunk_points=self.chunk_points, **kw)
         # the job's uploads and scene set-up ran on the current stream; the
         # batch slots use their own streams
         torch.cuda.current_stream().synchronize()
@@ -172,7 +241,7 @@ class Server:
         while self.waiting_jobs:
             job_id, kw = self.waiting_jobs[0]
             need = Job.device_bytes(len(kw["points"]), len(kw["centers"]), kw["config"].n_bands,
-                                    kw["target"] is not None)
+                                    kw["target"] is not None, self.chunk_points)
             if self.used + need > self.budget:
                 break
             self.waiting_jobs.popleft()
@@ -188,15 +257,20 @@ class Server:
         r = Request(self._req_ids, job_id, op, time.perf_counter() if arrival is None else arrival,
                     on_done=on_done)
         self._req_ids += 1
-        self.pending.append(r)
+        # one task per chunk of the job (its chunk count is known once admitted)
+        self.pending.append((r, None))
         return r
 
     def _retire(self, slot):
-        now = time.perf_counter()
-        for r in slot.requests:
-            r.done = now
+        for r, chunk in slot.requests:
+            r.left -= 1
+            if r.left:
+                continue
             job = self.jobs[r.job_id]
+            job.finish(r.op)
+            r.done = time.perf_counter()
             job.busy = False
+            job.active = None
             if r.on_done is not None:
                 r.on_done(r, job)
             self.completed.append(r)
@@ -213,29 +287,43 @@ class Server:
         for slot in self.slots:
             if slot.event is not None:
                 continue
-            batch, keep = [], deque()
+            batch, keep, work = [], deque(), 0.0
             while self.pending and len(batch) < self.max_batch:
-                r = self.pending.popleft()
+                r, chunk = self.pending.popleft()
                 job = self.jobs.get(r.job_id)
-                if job is None or job.busy or any(b.job_id == r.job_id for b in batch):
-                    keep.append(r)
+                # a job serves one request at a time; a batch takes one task of a request
+                if job is None or (job.busy and job.active is not r) or any(b[0] is r for b in batch):
+                    keep.append((r, chunk))
                     continue
-                if r.op == "fwdbwd" and job.target is None:
-                    raise ValueError(f"job {r.job_id} has no target for a fwdbwd request")
-                batch.append(r)
+                c0 = 0 if chunk is None else chunk
+                w = task_work(job.ranges[c0][1] - job.ranges[c0][0], job.N, job.config.n_bands, r.op)
+                if batch and work + w > self.batch_work:
+                    keep.append((r, chunk))
+                    continue
+                work += w
+                if chunk is None:
+                    # first task of the request: expand it into its chunks
+                    if r.op == "fwdbwd" and job.target is None:
+                        raise ValueError(f"job {r.job_id} has no target for a fwdbwd request")
+                    r.left = len(job.ranges)
+                    r.pairs = job.P * job.N
+                    keep.extend((r, c) for c in range(1, len(job.ranges)))
+                    chunk = 0
+                    job.busy = True
+                    job.active = r
+                batch.append((r, chunk))
             keep.extend(self.pending)
             self.pending = keep
             if not batch:
                 break
             arr = (ShsRequest * len(batch))()
             now = time.perf_counter()
-            for i, r in enumerate(batch):
+            for i, (r, chunk) in enumerate(batch):
                 job = self.jobs[r.job_id]
-                job.busy = True
-                arr[i] = job.request_struct(r.op)
-                r.launched = now
+                arr[i] = job.request_struct(r.op, chunk)
+                if not r.launched:
+                    r.launched = now
                 r.batch = self.batches
-                r.pairs = job.P * job.N
             check(self.lib.shs_shade_batch(slot.ctx, arr, len(batch), ctypes.c_void_p(slot.stream.cuda_stream)),
                   "shs_shade_batch")
             slot.event = torch.cuda.Event()

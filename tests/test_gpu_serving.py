@@ -28,14 +28,21 @@ def _jobs(seed=0, n_jobs=6):
     return out
 
 
-def test_mixed_batches_match_requests_alone():
+@pytest.mark.parametrize("chunk_points", [None, 512])
+def test_mixed_batches_match_requests_alone(chunk_points):
+    """With chunk_points = 512 every job of more than 512 points runs as
+    chunks with their own scenes, spread over several batches, and its scene
+    gradients and loss are summed from the chunks'."""
     import torch
     from paper_2104_00359_gb300 import Config, serve
     jobs = _jobs()
-    srv = serve.Server(hbm_budget_bytes=2e9, n_slots=3, max_batch=4)
+    srv = serve.Server(hbm_budget_bytes=2e9, n_slots=3, max_batch=4,
+                       chunk_points=chunk_points or serve.CHUNK_POINTS)
     for j, sc, target in jobs:
         assert srv.add_job(j, sc["points"], sc["normals"], sc["albedo"], sc["centers"], sc["radii"],
                            sc["light"], Config(n_bands=sc["n_bands"]), target=target)
+    if chunk_points:
+        assert sum(len(job.ranges) > 1 for job in srv.jobs.values()) >= 4
     # alone: per-call API on each job's resident buffers
     alone = {}
     runner = serve.PerCallRunner(srv.jobs)

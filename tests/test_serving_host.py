@@ -23,6 +23,8 @@ def test_budget_queue_order(monkeypatch):
     srv.budget, srv.jobs, srv.used = 0.0, {}, 0
     srv.waiting_jobs = serve.deque()
     srv.device = "cpu"
+    srv.chunk_points = serve.CHUNK_POINTS
+    srv.batch_work = serve.BATCH_WORK
     monkeypatch.setattr(serve, "Job", type("J", (FakeJob,), {"device_bytes": staticmethod(serve.Job.device_bytes)}))
     monkeypatch.setattr(torch.cuda, "current_stream", lambda: type("S", (), {"synchronize": lambda self: None})())
     size = serve.Job.device_bytes(1000, 10, 4, False)
