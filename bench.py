@@ -683,7 +683,7 @@ def bench_heightfield(args, world, rank, local):
     # tails in BF16 / TF32 / FP16; exp_mode 1 is the projected-exponential
     # variant, 2 the optimal linear step with the fitted 8-band table
     all_precs = (("fp32", 0, 0), ("bf16_tc", 2, 0), ("tf32_tc", 1, 0), ("fp16_tc", 3, 0), ("fp32_projexp", 0, 1),
-                 ("fp32_oltable", 0, 2))
+                 ("bf16_tc_projexp", 2, 1), ("tf32_tc_projexp", 1, 1), ("fp32_oltable", 0, 2))
     # the library stores the table as float32: give the oracle the same values
     table = tuple(np.float32(x).astype(np.float64) if i < 2 else x for i, x in
                   enumerate(read_ol_table(os.path.join(ROOT, "tests", "golden", "ol_table_n8.txt"))))
@@ -751,7 +751,7 @@ def bench_heightfield(args, world, rank, local):
                           "tail_fwd_ms": statistics.fmean(tail_f), "tail_bwd_ms": statistics.fmean(tail_b)}
         if prec != 0:
             out[prec_name]["roofline_tail"] = _tc_tail_roofline(prec, k, statistics.fmean(tail_f),
-                                                                statistics.fmean(tail_b))
+                                                                statistics.fmean(tail_b), mode)
         if mode in (1, 2):
             # accuracy of the exponential methods (FP64) against the projection of
             # exp(f) by a fine rule (64 x 128 nodes) on the same sample
@@ -775,15 +775,17 @@ def bench_heightfield(args, world, rank, local):
                 precisions=out)
 
 
-def _tc_tail_roofline(prec, k, fwd_ms, bwd_ms):
+def _tc_tail_roofline(prec, k, fwd_ms, bwd_ms, mode=0):
     """Tensor-core tails against the measured dense peak of their operand type.
     Work = the MMAs the method issues: per 128-point tile (kt = the tile's
-    largest k) and pass over the 256 quadrature directions, the evaluation
-    GEMM X = S Y^T and the projection GEMM (X o X)(w Y) are 2 x 128 x 256 x 64
+    largest k) and pass over the Q quadrature directions, the evaluation
+    GEMM X = S Y^T and the projection GEMM (X o X)(w Y) are 2 x 128 x Q x 64
     flop each, times the product terms of the split operands (BF16: 6, TF32 /
     FP16: 3).  Forward: kt squaring passes (2 GEMMs) and a shading pass (1).
     Adjoint: kt recomputed squarings (2), the shading adjoint (1 + 2) and kt
-    squaring adjoints (2 evaluations + 1 projection): 5 kt + 3."""
+    squaring adjoints (2 evaluations + 1 projection): 5 kt + 3.  Squarings:
+    Q = 256 (the 11 x 22 product rule); the projected exponential (mode 1):
+    Q = 512 (its 16 x 32 rule) and kt = 1 (one exp pass)."""
     peaks = load_peaks()
     bf16 = peaks.get("bf16_tflops") or 1900.0
     terms = 6 if prec == 2 else 3
@@ -791,7 +793,11 @@ def _tc_tail_roofline(prec, k, fwd_ms, bwd_ms):
     peak = bf16 * (1.1 / 2.25) if prec == 1 else bf16
     P = k.shape[0]
     kt = np.array([k[i:i + 128].max() for i in range(0, P, 128)], np.int64)
-    gemm = 2.0 * 128 * 256 * 64 * terms
+    Q = 256
+    if mode == 1:
+        kt = np.ones_like(kt)
+        Q = 512
+    gemm = 2.0 * 128 * Q * 64 * terms
     f_fwd = gemm * float(np.sum(2 * kt + 1))
     f_bwd = gemm * float(np.sum(5 * kt + 3))
     a_f = f_fwd / (fwd_ms * 1e-3) / 1e12
@@ -1029,8 +1035,10 @@ def main():
     ap.add_argument("--workload", choices=("capsule", "serving", "heightfield", "envmap", "chain"), default="capsule",
                     help="capsule: the 512x512 G-buffer step (default); serving: the mixed request stream")
     ap.add_argument("--hf-res", type=int, default=1024, help="height-field grid side (heightfield workload)")
-    ap.add_argument("--precisions", default="fp32,bf16_tc,tf32_tc,fp16_tc,fp32_projexp,fp32_oltable",
+    ap.add_argument("--precisions", default="fp32,bf16_tc,tf32_tc,fp16_tc,fp32_projexp,bf16_tc_projexp,"
+                    "tf32_tc_projexp,fp32_oltable",
                     help="heightfield workload: comma list of fp32, bf16_tc, tf32_tc, fp16_tc, fp32_projexp, "
+                         "bf16_tc_projexp, tf32_tc_projexp, "
                          "fp32_oltable")
     ap.add_argument("--env-res", type=int, default=4096, help="environment map rows (width = 2 x rows)")
     ap.add_argument("--serve-jobs", type=int, default=64)

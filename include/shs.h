@@ -74,6 +74,9 @@ typedef enum {
  *     memory.  Every operand is carried as a sum of parts of the MMA type:
  *     BF16 three parts (six MMAs per product), TF32 and FP16 two parts
  *     (three MMAs).  The shading's sums over the directions run in float32.
+ *     With exp_mode 1 the projected exponential takes the same form through
+ *     its 16 x 32 rule: X = f^ Y^T, U = (exp(X) o w) Y, adjoint
+ *     df^ = (exp(f^ Y^T) o (dU Y^T))(w Y); BF16 and TF32 only.
  *     Error against the FP64 reference stays below 2e-3 for the radiance
  *     and every gradient output. */
 enum { SHS_FP32 = 0, SHS_TF32 = 1, SHS_BF16 = 2, SHS_FP16 = 3 };
@@ -92,7 +95,8 @@ typedef struct {
                            /*    gradient through that selection)                          */
     int32_t exp_mode;      /* 0: the SH exponential by scaling, optimal linear step and    */
                            /*    squarings (Sec. 3.3.2);  1: projected exponential         */
-                           /*    P_n[exp(f)] by a 2n x 4n quadrature (FP32 precision only);*/
+                           /*    P_n[exp(f)] by a 2n x 4n quadrature (FP32, or at 8 bands  */
+                           /*    BF16 / TF32 on the tensor cores; FP16 is refused);        */
                            /*    2: as 0, with the optimal linear coefficients a(s), b(s)  */
                            /*    from a fitted table (shs_scene_set_ol_table)              */
 } shs_config;

@@ -155,8 +155,10 @@ shs_status check_config(const shs_config* c) {
     if (c->deterministic != 0 && c->deterministic != 1) return fail(SHS_ERR_INVALID_ARG, "deterministic must be 0 or 1");
     if (c->horizon_cull != 0 && c->horizon_cull != 1) return fail(SHS_ERR_INVALID_ARG, "horizon_cull must be 0 or 1");
     if (c->exp_mode < 0 || c->exp_mode > 2) return fail(SHS_ERR_INVALID_ARG, "exp_mode must be 0, 1 or 2");
-    if (c->exp_mode == 1 && c->precision != SHS_FP32)
-        return fail(SHS_ERR_UNSUPPORTED, "the projected exponential runs in SHS_FP32 only");
+    if (c->exp_mode == 1 && c->precision == SHS_FP16)
+        return fail(SHS_ERR_UNSUPPORTED,
+                    "the projected exponential on the tensor cores takes BF16 or TF32 operands "
+                    "(exp of the log-visibility exceeds the FP16 range)");
     return SHS_OK;
 }
 
@@ -256,11 +258,13 @@ void gauss_legendre(int n, double* x, double* w) {
     }
 }
 
-// Tensor-core tail tables, per device and operand type, for the product
-// quadrature 11 Gauss-Legendre nodes in z x 22 uniform azimuths (exact for the
-// degree-21 integrand of an 8-band triple product); directions 242..255 have
-// zero weight.  Built in double precision on the host and split there into
-// parts of the operand type (p_0 = rnd(x), p_1 = rnd(x - p_0), ...).
+// Tensor-core tail tables, per device, operand type and variant.  Variant 0:
+// the product quadrature 11 Gauss-Legendre nodes in z x 22 uniform azimuths
+// (exact for the degree-21 integrand of an 8-band triple product);
+// directions 242..255 have zero weight.  Variant 1: the projected
+// exponential's 2n x 4n rule, 16 x 32 (512 directions).  Built in double
+// precision on the host and split there into parts of the operand type
+// (p_0 = rnd(x), p_1 = rnd(x - p_0), ...).
 //   chunks: per chunk c of CQ directions, the parts of Y_c (rows q, 64 columns)
 //           then the parts of (2^8 w Y)_c (rows i, CQ columns), canonical
 //           K-major layout;
@@ -270,7 +274,7 @@ struct TcTables {
     float4* dirs = nullptr;
     float* ytab = nullptr;
 };
-TcTables g_tc_tables[64][3][2];   // device, operand type, forward / adjoint chunking
+TcTables g_tc_tables[64][3][2][2];   // device, operand type, forward / adjoint chunking, variant
 std::mutex g_tc_mutex;
 
 // x rounded to the operand type (round to nearest even).
@@ -317,15 +321,15 @@ void store_elem(unsigned char* base, size_t off, uint32_t bits, int eb) {
     }
 }
 
-shs_status tc_tables(int prec, int adjoint, TcTables* out) {
+shs_status tc_tables(int prec, int adjoint, int variant, TcTables* out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= 64) return fail(SHS_ERR_UNSUPPORTED, "device ordinal %d", dev);
     std::lock_guard<std::mutex> lock(g_tc_mutex);
-    TcTables& t = g_tc_tables[dev][prec][adjoint ? 1 : 0];
+    TcTables& t = g_tc_tables[dev][prec][adjoint ? 1 : 0][variant ? 1 : 0];
     if (!t.chunks) {
-        const int Q = shs::kTcQ, K = 64, NZ = 11, NP = 22;
+        const int Q = variant ? shs::kTcQExp : shs::kTcQ, K = 64, NZ = variant ? 16 : 11, NP = variant ? 32 : 22;
         const int CQ = shs::tail_tc_chunk(prec, adjoint), NCH = Q / CQ;
         const int eb = prec == shs::tc_prec_tf32 ? 4 : 2;
         const int parts = prec == shs::tc_prec_bf16 ? 3 : 2;
@@ -333,7 +337,7 @@ shs_status tc_tables(int prec, int adjoint, TcTables* out) {
         if (chunk != shs::tail_tc_chunk_bytes(prec, adjoint)) return fail(SHS_ERR_UNSUPPORTED, "tensor-core chunk size");
         std::vector<double> Y(static_cast<size_t>(Q) * K, 0.0), w(Q, 0.0);
         std::vector<float4> dirs(Q, make_float4(0.f, 0.f, 0.f, 0.f));
-        double zx[NZ], zw[NZ], y[64];
+        double zx[16], zw[16], y[64];
         gauss_legendre(NZ, zx, zw);
         for (int a = 0; a < NZ; ++a)
             for (int b = 0; b < NP; ++b) {
@@ -629,7 +633,7 @@ shs_status shs_shade(shs_scene_t sc, int64_t n_points, const float* points, cons
             a.saved_f = sc->fwork;
         }
         TcTables tt;
-        shs_status ts = tc_tables(tc_prec(sc->cfg), 0, &tt);
+        shs_status ts = tc_tables(tc_prec(sc->cfg), 0, sc->cfg.exp_mode == 1, &tt);
         if (ts != SHS_OK) return ts;
         cudaError_t e = shs::launch_forward_pairs<8>(a, st);
         if (e != cudaSuccess) return cuda_fail(e, "launch pair terms");
@@ -637,6 +641,7 @@ shs_status shs_shade(shs_scene_t sc, int64_t n_points, const float* points, cons
         t.sc = a.sc;
         t.n_points = n_points;
         t.prec = tc_prec(sc->cfg);
+        t.variant = sc->cfg.exp_mode == 1 ? 1 : 0;
         t.normals = normals;
         t.albedo = albedo;
         t.radiance = radiance;
@@ -668,12 +673,13 @@ shs_status shs_shade_tail(shs_scene_t sc, int64_t n_points, const float* normals
     split_saved(sc, n_points, const_cast<void*>(saved), &sf, &sk);
     if (tensor_core_precision(sc->cfg)) {
         TcTables tt;
-        shs_status ts = tc_tables(tc_prec(sc->cfg), 0, &tt);
+        shs_status ts = tc_tables(tc_prec(sc->cfg), 0, sc->cfg.exp_mode == 1, &tt);
         if (ts != SHS_OK) return ts;
         shs::TcArgs t{};
         t.sc = view_of(sc);
         t.n_points = n_points;
         t.prec = tc_prec(sc->cfg);
+        t.variant = sc->cfg.exp_mode == 1 ? 1 : 0;
         t.normals = normals;
         t.albedo = albedo;
         t.radiance = radiance;
@@ -765,7 +771,7 @@ static shs_status backward_common(shs_scene_t sc, int64_t n_points, const float*
         // the exponential's and the shading's adjoint on the tensor cores, then
         // the float32 pair pass of the split backward
         TcTables tt;
-        shs_status ts = tc_tables(tc_prec(sc->cfg), 1, &tt);
+        shs_status ts = tc_tables(tc_prec(sc->cfg), 1, sc->cfg.exp_mode == 1, &tt);
         if (ts != SHS_OK) return ts;
         const int hgrid = shs::tail_tc_bwd_grid();
         if (!sc->hwork) {
@@ -802,6 +808,7 @@ static shs_status backward_common(shs_scene_t sc, int64_t n_points, const float*
         t.sc = a.sc;
         t.n_points = n_points;
         t.prec = tc_prec(sc->cfg);
+        t.variant = sc->cfg.exp_mode == 1 ? 1 : 0;
         t.normals = normals;
         t.albedo = albedo;
         t.f = f;

@@ -94,26 +94,31 @@ struct BwdBatch {
 };
 
 // Reduced-precision tails on the tensor cores (8 bands): the log-visibility f
-// comes from the pair pass; the tables are the product quadrature's Y_c and
+// comes from the pair pass; the tables are the quadrature's Y_c and
 // (2^8 w Y)_c per chunk of directions, split into parts of the operand type
 // and laid out in the canonical K-major layout, chunk after chunk.
+// variant 0: the SH exponential by squarings through the 11 x 22 product rule
+// (kTcQ directions); variant 1: the projected exponential, V = e0 P[exp(f^)],
+// through its own 16 x 32 rule (kTcQExp directions), which also integrates
+// the shading exactly.
 struct TcArgs {
     SceneView sc;
     int64_t n_points;
     int prec;                // 0 = BF16 (3 parts), 1 = FP16 (2), 2 = TF32 (2)
+    int variant;             // 0 = squarings, 1 = projected exponential
     const float* normals;
     const float* albedo;
     float* radiance;         // forward: [P,3] out
     const float* f;          // [K][P]
     int* saved_k;            // forward: [P] out, or null
     const void* chunks;      // tables, chunk after chunk
-    const float4* dirs;      // [256] (x, y, z, w_q), zero weight past 242
-    const float* ytab;       // [256][64] y_i(w_q), float32
+    const float4* dirs;      // [Q] (x, y, z, w_q); the product rule has zero weight past 242
+    const float* ytab;       // [Q][64] y_i(w_q), float32
     float b2_unscale;        // 2^-8
     float lobe_c1;           // clamped-cosine lobe H(t) = c1 t + e0 + e1 t^2 + e2 t^4 + e3 t^6
     float lobe_e[4];
     // adjoint
-    const int* k_in;         // [P] squarings (saved by the forward)
+    const int* k_in;         // [P] squarings (saved by the forward); unused by variant 1
     const float* d_radiance; // [P,3], or null in L2 mode
     const float* radiance_in;// [P,3] (L2 mode)
     const float* target;     // [P,3] (L2 mode) or null
@@ -128,12 +133,13 @@ struct TcArgs {
 };
 
 constexpr int tc_prec_bf16 = 0, tc_prec_fp16 = 1, tc_prec_tf32 = 2;   // operand types of the tensor-core tails
-constexpr int kTcQ = 256;    // quadrature directions (242 used) for 8 bands
+constexpr int kTcQ = 256;    // product-rule directions (242 used) for 8 bands
+constexpr int kTcQExp = 512; // projected-exponential rule at 8 bands: 2n x 4n = 16 x 32
 
 template <int NB> cudaError_t launch_forward_pairs(const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_tail_tc_fwd(const TcArgs& a, cudaStream_t s);
 cudaError_t launch_tail_tc_bwd(const TcArgs& a, cudaStream_t s);
-int tail_tc_chunk(int precision, int adjoint);            // directions per table chunk
+int tail_tc_chunk(int precision, int adjoint);            // directions per table chunk (both rules)
 size_t tail_tc_chunk_bytes(int precision, int adjoint);
 int tail_tc_bwd_grid();                         // blocks of the adjoint tail (rows of its workspace)
 template <int NB> cudaError_t launch_forward_batch(const FwdBatch& b, cudaStream_t s);

@@ -20,6 +20,14 @@
 // l >= 3).  X_S comes from the tensor cores; the sum over directions runs on
 // the CUDA cores.
 //
+// Projected exponential (variant 1).  V = e0 P[exp(f^)] by the 2n x 4n rule
+// (16 Gauss-Legendre nodes x 32 azimuths, 512 directions) is one pass of the
+// same form: X = f^ Y^T, U = (exp(X) o w) Y, exp on the CUDA cores in place
+// of the square.  The rule is exact to degree 31, so the shading pass (and
+// in the adjoint its projections) runs through it too: one table set of 512
+// directions, streamed.  The adjoint's last pass is
+// df^ = P[exp(f^ Y^T) o (dU Y^T)], with dU = e0 dV.
+//
 // Roles in a block of 288 threads: warps 0-7 are the compute warps, two
 // threads per point (tensor-memory lane): warps w and w + 4 read lanes
 // 32 (w % 4) .. + 31 and take the two halves of each chunk's columns and of
@@ -48,7 +56,6 @@ namespace {
 
 constexpr int K = 64;
 constexpr int KPAD = 64;
-constexpr int kQ = kTcQ;          // 256 directions (242 with weight)
 constexpr int kCompute = 256;     // compute threads: two per point (one per half of each chunk)
 constexpr int kThreads = 288;     // + the MMA / copy warp
 constexpr int kMmaWarp = kCompute / 32;
@@ -86,9 +93,16 @@ __device__ __forceinline__ int row_shift(const float* S) {
     return min(64, max(-64, ilogbf(1.25f * sabs) - 6));
 }
 
+// Directions of a variant's rule.
+template <int VAR>
+constexpr int rule_dirs() {
+    return VAR ? kTcQExp : kTcQ;
+}
+
 // Direction table: s_dir[q] = (x, y, z, w_q), s_lc[c][q] = L_c(w_q).
-__device__ void load_directions(const TcArgs& a, float4* s_dir, float (*s_lc)[kQ]) {
-    for (int q = threadIdx.x; q < kQ; q += kCompute) {
+template <int Q>
+__device__ void load_directions(const TcArgs& a, float4* s_dir, float (*s_lc)[Q]) {
+    for (int q = threadIdx.x; q < Q; q += kCompute) {
         s_dir[q] = __ldg(a.dirs + q);
         const float* y = a.ytab + q * K;
         float l0 = 0.f, l1 = 0.f, l2 = 0.f;
@@ -134,6 +148,19 @@ __device__ __forceinline__ ExpState exp_setup(const SceneView& sc, const float* 
     S[0] = x.ol.a * kSqrt4Pi;
 #pragma unroll
     for (int i = 1; i < K; ++i) S[i] = x.ol.b * (f[i] * x.scale);
+    return x;
+}
+
+// Projected exponential: one pass (k = 1) evaluates and projects exp(f^);
+// S = f^, f without its constant term.
+__device__ __forceinline__ ExpState proj_setup(float* S) {
+    ExpState x;
+    x.k = 1;
+    x.e0 = expf(S[0] * kInvSqrt4Pi);
+    x.scale = 1.f;
+    x.nrm2 = 0.f;
+    x.ol = OLCoef{1.f, 1.f, 0.f, 0.f};
+    S[0] = 0.f;
     return x;
 }
 
@@ -209,15 +236,15 @@ struct Ring {
 // and streamed through a ring for TF32.  Tensor-memory columns: the split S
 // (kTmS), two fp32 buffers of X = S Y_c^T (kTmX), two split (X o X) operands
 // (kTmXs), the accumulator S' (kTmAcc).
-template <int PR, int CQ>
+template <int PR, int CQ, int Q>
 struct PlanF {
     using P = tc::Prec<PR>;
     static constexpr int EB = P::kElem, NP = P::kParts;
-    static constexpr int NCH = kQ / CQ;
+    static constexpr int NCH = Q / CQ;
     static constexpr uint32_t kTb = CQ * 64u * EB;       // one part of Y_c or (wY)_c
     static constexpr uint32_t kChunk = 2u * NP * kTb;
     static constexpr uint32_t kOffDir = 0;
-    static constexpr uint32_t kOffRing = kQ * 28;         // float4 dir, 3 floats of light
+    static constexpr uint32_t kOffRing = Q * 28;          // float4 dir, 3 floats of light
     static constexpr int kStatic = 4096;
     static constexpr int R0 = static_cast<int>((kSmemBudget - kStatic - kOffRing) / kChunk);
     static constexpr int R = R0 >= NCH ? NCH : (R0 > 6 ? 6 : R0);
@@ -234,9 +261,10 @@ struct PlanF {
     static constexpr uint32_t kIdescS = tc::idesc_of<PR>(128, 64);
 };
 
-template <int PR, int CQ>
+template <int PR, int CQ, int VAR>
 __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_constant__ TcArgs a) {
-    using PL = PlanF<PR, CQ>;
+    constexpr int Q = rule_dirs<VAR>();
+    using PL = PlanF<PR, CQ, Q>;
     constexpr int NCH = PL::NCH, R = PL::R, NP = PL::NP;
     constexpr int HQ = CQ / 2;   // each of a point's two threads takes half of a chunk's columns
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -247,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_c
     __shared__ float s_bx[128][3];
     const int tid = threadIdx.x, warp = tid >> 5;
     float4* s_dir = reinterpret_cast<float4*>(sm + PL::kOffDir);
-    float (*s_lc)[kQ] = reinterpret_cast<float (*)[kQ]>(s_dir + kQ);
+    float (*s_lc)[Q] = reinterpret_cast<float (*)[Q]>(s_dir + Q);
     unsigned char* sRing = sm + PL::kOffRing;
     volatile int* abort = &s_abort;
 
@@ -334,7 +362,7 @@ __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_c
         }
     } else {
         // ---------------- compute warps
-        load_directions(a, s_dir, s_lc);
+        load_directions<Q>(a, s_dir, s_lc);
         named_sync_compute();
         const int row = tid & 127, half = tid >> 7;
         const uint32_t lane_tm = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
@@ -348,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_c
             float S[K];
 #pragma unroll
             for (int i = 0; i < K; ++i) S[i] = live ? __ldg(a.f + i * P + q) : 0.f;
-            const ExpState ex = exp_setup(a.sc, S, S);
+            const ExpState ex = VAR ? proj_setup(S) : exp_setup(a.sc, S, S);
             atomicMax(&s_kt, static_cast<int>((it << 5) | ex.k));
             float ux = 0.f, uy = 0.f, uz = 1.f;
             if (live) {
@@ -395,8 +423,14 @@ __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_c
                     float X[HQ];
                     tc::tmem_ld<HQ>(lane_tm + PL::kTmX + b * CQ + half * HQ, X);
                     if (!shading) {
+                        if constexpr (VAR) {
+                            const float xs = ldexpf(1.f, sh);   // X holds f^ 2^-sh at the directions
 #pragma unroll
-                        for (int i = 0; i < HQ; ++i) X[i] *= X[i];
+                            for (int i = 0; i < HQ; ++i) X[i] = expf(X[i] * xs);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < HQ; ++i) X[i] *= X[i];
+                        }
                         if (c >= 2) {
                             ok = warp_wait(&g2[b], ((g2n - 2) >> 1) & 1u, abort, a.sc.status);
                             if (!ok) break;
@@ -428,7 +462,7 @@ __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_c
                 // tensor-memory loads are warp-collective: every lane loads, then
                 // only points that take part in this squaring keep the result
                 const bool take = pass < ex.k;
-                const float up = ldexpf(a.b2_unscale, 2 * sh);
+                const float up = VAR ? a.b2_unscale : ldexpf(a.b2_unscale, 2 * sh);
 #pragma unroll
                 for (int h2 = 0; h2 < 2; ++h2) {
                     float Sn[32];
@@ -461,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_c
                     a.radiance[3 * q] = __ldg(a.albedo + 3 * q) * B0 * s3;
                     a.radiance[3 * q + 1] = __ldg(a.albedo + 3 * q + 1) * B1 * s3;
                     a.radiance[3 * q + 2] = __ldg(a.albedo + 3 * q + 2) * B2 * s3;
-                    if (a.saved_k) a.saved_k[q] = ex.k;
+                    if (a.saved_k) a.saved_k[q] = VAR ? 0 : ex.k;
                 }
             }
         }
@@ -490,20 +524,23 @@ __global__ void __launch_bounds__(kThreads, 1) tail_fwd_tc_kernel(const __grid_c
 //                   chunk (the tables are those of the forward: the adjoint of
 //                   projecting with w Y is evaluating with Y, and back).
 // Then the optimal-linear step and the scaling in float32 (as the CUDA-core
-// adjoint) give df, stored for the pair pass.
+// adjoint) give df, stored for the pair pass.  The projected exponential
+// (variant 1) is the case kt = 1 with exp in place of the square: pass 0
+// projects exp(f^), the adjoint pass forms P[exp(f^ Y^T) o (dU Y^T)], which
+// is df^ itself.
 // Operands in tensor memory as in the forward: A (S_t) and A2 (dS_{t+1}, or
 // in the shading pass the second projected operand X_S H), two fp32 buffers
 // each of X = A Y_c^T and G = A2 Y_c^T, two split chunk operands Z, and the
 // accumulators (the second, W, shares G's columns where they suffice).
-template <int PR, int CQ>
+template <int PR, int CQ, int Q>
 struct PlanB {
     using P = tc::Prec<PR>;
     static constexpr int EB = P::kElem, NP = P::kParts;
-    static constexpr int NCH = kQ / CQ;
+    static constexpr int NCH = Q / CQ;
     static constexpr uint32_t kTb = CQ * 64u * EB;
     static constexpr uint32_t kChunk = 2u * NP * kTb;
     static constexpr uint32_t kOffDir = 0;
-    static constexpr uint32_t kOffRing = kQ * 28;
+    static constexpr uint32_t kOffRing = Q * 28;
     static constexpr int kStatic = 8192;
     static constexpr int R0 = static_cast<int>((kSmemBudget - kStatic - kOffRing) / kChunk);
     static constexpr int R = R0 >= NCH ? NCH : (R0 > 6 ? 6 : R0);
@@ -524,9 +561,10 @@ struct PlanB {
     static constexpr uint32_t kIdescS = tc::idesc_of<PR>(128, 64);
 };
 
-template <int PR, int CQ>
+template <int PR, int CQ, int VAR>
 __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_constant__ TcArgs a) {
-    using PL = PlanB<PR, CQ>;
+    constexpr int Q = rule_dirs<VAR>();
+    using PL = PlanB<PR, CQ, Q>;
     constexpr int NCH = PL::NCH, R = PL::R, NP = PL::NP;
     constexpr int HQ = CQ / 2;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -539,7 +577,7 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
     __shared__ float s_bx[128][7];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float4* s_dir = reinterpret_cast<float4*>(sm + PL::kOffDir);
-    float (*s_lc)[kQ] = reinterpret_cast<float (*)[kQ]>(s_dir + kQ);
+    float (*s_lc)[Q] = reinterpret_cast<float (*)[Q]>(s_dir + Q);
     unsigned char* sRing = sm + PL::kOffRing;
     volatile int* abort = &s_abort;
 
@@ -636,7 +674,7 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
         }
     } else {
         // ---------------- compute warps
-        load_directions(a, s_dir, s_lc);
+        load_directions<Q>(a, s_dir, s_lc);
         named_sync_compute();
         const int row = tid & 127, half = tid >> 7, lg = warp & 3;
         const uint32_t lane_tm = tmem + (static_cast<uint32_t>(lg * 32) << 16);
@@ -653,16 +691,23 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
             float V[K];      // S (forward passes), then dS (adjoint passes)
 #pragma unroll
             for (int i = 0; i < K; ++i) V[i] = live ? __ldg(a.f + i * P + q) : 0.f;
-            float nrm2 = 0.f;
-#pragma unroll
-            for (int i = 1; i < K; ++i) nrm2 = fmaf(V[i], V[i], nrm2);
-            const int k = a.k_in ? (live ? min(max(__ldg(a.k_in + q), 0), kMaxK) : 0) : scaling_k(a.sc, nrm2);
             const float e0 = expf(V[0] * kInvSqrt4Pi);
-            const float scale = ldexpf(1.f, -k);
-            const OLCoef ol = ol_coef(a.sc, nrm2 * scale * scale);
-            V[0] = ol.a * kSqrt4Pi;
+            int k = 1;
+            float scale = 1.f;
+            OLCoef ol{1.f, 1.f, 0.f, 0.f};
+            if constexpr (VAR) {
+                V[0] = 0.f;   // S_0 = f^
+            } else {
+                float nrm2 = 0.f;
 #pragma unroll
-            for (int i = 1; i < K; ++i) V[i] = ol.b * (V[i] * scale);
+                for (int i = 1; i < K; ++i) nrm2 = fmaf(V[i], V[i], nrm2);
+                k = a.k_in ? (live ? min(max(__ldg(a.k_in + q), 0), kMaxK) : 0) : scaling_k(a.sc, nrm2);
+                scale = ldexpf(1.f, -k);
+                ol = ol_coef(a.sc, nrm2 * scale * scale);
+                V[0] = ol.a * kSqrt4Pi;
+#pragma unroll
+                for (int i = 1; i < K; ++i) V[i] = ol.b * (V[i] * scale);
+            }
             atomicMax(&s_kt, static_cast<int>((it << 5) | k));
             float ux = 0.f, uy = 0.f, uz = 1.f, il = 0.f;
             float dB[3] = {0.f, 0.f, 0.f}, u[3] = {0.f, 0.f, 0.f};
@@ -761,11 +806,23 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
                     if (adj) {
                         float G[HQ];
                         tc::tmem_ld<HQ>(lane_tm + PL::kTmG + b * CQ + half * HQ, G);
+                        if constexpr (VAR) {
+                            const float xs = ldexpf(1.f, sh);
 #pragma unroll
-                        for (int i = 0; i < HQ; ++i) X[i] = 2.f * X[i] * G[i];
+                            for (int i = 0; i < HQ; ++i) X[i] = expf(X[i] * xs) * G[i];
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < HQ; ++i) X[i] = 2.f * X[i] * G[i];
+                        }
                     } else if (!shade) {
+                        if constexpr (VAR) {
+                            const float xs = ldexpf(1.f, sh);
 #pragma unroll
-                        for (int i = 0; i < HQ; ++i) X[i] *= X[i];
+                            for (int i = 0; i < HQ; ++i) X[i] = expf(X[i] * xs);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < HQ; ++i) X[i] *= X[i];
+                        }
                     } else {
                         // this half's directions: the sums, Z = D H (scaled 2^-sz), Z2 = X H
                         const int q0 = c * CQ + half * HQ;
@@ -810,9 +867,9 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
                 tc::fence_after_sync();
                 // the pass's accumulator (S', dV or dS') replaces V where the point takes part
                 const bool take = pass < kt ? pass < k : pass == kt ? true : 2 * kt - pass < k;
-                const float up = pass < kt ? ldexpf(a.b2_unscale, 2 * sh)
+                const float up = pass < kt ? ldexpf(a.b2_unscale, VAR ? 0 : 2 * sh)
                                            : pass == kt ? e0 * ldexpf(a.b2_unscale, sz)
-                                                        : ldexpf(a.b2_unscale, sh + shg);
+                                                        : ldexpf(a.b2_unscale, VAR ? shg : sh + shg);
 #pragma unroll
                 for (int h2 = 0; h2 < 2; ++h2) {
                     float Sn[32];
@@ -871,8 +928,16 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
             }
             if (!ok) break;
             // optimal linear step and scaling: S_0 = a(s) sqrt(4 pi), S_i = b(s) g_i, g = f^ 2^-k;
-            // each half writes its 32 coefficients of df
-            if (live) {
+            // each half writes its 32 coefficients of df.  The projected
+            // exponential's adjoint pass left df^ itself in V.
+            if (live && VAR) {
+                if (half == 0) a.dfp_ws[q] = de0 * e0 * kInvSqrt4Pi * a.sc.neg_2pi_eps * SH::norm(0);
+#pragma unroll
+                for (int i = 1; i < K; ++i) {
+                    if ((i >> 5) != half) continue;
+                    a.dfp_ws[i * P + q] = V[i] * a.sc.neg_2pi_eps * SH::norm(i);
+                }
+            } else if (live) {
                 float dBs = 0.f;
 #pragma unroll
                 for (int i = 1; i < K; ++i) dBs = fmaf(V[i], __ldg(a.f + i * P + q) * scale, dBs);
@@ -910,10 +975,10 @@ __global__ void __launch_bounds__(kThreads, 1) tail_bwd_tc_kernel(const __grid_c
     }
 }
 
-template <int PR, int CQ>
+template <int PR, int CQ, int VAR>
 cudaError_t launch_fwd_t(const TcArgs& a, cudaStream_t s) {
-    using PL = PlanF<PR, CQ>;
-    auto kern = tail_fwd_tc_kernel<PR, CQ>;
+    using PL = PlanF<PR, CQ, rule_dirs<VAR>()>;
+    auto kern = tail_fwd_tc_kernel<PR, CQ, VAR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(PL::kBytes));
     if (e != cudaSuccess) return e;
@@ -928,10 +993,10 @@ cudaError_t launch_fwd_t(const TcArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int PR, int CQ>
+template <int PR, int CQ, int VAR>
 cudaError_t launch_bwd_t(const TcArgs& a, cudaStream_t s) {
-    using PL = PlanB<PR, CQ>;
-    auto kern = tail_bwd_tc_kernel<PR, CQ>;
+    using PL = PlanB<PR, CQ, rule_dirs<VAR>()>;
+    auto kern = tail_bwd_tc_kernel<PR, CQ, VAR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(PL::kBytes));
     if (e != cudaSuccess) return e;
@@ -952,12 +1017,22 @@ int tail_tc_bwd_grid() {
     return sms > 0 ? sms : 1;
 }
 
+// The projected exponential takes BF16 or TF32 operands only: exp(f^) spans
+// more than the half-precision exponent range.
 cudaError_t launch_tail_tc_bwd(const TcArgs& a, cudaStream_t s) {
     if (a.n_points <= 0) return cudaSuccess;
+    if (a.variant == 1) {
+        switch (a.prec) {
+            case tc::kPrecBF16: return launch_bwd_t<tc::kPrecBF16, kCqBwdBF16, 1>(a, s);
+            case tc::kPrecTF32: return launch_bwd_t<tc::kPrecTF32, kCqBwdTF32, 1>(a, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (a.variant != 0) return cudaErrorInvalidValue;
     switch (a.prec) {
-        case tc::kPrecBF16: return launch_bwd_t<tc::kPrecBF16, kCqBwdBF16>(a, s);
-        case tc::kPrecFP16: return launch_bwd_t<tc::kPrecFP16, kCqBwdFP16>(a, s);
-        case tc::kPrecTF32: return launch_bwd_t<tc::kPrecTF32, kCqBwdTF32>(a, s);
+        case tc::kPrecBF16: return launch_bwd_t<tc::kPrecBF16, kCqBwdBF16, 0>(a, s);
+        case tc::kPrecFP16: return launch_bwd_t<tc::kPrecFP16, kCqBwdFP16, 0>(a, s);
+        case tc::kPrecTF32: return launch_bwd_t<tc::kPrecTF32, kCqBwdTF32, 0>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -973,21 +1048,29 @@ int tail_tc_chunk(int precision, int adjoint) {
 size_t tail_tc_chunk_bytes(int precision, int adjoint) {
     switch (precision) {
         case tc::kPrecBF16:
-            return adjoint ? PlanB<tc::kPrecBF16, kCqBwdBF16>::kChunk : PlanF<tc::kPrecBF16, kCqFwdBF16>::kChunk;
+            return adjoint ? PlanB<tc::kPrecBF16, kCqBwdBF16, kTcQ>::kChunk : PlanF<tc::kPrecBF16, kCqFwdBF16, kTcQ>::kChunk;
         case tc::kPrecFP16:
-            return adjoint ? PlanB<tc::kPrecFP16, kCqBwdFP16>::kChunk : PlanF<tc::kPrecFP16, kCqFwdFP16>::kChunk;
+            return adjoint ? PlanB<tc::kPrecFP16, kCqBwdFP16, kTcQ>::kChunk : PlanF<tc::kPrecFP16, kCqFwdFP16, kTcQ>::kChunk;
         case tc::kPrecTF32:
-            return adjoint ? PlanB<tc::kPrecTF32, kCqBwdTF32>::kChunk : PlanF<tc::kPrecTF32, kCqFwdTF32>::kChunk;
+            return adjoint ? PlanB<tc::kPrecTF32, kCqBwdTF32, kTcQ>::kChunk : PlanF<tc::kPrecTF32, kCqFwdTF32, kTcQ>::kChunk;
         default: return 0;
     }
 }
 
 cudaError_t launch_tail_tc_fwd(const TcArgs& a, cudaStream_t s) {
     if (a.n_points <= 0) return cudaSuccess;
+    if (a.variant == 1) {
+        switch (a.prec) {
+            case tc::kPrecBF16: return launch_fwd_t<tc::kPrecBF16, kCqFwdBF16, 1>(a, s);
+            case tc::kPrecTF32: return launch_fwd_t<tc::kPrecTF32, kCqFwdTF32, 1>(a, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (a.variant != 0) return cudaErrorInvalidValue;
     switch (a.prec) {
-        case tc::kPrecBF16: return launch_fwd_t<tc::kPrecBF16, kCqFwdBF16>(a, s);
-        case tc::kPrecFP16: return launch_fwd_t<tc::kPrecFP16, kCqFwdFP16>(a, s);
-        case tc::kPrecTF32: return launch_fwd_t<tc::kPrecTF32, kCqFwdTF32>(a, s);
+        case tc::kPrecBF16: return launch_fwd_t<tc::kPrecBF16, kCqFwdBF16, 0>(a, s);
+        case tc::kPrecFP16: return launch_fwd_t<tc::kPrecFP16, kCqFwdFP16, 0>(a, s);
+        case tc::kPrecTF32: return launch_fwd_t<tc::kPrecTF32, kCqFwdTF32, 0>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -44,7 +44,9 @@ def test_projected_exp_backward(n, n_spheres):
         assert err.max() <= TOL, f"{name}: max err {err.max():.3e}"
 
 
-def test_projected_exp_rejected_with_tensor_core_precision():
+def test_projected_exp_rejected_with_fp16_operands():
+    """exp(f^) spans more than the half-precision range: FP16 operands are
+    refused for the projected exponential (BF16 and TF32 run it)."""
     import torch
     from paper_2104_00359_gb300 import Config, Scene, _lib
     dev = torch.device("cuda:0")
@@ -52,6 +54,8 @@ def test_projected_exp_rejected_with_tensor_core_precision():
     with pytest.raises(_lib.ShsError) as e:
         Scene(None, None, light, Config(n_bands=8, precision=_lib.SHS_FP16, exp_mode=1))
     assert e.value.status == 2
+    for prec in (_lib.SHS_BF16, _lib.SHS_TF32):
+        Scene(None, None, light, Config(n_bands=8, precision=prec, exp_mode=1)).close()
 
 
 def test_projected_exp_with_horizon_cull_backward():

@@ -8,7 +8,10 @@
    forward and adjoint) against the FP64 oracle, per output: radiance and
    every gradient within 2e-3 (the stated reduced-precision tolerance) for
    BF16, TF32 and FP16, with the per-point squaring counts k from the GPU.
-   The float32 pair terms f and k must equal the FP32 path's bitwise."""
+   The float32 pair terms f and k must equal the FP32 path's bitwise.
+3. The projected exponential (exp_mode 1, V = e0 P[exp(f^)] by the 2n x 4n
+   rule) on the tensor cores, BF16 and TF32, forward and adjoint, against the
+   oracle's projected exponential, every output within 2e-3."""
 
 import ctypes
 
@@ -47,7 +50,7 @@ def test_tc_gemm_matches_numpy(n, k):
         assert err.max() <= tol, (mode, err.max())
 
 
-def _run(sc, prec, dB, saved=True, deterministic=True, target=None):
+def _run(sc, prec, dB, saved=True, deterministic=True, target=None, exp_mode=0):
     import torch
     from paper_2104_00359_gb300 import Config, Scene
     from gpu_helpers import FIELDS
@@ -55,7 +58,7 @@ def _run(sc, prec, dB, saved=True, deterministic=True, target=None):
     T = {k: torch.from_numpy(np.ascontiguousarray(sc[k])).to(dev) for k in FIELDS}
     P = sc["points"].shape[0]
     scene = Scene(T["centers"], T["radii"], T["light"], Config(n_bands=8, precision=prec,
-                                                               deterministic=deterministic))
+                                                               deterministic=deterministic, exp_mode=exp_mode))
     sv = scene.new_saved(P, dev)
     B = scene.shade(T["points"], T["normals"], T["albedo"], saved=sv)
     if target is not None:
@@ -74,11 +77,11 @@ def _run(sc, prec, dB, saved=True, deterministic=True, target=None):
     return out
 
 
-def _errors(sc, got, dB, k):
+def _errors(sc, got, dB, k, exp_mode=0):
     from oracle import shs_oracle as O
     from gpu_helpers import FIELDS, grad_err, rel_err
     args = [sc[x] for x in FIELDS]
-    cfg = O.Config(n_bands=8)
+    cfg = O.Config(n_bands=8, exp_mode=exp_mode)
     ref = O.shade_backward(cfg, *args, dB, k=k)
     errs = {"radiance": float(rel_err(got["radiance"], ref["forward"]["radiance"]).max())}
     for name in GRADS:
@@ -146,3 +149,69 @@ def test_tensor_core_adjoint_modes():
     assert abs(float(d["loss"]) - 0.5 * np.sum(dBl ** 2)) <= 1e-5 * np.sum(dBl ** 2)
     for name in GRADS:
         assert grad_err(name, d[name], ref).max() <= TOL_TC, name
+
+
+@pytest.mark.parametrize("scene_kind", ["random", "heightfield"])
+@pytest.mark.parametrize("prec_name", ["bf16", "tf32"])
+def test_tensor_core_projected_exp_n8_against_oracle(prec_name, scene_kind):
+    """exp_mode 1 on the tensor cores: the exp pass, shading and adjoint
+    through the 16 x 32 rule, every output vs the oracle's projected
+    exponential; the float32 CUDA-core variant is checked beside it."""
+    from paper_2104_00359_gb300._lib import SHS_BF16, SHS_FP32, SHS_TF32
+    prec = dict(bf16=SHS_BF16, tf32=SHS_TF32)[prec_name]
+    sc = _sample_scene(scene_kind)
+    P = sc["points"].shape[0]
+    dB = np.random.default_rng(15).normal(size=(P, 3))
+    g32 = _run(sc, SHS_FP32, dB, exp_mode=1)
+    gtc = _run(sc, prec, dB, exp_mode=1)
+    np.testing.assert_array_equal(gtc["f"], g32["f"])
+    assert np.all(gtc["k"] == 0) and np.all(g32["k"] == 0)
+    e32 = _errors(sc, g32, dB, None, exp_mode=1)
+    etc = _errors(sc, gtc, dB, None, exp_mode=1)
+    print(f"{prec_name} projexp {scene_kind}: " + ", ".join(f"{k} {v:.2e}" for k, v in etc.items()))
+    print(f"fp32 projexp {scene_kind}: " + ", ".join(f"{k} {v:.2e}" for k, v in e32.items()))
+    assert e32["radiance"] <= 1e-4
+    for name, v in etc.items():
+        assert v <= TOL_TC, f"{prec_name} projexp {scene_kind}: {name} max normalised error {v:.3e}"
+
+
+def test_tensor_core_projected_exp_modes():
+    """BF16 projected exponential: recompute (no saved state) equals saved,
+    the fused L2 adjoint against the oracle, and the re-shading tail."""
+    import torch
+    from oracle import shs_oracle as O
+    from paper_2104_00359_gb300 import Config, Scene, synthetic as S
+    from paper_2104_00359_gb300._lib import SHS_BF16
+    from gpu_helpers import FIELDS, grad_err, rel_err
+    sc = S.random_scene(79, 301, 17, 8, inside_fraction=0.05)
+    P = sc["points"].shape[0]
+    dB = np.random.default_rng(16).normal(size=(P, 3))
+    a = _run(sc, SHS_BF16, dB, exp_mode=1)
+    b = _run(sc, SHS_BF16, dB, saved=False, exp_mode=1)
+    for name in GRADS:
+        np.testing.assert_allclose(b[name], a[name], rtol=0, atol=1e-6 * np.abs(a[name]).max())
+    cfg = O.Config(n_bands=8, exp_mode=1)
+    tgt = S.perturb_scene(sc, 4)
+    target = O.shade_forward(cfg, *[tgt[x] for x in FIELDS])["radiance"]
+    d = _run(sc, SHS_BF16, None, target=target, exp_mode=1)
+    dBl = d["radiance"].astype(np.float64) - target.astype(np.float32)
+    ref = O.shade_backward(cfg, *[sc[x] for x in FIELDS], dBl)
+    assert abs(float(d["loss"]) - 0.5 * np.sum(dBl ** 2)) <= 1e-5 * np.sum(dBl ** 2)
+    for name in GRADS:
+        assert grad_err(name, d[name], ref).max() <= TOL_TC, name
+    # shs_shade_tail from the saved pair terms under new lighting
+    dev = torch.device("cuda:0")
+    T = {k: torch.from_numpy(np.ascontiguousarray(sc[k])).to(dev) for k in FIELDS}
+    scene = Scene(T["centers"], T["radii"], T["light"], Config(n_bands=8, precision=SHS_BF16, exp_mode=1))
+    sv = scene.new_saved(P, dev)
+    scene.shade(T["points"], T["normals"], T["albedo"], saved=sv)
+    light2 = np.random.default_rng(17).normal(scale=0.3, size=sc["light"].shape).astype(np.float32)
+    light2[:, 0] = 1.0
+    scene.update(light=torch.from_numpy(light2).to(dev))
+    B2 = scene.shade_tail(T["normals"], T["albedo"], sv).cpu().numpy()
+    assert scene.device_status() == 0
+    scene.close()
+    args = [sc[x] for x in FIELDS]
+    args[FIELDS.index("light")] = light2
+    ref2 = O.shade_forward(cfg, *args)["radiance"]
+    assert rel_err(B2, ref2).max() <= TOL_TC
