@@ -71,6 +71,7 @@ def flop_model(n, n_spheres, k_mean):
 
 
 KERNEL_SOURCES = ("paper_2104_00359_gb300/csrc/shs_kern.cu", "paper_2104_00359_gb300/csrc/shs_internal.h",
+                  "paper_2104_00359_gb300/csrc/shs_exp.cuh", "paper_2104_00359_gb300/csrc/shs_warp.cuh",
                   "paper_2104_00359_gb300/csrc/generated/shs_sh_gen.cuh")
 
 
@@ -688,6 +689,7 @@ def bench_heightfield(args, world, rank, local):
     table = tuple(np.float32(x).astype(np.float64) if i < 2 else x for i, x in
                   enumerate(read_ol_table(os.path.join(ROOT, "tests", "golden", "ol_table_n8.txt"))))
     fine = None
+    fma_peak = None
     oracle_cache = {}
     grads = ("d_light", "d_albedo", "d_centers", "d_radii", "d_points", "d_normals")
     for prec_name, prec, mode in [x for x in all_precs if x[0] in args.precisions.split(",")]:
@@ -752,6 +754,12 @@ def bench_heightfield(args, world, rank, local):
         if prec != 0:
             out[prec_name]["roofline_tail"] = _tc_tail_roofline(prec, k, statistics.fmean(tail_f),
                                                                 statistics.fmean(tail_b), mode)
+        elif mode == 0:
+            if fma_peak is None:
+                from paper_2104_00359_gb300 import _lib
+                fma_peak = measure_fma_peak(_lib.load(), dev, torch.cuda.current_stream())
+            out[prec_name]["roofline"] = _fp32_roofline_n8(P, N, float(k.mean()), statistics.fmean(times_f),
+                                                           statistics.fmean(times_b), fma_peak)
         if mode in (1, 2):
             # accuracy of the exponential methods (FP64) against the projection of
             # exp(f) by a fine rule (64 x 128 nodes) on the same sample
@@ -773,6 +781,40 @@ def bench_heightfield(args, world, rank, local):
                 config={"workload": f"height field {args.hf_res}x{args.hf_res} points, 300 spheres, n_bands=8 (64 SH coeffs)",
                         "points": P, "spheres": N, "error_sample_points": int(len(sel))},
                 precisions=out)
+
+
+def _fp32_roofline_n8(P, N, k_mean, fwd_ms, bwd_ms, fma_peak):
+    """The FP32 CUDA-core 8-band step against the FP32 FMA peak.  Work per
+    point = the smaller of the flop model (flop_model) and the FP32 flop the
+    kernels execute per point, counted by ncu on the 512 x 512 height field
+    (same 300 spheres; 'flops <kernel> heightfield512_n8' lines in profiles/,
+    used only while the kernel sources are unchanged).  Forward: the shading
+    kernel; backward: the tail adjoint pass and the pair pass (the lighting
+    reduction is not counted)."""
+    fm = flop_model(8, N, k_mean)
+    peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    pts512 = 512 * 512
+    ex_f = profiled_value("flops", "forward_kernel_t", "heightfield512_n8")
+    ex_t = profiled_value("flops", "backward_kernel_t", "heightfield512_n8")
+    ex_p = profiled_value("flops", "bwd_pairs_t_kernel", "heightfield512_n8")
+    ex_f = ex_f / pts512 if ex_f else None
+    ex_b = (ex_t + ex_p) / pts512 if (ex_t and ex_p) else None
+    wf = min(fm["fwd"], ex_f) if ex_f else fm["fwd"]
+    wb = min(fm["bwd"], ex_b) if ex_b else fm["bwd"]
+    af = wf * P / (fwd_ms * 1e-3) / 1e12
+    ab = wb * P / (bwd_ms * 1e-3) / 1e12
+    return {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+            "peak_source": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz",
+            "peak_measured": fma_peak,
+            "forward": {"achieved": af, "frac": af / peak, "frac_of_measured": af / fma_peak if fma_peak else None,
+                        "flops_per_point": wf, "flops_per_point_model": fm["fwd"],
+                        "flops_per_point_executed": ex_f},
+            "backward": {"achieved": ab, "frac": ab / peak, "frac_of_measured": ab / fma_peak if fma_peak else None,
+                         "flops_per_point": wb, "flops_per_point_model": fm["bwd"],
+                         "flops_per_point_executed": ex_b},
+            "work_basis": "min(model, ncu-executed FP32 flop per point)" if (ex_f and ex_b)
+                          else "model (no current ncu count)",
+            "k_mean": k_mean, "kernel_source_hash": kernel_source_hash()}
 
 
 def _tc_tail_roofline(prec, k, fwd_ms, bwd_ms, mode=0):

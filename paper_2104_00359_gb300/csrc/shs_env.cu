@@ -18,6 +18,7 @@
 
 #include "shs.h"
 #include "shs_internal.h"
+#include "shs_warp.cuh"
 
 namespace {
 
@@ -34,13 +35,8 @@ struct EnvArgs {
     float norm[64];          // N'_lm by linear index
     float* partials;         // [gridDim.x][3K]
     int vec4;                // 16-byte aligned map and width % 4 == 0: rows read as float4
+    int sym;                 // ... and width % 16 == 0: the four-fold azimuthal symmetry path
 };
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // P_l^m(x) without the Condon-Shortley phase, s = sqrt(1 - x^2) >= 0:
 // P_m^m = (2m-1)!! s^m, P_{m+1}^m = (2m+1) x P_m^m,
@@ -89,41 +85,144 @@ __device__ __forceinline__ void add_pixel(float v0, float v1, float v2, float c1
     }
 }
 
+// Four columns at once through the azimuthal symmetries of the pixel
+// centres: with phi the angle of column c < W/4, the columns W/2 - 1 - c,
+// W/2 + c and W - 1 - c sit at pi - phi, pi + phi and -phi, where
+//   cos(m (pi + phi)) = (-1)^m cos(m phi),  sin(m (pi + phi)) = (-1)^m sin(m phi),
+//   cos(m (-phi)) = cos(m phi),             sin(m (-phi)) = -sin(m phi),
+//   cos(m (pi - phi)) = (-1)^m cos(m phi),  sin(m (pi - phi)) = -(-1)^m sin(m phi).
+// So with v1..v4 the values at phi, pi + phi, -phi, pi - phi, the four
+// pixels add cos(m phi) (v1 + v3 +- (v2 + v4)) and sin(m phi) (v1 - v3 +-
+// (v2 - v4)) to the moments (+ for even m, - for odd): one evaluation of the
+// harmonics and one multiply-add per moment for four pixels.  cos(m phi),
+// sin(m phi) by the recurrence x_{m+1} = 2 cos(phi) x_m - x_{m-1} (for
+// m < 8 its rounding error stays within a few tens of ulps).
+template <int NB>
+__device__ __forceinline__ void add_quad(const float* v1, const float* v2, const float* v3, const float* v4,
+                                         float c1, float s1, float* acc, float2* acc2) {
+    float ep[3], em[3], sp[3], sm[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const float p = v1[ch] + v3[ch], q = v2[ch] + v4[ch], r = v1[ch] - v3[ch], t = v2[ch] - v4[ch];
+        ep[ch] = p + q;
+        em[ch] = p - q;
+        sp[ch] = r + t;
+        sm[ch] = r - t;
+        acc[ch] += ep[ch];
+    }
+    if constexpr (NB > 1) {
+        const float two_c = c1 + c1;
+        float cp = 1.f, spv = 0.f, cm = c1, smv = s1;
+#pragma unroll
+        for (int mm = 1; mm < NB; ++mm) {
+            const float2 t = make_float2(cm, smv);
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float2 w = (mm & 1) ? make_float2(em[ch], sm[ch]) : make_float2(ep[ch], sp[ch]);
+                acc2[3 * (mm - 1) + ch] = __ffma2_rn(w, t, acc2[3 * (mm - 1) + ch]);
+            }
+            if (mm + 1 < NB) {
+                const float cn = fmaf(two_c, cm, -cp), sn = fmaf(two_c, smv, -spv);
+                cp = cm;
+                spv = smv;
+                cm = cn;
+                smv = sn;
+            }
+        }
+    }
+}
+
 #ifndef SHS_ENV_MINB
-#define SHS_ENV_MINB 1
+#define SHS_ENV_MINB 4
 #endif
 #ifndef SHS_ENV_UNROLL
-#define SHS_ENV_UNROLL 2
+#define SHS_ENV_UNROLL 4
 #endif
 constexpr int kEnvUnroll = SHS_ENV_UNROLL;
+constexpr int kEnvWarps = kEnvBlock / 32;
 
+// Warp total of each of NV values, written to dst[0..NV) by the lanes that
+// hold them (halving exchanges over 32, then over the power-of-two rest).
+template <int NV>
+__device__ __forceinline__ void warp_totals(const float* vals, float* dst, int lane) {
+#pragma unroll
+    for (int base = 0; base < NV; base += 32) {
+        constexpr int R = NV % 32 == 0 ? 32 : NV % 32;
+        constexpr int RP = shs::pow2_at_least(R);
+        if (NV - base >= 32) {
+            float v[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = vals[base + i];
+            shs::warp_transpose_sum<32>(v, lane);
+            dst[base + lane] = v[0];
+        } else {
+            float v[RP];
+#pragma unroll
+            for (int i = 0; i < RP; ++i) v[i] = i < R ? vals[base + i] : 0.f;
+            shs::warp_transpose_sum<RP>(v, lane);
+            constexpr int sh = 5 - shs::log2c(RP);
+            const int idx = lane >> sh;
+            if ((lane & ((1 << sh) - 1)) == 0 && idx < R) dst[base + idx] = v[0];
+        }
+    }
+}
+
+// One warp per map row: the lanes stream the row (4 pixels per lane and
+// step, kEnvUnroll steps of loads in flight), the warp sums the row's
+// moments and each lane adds them, weighted by the row's Legendre factors,
+// into the coefficients it owns (e = lane + 32 j).  No block-wide barrier
+// per row; the block's warps meet once, at the end, to write the block's
+// partial row in a fixed order.
 template <int NB>
 __global__ void __launch_bounds__(kEnvBlock, SHS_ENV_MINB) envmap_rows_kernel(const __grid_constant__ EnvArgs a) {
-    constexpr int K = NB * NB, NF = 2 * NB - 1, NV = 3 * NF, NOWN = (3 * K + kEnvBlock - 1) / kEnvBlock;
-    __shared__ float s_red[kEnvBlock / 32][NV];
-    __shared__ float s_row[NV];
+    constexpr int K = NB * NB, NF = 2 * NB - 1, NV = 3 * NF, NOWN = (3 * K + 31) / 32;
+    __shared__ float s_mom[kEnvWarps][NV];
+    __shared__ float s_coef[kEnvWarps][3 * K];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // thread t owns coefficients e = t + j kEnvBlock < 3K (channel e / K, index e % K)
     float coef[NOWN];
 #pragma unroll
     for (int j = 0; j < NOWN; ++j) coef[j] = 0.f;
     const bool vec = a.vec4 != 0;
+    const int nwarps = gridDim.x * kEnvWarps;
 
-    for (int r = blockIdx.x; r < a.H; r += gridDim.x) {
+    for (int r = blockIdx.x * kEnvWarps + warp; r < a.H; r += nwarps) {
         // moments: acc = channel sums (m = 0), acc2[3 (m-1) + ch] = (cos, sin) moments
         float acc[3] = {0.f, 0.f, 0.f};
         float2 acc2[NB > 1 ? 3 * (NB - 1) : 1];
 #pragma unroll
         for (int v = 0; v < (NB > 1 ? 3 * (NB - 1) : 1); ++v) acc2[v] = make_float2(0.f, 0.f);
         const float* row = a.env + static_cast<size_t>(r) * a.W * 3;
-        if (vec) {
-            // 4 pixels (3 float4 of the map, 2 float4 of the azimuth table) per
-            // thread and step, two steps in flight
+        if (a.sym) {
+            // per lane and step: the 4-column group g of the first quarter of
+            // the row and its three mirror groups (3 float4 of the map each)
+            const float4* row4 = reinterpret_cast<const float4*>(row);
+            const float4* trig4 = reinterpret_cast<const float4*>(a.trig);
+            const int q4 = a.W >> 4, w8 = a.W >> 3, w4 = a.W >> 2;
+            for (int g = lane; g < q4; g += 32) {
+                float A[12], B[12], C[12], D[12];
+                const int gg[4] = {g, w8 - 1 - g, w8 + g, w4 - 1 - g};   // phi, pi - phi, pi + phi, -phi
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float4 qa = __ldcs(row4 + 3 * gg[0] + k), qb = __ldcs(row4 + 3 * gg[1] + k),
+                                 qc = __ldcs(row4 + 3 * gg[2] + k), qd = __ldcs(row4 + 3 * gg[3] + k);
+                    A[4 * k] = qa.x; A[4 * k + 1] = qa.y; A[4 * k + 2] = qa.z; A[4 * k + 3] = qa.w;
+                    B[4 * k] = qb.x; B[4 * k + 1] = qb.y; B[4 * k + 2] = qb.z; B[4 * k + 3] = qb.w;
+                    C[4 * k] = qc.x; C[4 * k + 1] = qc.y; C[4 * k + 2] = qc.z; C[4 * k + 3] = qc.w;
+                    D[4 * k] = qd.x; D[4 * k + 1] = qd.y; D[4 * k + 2] = qd.z; D[4 * k + 3] = qd.w;
+                }
+                const float4 t0 = __ldg(trig4 + 2 * g), t1 = __ldg(trig4 + 2 * g + 1);
+                const float tc[4] = {t0.x, t0.z, t1.x, t1.z}, ts[4] = {t0.y, t0.w, t1.y, t1.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)   // column 4g + j; its mirrors sit at 3 - j in B and D
+                    add_quad<NB>(&A[3 * j], &C[3 * j], &D[3 * (3 - j)], &B[3 * (3 - j)], tc[j], ts[j], acc, acc2);
+            }
+        } else if (vec) {
+            // 4 pixels (3 float4 of the map, 2 float4 of the azimuth table) per lane and step
             const float4* row4 = reinterpret_cast<const float4*>(row);
             const float4* trig4 = reinterpret_cast<const float4*>(a.trig);
             const int groups = a.W >> 2;
 #pragma unroll kEnvUnroll
-            for (int g = tid; g < groups; g += kEnvBlock) {
+            for (int g = lane; g < groups; g += 32) {
                 const float4 q0 = __ldcs(row4 + 3 * g), q1 = __ldcs(row4 + 3 * g + 1), q2 = __ldcs(row4 + 3 * g + 2);
                 const float4 t0 = __ldg(trig4 + 2 * g), t1 = __ldg(trig4 + 2 * g + 1);
                 add_pixel<NB>(q0.x, q0.y, q0.z, t0.x, t0.y, acc, acc2);
@@ -133,7 +232,7 @@ __global__ void __launch_bounds__(kEnvBlock, SHS_ENV_MINB) envmap_rows_kernel(co
             }
         } else {
 #pragma unroll 4
-            for (int col = tid; col < a.W; col += kEnvBlock) {
+            for (int col = lane; col < a.W; col += 32) {
                 const float2 t = __ldg(a.trig + col);
                 add_pixel<NB>(__ldcs(row + 3 * col), __ldcs(row + 3 * col + 1), __ldcs(row + 3 * col + 2), t.x, t.y,
                               acc, acc2);
@@ -150,42 +249,36 @@ __global__ void __launch_bounds__(kEnvBlock, SHS_ENV_MINB) envmap_rows_kernel(co
                 mom[ch * NF + 2 * mm] = acc2[3 * (mm - 1) + ch].y;
             }
         }
-        float* acc_all = mom;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc_all[v] = warp_sum(acc_all[v]);
-        if (lane == 0) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) s_red[warp][v] = acc_all[v];
-        }
-        __syncthreads();
-        if (tid < NV) {
-            float t = 0.f;
-#pragma unroll
-            for (int w = 0; w < kEnvBlock / 32; ++w) t += s_red[w][tid];
-            s_row[tid] = t;
-        }
-        __syncthreads();
+        warp_totals<NV>(mom, s_mom[warp], lane);
+        __syncwarp();
         float st, ct;
         sincospif((r + 0.5f) / a.H, &st, &ct);
         const float w_row = a.domega_scale * st;
 #pragma unroll
         for (int j = 0; j < NOWN; ++j) {
-            const int e = tid + j * kEnvBlock;
+            const int e = lane + 32 * j;
             if (e < 3 * K) {
                 const int ch = e / K, idx = e % K;
                 int l = 0;
                 while ((l + 1) * (l + 1) <= idx) ++l;
                 const int m = idx - l * l - l, am = m < 0 ? -m : m;
                 const int f = m == 0 ? 0 : (m > 0 ? 2 * m - 1 : 2 * am);   // moment index of T_m
-                coef[j] = fmaf(w_row * a.norm[idx] * assoc_legendre(l, am, ct, st), s_row[ch * NF + f], coef[j]);
+                coef[j] = fmaf(w_row * a.norm[idx] * assoc_legendre(l, am, ct, st), s_mom[warp][ch * NF + f], coef[j]);
             }
         }
-        __syncthreads();   // s_red / s_row are rewritten by the next row
+        __syncwarp();   // s_mom[warp] is rewritten by the warp's next row
     }
 #pragma unroll
     for (int j = 0; j < NOWN; ++j) {
-        const int e = tid + j * kEnvBlock;
-        if (e < 3 * K) a.partials[static_cast<size_t>(blockIdx.x) * (3 * K) + e] = coef[j];
+        const int e = lane + 32 * j;
+        if (e < 3 * K) s_coef[warp][e] = coef[j];
+    }
+    __syncthreads();
+    for (int e = tid; e < 3 * K; e += kEnvBlock) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < kEnvWarps; ++w) t += s_coef[w][e];
+        a.partials[static_cast<size_t>(blockIdx.x) * (3 * K) + e] = t;
     }
 }
 
@@ -218,11 +311,25 @@ __global__ void __launch_bounds__(32 * kEnvReduceWarps) envmap_reduce_kernel(con
     light[e] = t;
 }
 
+// Rows are spread evenly over one wave of warps: R = ceil(H / resident
+// warps) rows each, ceil(H / R) warps, at most max_grid blocks (the partial
+// rows the workspace holds).
 template <int NB>
-cudaError_t launch_env(EnvArgs& a, int grid, float* light, cudaStream_t s) {
+cudaError_t launch_env(EnvArgs& a, int max_grid, float* light, cudaStream_t s) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e0 == cudaSuccess)
+        e0 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, envmap_rows_kernel<NB>, kEnvBlock, 0);
+    if (e0 != cudaSuccess) return e0;
+    const long long cap = static_cast<long long>(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1) * kEnvWarps;
+    const long long rows_per_warp = (a.H + cap - 1) / cap;
+    const long long warps = (a.H + rows_per_warp - 1) / rows_per_warp;
+    long long g = (warps + kEnvWarps - 1) / kEnvWarps;
+    const int grid = static_cast<int>(g < max_grid ? g : max_grid);
     envmap_trig_kernel<<<(a.W + 255) / 256, 256, 0, s>>>(a.W, const_cast<float2*>(a.trig));
     shs::count_launch();
-    cudaError_t e0 = cudaGetLastError();
+    e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
     envmap_rows_kernel<NB><<<grid, kEnvBlock, 0, s>>>(a);
     shs::count_launch();
@@ -285,6 +392,7 @@ extern "C" shs_status shs_project_envmap(const float* env, int32_t height, int32
     a.partials = reinterpret_cast<float*>(static_cast<unsigned char*>(workspace) + trig_bytes(width));
     // rows of 4k pixels are 48k bytes, so an aligned map keeps every row aligned
     a.vec4 = (width % 4 == 0 && (reinterpret_cast<uintptr_t>(env) & 15u) == 0) ? 1 : 0;
+    a.sym = (a.vec4 && width % 16 == 0) ? 1 : 0;
     const int grid = env_grid(height);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;

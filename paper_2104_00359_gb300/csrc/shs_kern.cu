@@ -1166,6 +1166,7 @@ __global__ void __launch_bounds__(kBlock) bwd_pairs_t_kernel(BwdArgs a) {
         }
         __syncthreads();
         for (int j0 = 0; j0 < N; j0 += kBlock) {
+            if (j0 + (warp << 5) >= N) continue;   // no sphere for this warp in this round
             const int j = j0 + tid;
             const bool has = j < N;
             const float4 sp = has ? s_sph[j] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1222,7 +1223,6 @@ __global__ void __launch_bounds__(kBlock) bwd_pairs_t_kernel(BwdArgs a) {
             }
         }
     }
-    (void)warp;
     __syncthreads();
     // sphere entries of the block's partial row (the tail pass wrote the others)
     const int E = 3 * K + 1 + 4 * N;
