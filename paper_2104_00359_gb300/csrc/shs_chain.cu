@@ -36,6 +36,13 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Sum over lanes 0 .. V-1 (the others hold zeros): log2 of the next power of
+// two >= V exchange rounds, then lane 0's total is broadcast.
+__device__ __forceinline__ float view_sum(float v, int rounds) {
+    for (int o = 1, r = 0; r < rounds; o <<= 1, ++r) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
 // R(w) = I + A K + B K^2, K = [w]x, A = sin th / th, B = (1 - cos th) / th^2
 // written as 2 sin^2(th/2) / th^2 (no cancellation at small th); series below
 // th = 1e-3.
@@ -70,7 +77,7 @@ __device__ __forceinline__ void rotation(const float* pose, float* R) {
 // Rows per warp and step: all of their basis loads are issued before any is
 // used, so a warp keeps RW * 3 * PL independent loads in flight.
 #ifndef SHS_CHAIN_ROWS
-#define SHS_CHAIN_ROWS 4
+#define SHS_CHAIN_ROWS 2
 #endif
 #ifdef SHS_CHAIN_MINB
 #define SHS_CHAIN_BOUNDS __launch_bounds__(kChainThreads, SHS_CHAIN_MINB)
@@ -101,21 +108,27 @@ __global__ void SHS_CHAIN_BOUNDS chain_forward_kernel(const float* base, const f
 #pragma unroll
     for (int i = 0; i < 12; ++i) R[i] = lane < V ? s_rt[lane][i] : 0.f;
     const int64_t step = static_cast<int64_t>(gridDim.x) * kChainWarps * RW;
-    for (int64_t m0 = (static_cast<int64_t>(blockIdx.x) * kChainWarps + (threadIdx.x >> 5)) * RW; m0 < M;
-         m0 += step) {
-        float b[RW][3][PL];
+    // the next step's rows are loaded while this step's are reduced
+    auto load = [&](float (*bb)[3][PL], int64_t mb) {
 #pragma unroll
         for (int r = 0; r < RW; ++r) {
-            const int64_t m = m0 + r;
+            const int64_t m = mb + r;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
 #pragma unroll
                 for (int j = 0; j < PL; ++j) {
                     const int d = lane + 32 * j;
-                    b[r][c][j] = (m < M && d < D) ? __ldcs(basis + (m * 3 + c) * D + d) : 0.f;
+                    bb[r][c][j] = (m < M && d < D) ? __ldcs(basis + (m * 3 + c) * D + d) : 0.f;
                 }
             }
         }
+    };
+    int64_t m0 = (static_cast<int64_t>(blockIdx.x) * kChainWarps + (threadIdx.x >> 5)) * RW;
+    float b[RW][3][PL];
+    load(b, m0);
+    for (; m0 < M; m0 += step) {
+        float bn[RW][3][PL];
+        load(bn, m0 + step);
         float acc[RW][3];
 #pragma unroll
         for (int r = 0; r < RW; ++r) {
@@ -145,6 +158,12 @@ __global__ void SHS_CHAIN_BOUNDS chain_forward_kernel(const float* base, const f
                 xo[2] = fmaf(R[6], a0, fmaf(R[7], a1, fmaf(R[8], a2, R[11])));
             }
         }
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int j = 0; j < PL; ++j) b[r][c][j] = bn[r][c][j];
     }
 }
 
@@ -166,6 +185,8 @@ __global__ void SHS_CHAIN_BOUNDS chain_backward_kernel(const float* base, const 
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool view = lane < V;
+    int vrounds = 0;
+    while ((1 << vrounds) < V) ++vrounds;
     float R[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) R[i] = view ? s_r[lane][i] : 0.f;
@@ -176,27 +197,34 @@ __global__ void SHS_CHAIN_BOUNDS chain_backward_kernel(const float* base, const 
 #pragma unroll
     for (int i = 0; i < kChainExtra; ++i) ex[i] = 0.f;
     const int64_t step = static_cast<int64_t>(gridDim.x) * kChainWarps * RW;
-    for (int64_t m0 = (static_cast<int64_t>(blockIdx.x) * kChainWarps + warp) * RW; m0 < M; m0 += step) {
-        float b[RW][3][PL], gg[RW][3];
+    // the next step's rows are loaded while this step's are reduced
+    auto load = [&](float (*bb)[3][PL], float (*gb)[3], int64_t mb) {
 #pragma unroll
         for (int r = 0; r < RW; ++r) {
-            const int64_t m = m0 + r;
+            const int64_t m = mb + r;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                gg[r][c] = (m < M && view) ? __ldg(g + (static_cast<int64_t>(lane) * M + m) * 3 + c) : 0.f;
+                gb[r][c] = (m < M && view) ? __ldg(g + (static_cast<int64_t>(lane) * M + m) * 3 + c) : 0.f;
 #pragma unroll
                 for (int j = 0; j < PL; ++j) {
                     const int d = lane + 32 * j;
-                    b[r][c][j] = (m < M && d < D) ? __ldcs(basis + (m * 3 + c) * D + d) : 0.f;
+                    bb[r][c][j] = (m < M && d < D) ? __ldcs(basis + (m * 3 + c) * D + d) : 0.f;
                 }
             }
         }
+    };
+    int64_t m0 = (static_cast<int64_t>(blockIdx.x) * kChainWarps + warp) * RW;
+    float b[RW][3][PL], gg[RW][3];
+    load(b, gg, m0);
+    for (; m0 < M; m0 += step) {
+        float bn[RW][3][PL], gn[RW][3];
+        load(bn, gn, m0 + step);
 #pragma unroll
         for (int r = 0; r < RW; ++r) {
             // sum over views of R_v^T g_v: the gradient in the rest frame
-            const float r0 = warp_sum(fmaf(R[0], gg[r][0], fmaf(R[3], gg[r][1], R[6] * gg[r][2])));
-            const float r1 = warp_sum(fmaf(R[1], gg[r][0], fmaf(R[4], gg[r][1], R[7] * gg[r][2])));
-            const float r2 = warp_sum(fmaf(R[2], gg[r][0], fmaf(R[5], gg[r][1], R[8] * gg[r][2])));
+            const float r0 = view_sum(fmaf(R[0], gg[r][0], fmaf(R[3], gg[r][1], R[6] * gg[r][2])), vrounds);
+            const float r1 = view_sum(fmaf(R[1], gg[r][0], fmaf(R[4], gg[r][1], R[7] * gg[r][2])), vrounds);
+            const float r2 = view_sum(fmaf(R[2], gg[r][0], fmaf(R[5], gg[r][1], R[8] * gg[r][2])), vrounds);
             float xr[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -219,6 +247,14 @@ __global__ void SHS_CHAIN_BOUNDS chain_backward_kernel(const float* base, const 
                 }
             }
         }
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                gg[r][c] = gn[r][c];
+#pragma unroll
+                for (int j = 0; j < PL; ++j) b[r][c][j] = bn[r][c][j];
+            }
     }
 #pragma unroll
     for (int j = 0; j < PL; ++j) s_dp[warp][lane + 32 * j] = dp[j];
@@ -240,63 +276,108 @@ __global__ void SHS_CHAIN_BOUNDS chain_backward_kernel(const float* base, const 
     }
 }
 
-// Fixed-order sum of the blocks' partial rows; thread v then maps view v's
-// dL/dR to dL/dw_v in double precision:
+// Fixed-order sum of the blocks' partial rows, spread over SMs (one SM
+// alone keeps too few loads in flight): block k < ceil(D / 32) sums entries
+// 32 k .. 32 k + 31 of dL/dp, block ceil(D / 32) + v the 12 entries of view v
+// and then maps its dL/dR to dL/dw_v.  In a block, lane l takes one entry
+// and warp w the rows b = w mod 32, in eight independent running sums (their
+// loads in flight together); warp 0 adds the warps' sums in order.  Thread a
+// < 3 of a view block maps dL/dR to dL/dw_v,a:
 // dR/dw_a = A K_a + B (K_a K + K K_a) + (A'/th) w_a K + (B'/th) w_a K^2.
-__global__ void __launch_bounds__(kChainThreads) chain_reduce_kernel(const float* partials, int nblk, int D, int V,
-                                                                     const float* poses, float* d_p, float* d_poses) {
-    __shared__ float s_ex[kChainMaxViews * kChainExtra];
+constexpr int kChainReduceThreads = 1024;
+__global__ void __launch_bounds__(kChainReduceThreads) chain_reduce_kernel(const float* partials, int nblk, int D,
+                                                                           int V, const float* poses, float* d_p,
+                                                                           float* d_poses) {
+    constexpr int NW = kChainReduceThreads / 32;
+    __shared__ float s_ex[kChainExtra];
+    __shared__ float s_red[NW][33];
     const int E = D + kChainExtra * V;
-    for (int i = threadIdx.x; i < E; i += kChainThreads) {
-        float t = 0.f;
-        for (int b = 0; b < nblk; ++b) t += partials[static_cast<int64_t>(b) * E + i];
-        if (i < D) d_p[i] = t;
-        else s_ex[i - D] = t;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ndp = (D + 31) / 32;
+    const bool dp_block = static_cast<int>(blockIdx.x) < ndp;
+    const int vb = blockIdx.x - ndp;                      // view of a view block
+    const int i = dp_block ? blockIdx.x * 32 + lane : D + kChainExtra * vb + lane;
+    const bool mine = dp_block ? i < D : lane < kChainExtra;
+    float t[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (mine) {
+        for (int b = warp; b < nblk; b += 8 * NW) {
+            // unconditional (clamped) loads: all eight are issued before any add
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int bu = b + u * NW < nblk ? b + u * NW : nblk - 1;
+                v[u] = partials[static_cast<int64_t>(bu) * E + i];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t[u] += b + u * NW < nblk ? v[u] : 0.f;
+        }
     }
+    s_red[warp][lane] = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
     __syncthreads();
-    const int v = threadIdx.x;
-    if (v >= V) return;
-    const float* ex = s_ex + kChainExtra * v;
+    if (warp == 0 && mine) {
+        float u = 0.f;
+#pragma unroll 8
+        for (int w = 0; w < NW; ++w) u += s_red[w][lane];
+        if (dp_block) d_p[i] = u;
+        else s_ex[lane] = u;
+    }
+    if (dp_block) return;
+    __syncthreads();
+    // one thread per rotation-vector component
+    const int v = vb, a = threadIdx.x;
+    if (a >= 3) return;
+    const float* ex = s_ex;
     const float* pose = poses + 6 * v;
     float* d_pose = d_poses + 6 * v;
-    const double w[3] = {pose[0], pose[1], pose[2]};
-    const double t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-    double A, B, dA, dB;
-    if (t2 < 1e-6) {
-        A = 1.0 - t2 / 6.0 + t2 * t2 / 120.0;
-        B = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
-        dA = -1.0 / 3.0 + t2 / 30.0;
-        dB = -1.0 / 12.0 + t2 / 180.0;
+    // float32 throughout (this part's FP64 latency dominated the reduction):
+    // below theta = 0.2 the four factors come from their series (the closed
+    // forms cancel there), above from sincos with the half-angle form of
+    // 1 - cos.
+    const float w[3] = {pose[0], pose[1], pose[2]};
+    const float t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    float A, B, dA, dB;
+    if (t2 < 0.04f) {
+        A = 1.f - t2 * (1.f / 6.f) * (1.f - t2 * (1.f / 20.f) * (1.f - t2 * (1.f / 42.f)));
+        B = 0.5f - t2 * (1.f / 24.f) * (1.f - t2 * (1.f / 30.f) * (1.f - t2 * (1.f / 56.f)));
+        dA = -1.f / 3.f + t2 * (1.f / 30.f) * (1.f - t2 * (1.f / 28.f));
+        dB = -1.f / 12.f + t2 * (1.f / 180.f) * (1.f - t2 * (3.f / 112.f));
     } else {
-        const double th = sqrt(t2);
-        double s, c;
-        sincos(th, &s, &c);
+        const float th = sqrtf(t2);
+        float s, c, sh, ch;
+        sincosf(th, &s, &c);
+        sincosf(0.5f * th, &sh, &ch);
+        const float omc = 2.f * sh * sh;                   // 1 - cos theta
         A = s / th;
-        B = (1.0 - c) / t2;
+        B = omc / t2;
         dA = (th * c - s) / (t2 * th);
-        dB = (th * s - 2.0 * (1.0 - c)) / (t2 * t2);
+        dB = (th * s - 2.f * omc) / (t2 * t2);
     }
-    const double K[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
-    double K2[9];
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) K2[3 * r + c] = w[r] * w[c] - (r == c ? t2 : 0.0);
-    for (int a = 0; a < 3; ++a) {
-        double Ka[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        // [e_a]x
-        if (a == 0) { Ka[5] = -1.0; Ka[7] = 1.0; }
-        if (a == 1) { Ka[2] = 1.0; Ka[6] = -1.0; }
-        if (a == 2) { Ka[1] = -1.0; Ka[3] = 1.0; }
-        double acc = 0.0;
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) {
-                double kk = 0.0;
-                for (int q = 0; q < 3; ++q) kk += Ka[3 * r + q] * K[3 * q + c] + K[3 * r + q] * Ka[3 * q + c];
-                const double G = A * Ka[3 * r + c] + B * kk + dA * w[a] * K[3 * r + c] + dB * w[a] * K2[3 * r + c];
-                acc += G * ex[3 * r + c];
-            }
-        d_pose[a] = static_cast<float>(acc);
+    // With K = [w]x, K_a = [e_a]x and X = dL/dR (row-major ex[0..8]):
+    //   sum K_a o X = X[a2][a1] - X[a1][a2]            (a1, a2 = a + 1, a + 2 mod 3)
+    //   K_a K + K K_a = w e_a^T + e_a w^T - 2 w_a I,  so sum (.) o X = (X^T w)_a + (X w)_a - 2 w_a tr X
+    //   sum K o X = w . (X[2][1] - X[1][2], X[0][2] - X[2][0], X[1][0] - X[0][1])
+    //   sum K^2 o X = w^T X w - t2 tr X
+    float X[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) X[e] = ex[e];
+    const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+    const float tr = X[0] + X[4] + X[8];
+    const float wa = a == 0 ? w[0] : a == 1 ? w[1] : w[2];
+    float xw_a = 0.f, xtw_a = 0.f, wxw = 0.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        xw_a = fmaf(ex[3 * a + q], w[q], xw_a);
+        xtw_a = fmaf(ex[3 * q + a], w[q], xtw_a);
+        float row = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) row = fmaf(X[3 * q + c], w[c], row);
+        wxw = fmaf(w[q], row, wxw);
     }
-    for (int a = 0; a < 3; ++a) d_pose[3 + a] = ex[9 + a];
+    const float sk = ex[3 * a2 + a1] - ex[3 * a1 + a2];
+    const float kx = w[0] * (X[7] - X[5]) + w[1] * (X[2] - X[6]) + w[2] * (X[3] - X[1]);
+    const float acc = A * sk + B * (xtw_a + xw_a - 2.f * wa * tr) + dA * wa * kx + dB * wa * (wxw - t2 * tr);
+    d_pose[a] = acc;
+    d_pose[3 + a] = ex[9 + a];
 }
 
 int chain_grid(int64_t M) {
@@ -412,7 +493,8 @@ shs_status backward_views(const float* base, const float* basis, int64_t n_rows,
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return static_cast<shs_status>(shs::report_cuda(e, "chain backward"));
     }
-    chain_reduce_kernel<<<1, kChainThreads, 0, s>>>(partials, nblk, n_params, n_views, poses, d_p, d_poses);
+    chain_reduce_kernel<<<(n_params + 31) / 32 + n_views, kChainReduceThreads, 0, s>>>(partials, nblk, n_params,
+                                                                                        n_views, poses, d_p, d_poses);
     shs::count_launch();
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SHS_OK : static_cast<shs_status>(shs::report_cuda(e, "chain reduce"));
