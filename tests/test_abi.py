@@ -141,7 +141,7 @@ def test_chain_argument_checks_without_gpu(lib):
     assert lib.shs_chain_workspace_bytes(10, 0) == 0
     assert lib.shs_chain_workspace_bytes(10, 257) == 0
     assert lib.shs_chain_workspace_bytes(0, 60) == 4 * (60 + 12)           # one partial row
-    assert lib.shs_chain_workspace_bytes(1000, 60) == 4 * 32 * (60 + 12)    # 32 blocks of 8 warps x 4 rows
+    assert lib.shs_chain_workspace_bytes(1000, 60) == 4 * 63 * (60 + 12)    # 63 blocks of 8 warps x 2 rows
     assert lib.shs_chain_workspace_bytes(50000, 60) == 4 * 608 * (60 + 12)  # capped at 608 partial rows
     assert lib.shs_chain_workspace_bytes(10 ** 7, 60) == 4 * 608 * (60 + 12)
     one = ctypes.c_void_p(16)
