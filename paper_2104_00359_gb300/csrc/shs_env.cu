@@ -35,7 +35,8 @@ struct EnvArgs {
     float norm[64];          // N'_lm by linear index
     float* partials;         // [gridDim.x][3K]
     int vec4;                // 16-byte aligned map and width % 4 == 0: rows read as float4
-    int sym;                 // ... and width % 16 == 0: the four-fold azimuthal symmetry path
+    int sym;                 // ... and width % 16 == 0: the four-fold symmetry path (reads the
+                             // azimuth table's first W / 4 columns only)
 };
 
 // P_l^m(x) without the Condon-Shortley phase, s = sqrt(1 - x^2) >= 0:
@@ -282,27 +283,40 @@ __global__ void __launch_bounds__(kEnvBlock, SHS_ENV_MINB) envmap_rows_kernel(co
     }
 }
 
-// (cos, sin) of each column's centre azimuth (c + 1/2) 2 pi / W, evaluated in
-// double precision and rounded once.
-__global__ void envmap_trig_kernel(int W, float2* trig) {
+// (cos, sin) of the centre azimuth (c + 1/2) 2 pi / W of columns c < n,
+// evaluated in double precision and rounded once; small blocks spread the
+// (slow, latency-bound) double-precision work over many SMs.
+constexpr int kEnvTrigBlock = 64;
+__global__ void __launch_bounds__(kEnvTrigBlock) envmap_trig_kernel(int W, int n, float2* trig) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= W) return;
+    if (c >= n) return;
     double s, co;
     sincospi((2.0 * c + 1.0) / W, &s, &co);
     trig[c] = make_float2(static_cast<float>(co), static_cast<float>(s));
 }
 
 // light[e] = sum over the nblk partial rows in a fixed order; one block per
-// 32 entries, 32 warps striding over the rows.
+// 32 entries, 32 warps striding over the rows, eight rows in flight each.
 __global__ void __launch_bounds__(32 * kEnvReduceWarps) envmap_reduce_kernel(const float* partials, int nblk, int E,
                                                                          float* light) {
     __shared__ float s[kEnvReduceWarps][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int e = blockIdx.x * 32 + lane;
-    float v = 0.f;
-    if (e < E)
-        for (int b = warp; b < nblk; b += kEnvReduceWarps) v += partials[static_cast<size_t>(b) * E + e];
-    s[warp][lane] = v;
+    float t8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (e < E) {
+        for (int b = warp; b < nblk; b += 8 * kEnvReduceWarps) {
+            // unconditional (clamped) loads: all eight are issued before any add
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int bu = b + u * kEnvReduceWarps < nblk ? b + u * kEnvReduceWarps : nblk - 1;
+                v[u] = partials[static_cast<size_t>(bu) * E + e];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t8[u] += b + u * kEnvReduceWarps < nblk ? v[u] : 0.f;
+        }
+    }
+    s[warp][lane] = ((t8[0] + t8[1]) + (t8[2] + t8[3])) + ((t8[4] + t8[5]) + (t8[6] + t8[7]));
     __syncthreads();
     if (warp != 0 || e >= E) return;
     float t = 0.f;
@@ -327,7 +341,9 @@ cudaError_t launch_env(EnvArgs& a, int max_grid, float* light, cudaStream_t s) {
     const long long warps = (a.H + rows_per_warp - 1) / rows_per_warp;
     long long g = (warps + kEnvWarps - 1) / kEnvWarps;
     const int grid = static_cast<int>(g < max_grid ? g : max_grid);
-    envmap_trig_kernel<<<(a.W + 255) / 256, 256, 0, s>>>(a.W, const_cast<float2*>(a.trig));
+    const int ntrig = a.sym ? a.W >> 2 : a.W;   // the symmetry path reads the first quarter
+    envmap_trig_kernel<<<(ntrig + kEnvTrigBlock - 1) / kEnvTrigBlock, kEnvTrigBlock, 0, s>>>(
+        a.W, ntrig, const_cast<float2*>(a.trig));
     shs::count_launch();
     e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;

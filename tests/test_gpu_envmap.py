@@ -55,7 +55,7 @@ def test_envmap_small_all_band_counts(n):
     _check(S.environment_map(seed=10 + n, height=48, width=96), n)
 
 
-@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (37, 50), (5, 129), (300, 2), (20, 36), (3, 16), (9, 80)])
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (37, 50), (5, 129), (300, 2), (20, 36), (3, 16), (9, 80), (2, 16400)])
 def test_envmap_ragged_and_degenerate_shapes(shape):
     """Widths that take each load path: scalar (odd), float4 rows (width a
     multiple of 4) and the four-fold symmetry path (a multiple of 16)."""
