@@ -142,6 +142,38 @@ __device__ __forceinline__ void add_quad(const float* v1, const float* v2, const
 constexpr int kEnvUnroll = SHS_ENV_UNROLL;
 constexpr int kEnvWarps = kEnvBlock / 32;
 
+// One exchange of the halving sum at lane distance O with CNT values left;
+// the recursion keeps every index a compile-time constant (the values stay
+// in registers).
+template <int CNT, int O>
+__device__ __forceinline__ void env_transpose_step(float* v, int lane) {
+    if constexpr (O > 0) {
+        if constexpr (CNT > 1) {
+            constexpr int half = CNT / 2;
+            const bool up = lane & O;
+#pragma unroll
+            for (int i = 0; i < half; ++i) {
+                const float send = up ? v[i] : v[i + half];
+                const float keep = up ? v[i + half] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+            }
+            env_transpose_step<half, O / 2>(v, lane);
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
+            env_transpose_step<1, O / 2>(v, lane);
+        }
+    }
+}
+
+// Halving-exchange sum of NV values (NV a power of two <= 32): afterwards v[0]
+// on lane l holds the warp total of value (l >> (5 - log2 NV)).  Unlike the
+// loop form shared by the shading kernels, every index here is a compile-time
+// constant, so the values stay in registers (this kernel has them to spare).
+template <int NV>
+__device__ __forceinline__ void env_transpose_sum(float* v, int lane) {
+    env_transpose_step<NV, 16>(v, lane);
+}
+
 // Warp total of each of NV values, written to dst[0..NV) by the lanes that
 // hold them (halving exchanges over 32, then over the power-of-two rest).
 template <int NV>
@@ -154,13 +186,13 @@ __device__ __forceinline__ void warp_totals(const float* vals, float* dst, int l
             float v[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = vals[base + i];
-            shs::warp_transpose_sum<32>(v, lane);
+            env_transpose_sum<32>(v, lane);
             dst[base + lane] = v[0];
         } else {
             float v[RP];
 #pragma unroll
             for (int i = 0; i < RP; ++i) v[i] = i < R ? vals[base + i] : 0.f;
-            shs::warp_transpose_sum<RP>(v, lane);
+            env_transpose_sum<RP>(v, lane);
             constexpr int sh = 5 - shs::log2c(RP);
             const int idx = lane >> sh;
             if ((lane & ((1 << sh) - 1)) == 0 && idx < R) dst[base + idx] = v[0];

@@ -12,34 +12,26 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// One exchange of the halving sum at lane distance O with CNT values left;
-// the recursion keeps every index a compile-time constant (the values stay
-// in registers).
-template <int CNT, int O>
-__device__ __forceinline__ void transpose_sum_step(float* v, int lane) {
-    if constexpr (O > 0) {
-        if constexpr (CNT > 1) {
-            constexpr int half = CNT / 2;
-            const bool up = lane & O;
-#pragma unroll
-            for (int i = 0; i < half; ++i) {
-                const float send = up ? v[i] : v[i + half];
-                const float keep = up ? v[i + half] : v[i];
-                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
-            }
-            transpose_sum_step<half, O / 2>(v, lane);
-        } else {
-            v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
-            transpose_sum_step<1, O / 2>(v, lane);
-        }
-    }
-}
-
 // Sum NV values (NV a power of two <= 32) over the warp by halving exchanges:
 // afterwards v[0] on lane l holds the warp total of value (l >> (5 - log2 NV)).
 template <int NV>
 __device__ __forceinline__ void warp_transpose_sum(float* v, int lane) {
-    transpose_sum_step<NV, 16>(v, lane);
+#pragma unroll
+    for (int o = 16, cnt = NV; o > 0; o >>= 1) {
+        if (cnt > 1) {
+            const int half = cnt / 2;
+            const bool up = lane & o;
+#pragma unroll
+            for (int i = 0; i < half; ++i) {
+                const float send = up ? v[i] : v[i + half];
+                const float keep = up ? v[i + half] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+            cnt = half;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        }
+    }
 }
 
 constexpr int log2c(int v) { return v <= 1 ? 0 : 1 + log2c(v / 2); }
