@@ -544,8 +544,8 @@ def bench_serving(args, world, rank, local):
     torch.cuda.set_device(local)
     rng = np.random.default_rng(4 + 1000 * rank)
     n_jobs, n_req = args.serve_jobs, args.serve_requests
-    srv = serve.Server(hbm_budget_bytes=80e9, n_slots=3, max_batch=32, chunk_points=args.serve_chunk,
-                       batch_work=args.serve_batch_work)
+    srv = serve.Server(hbm_budget_bytes=80e9, n_slots=args.serve_slots, max_batch=32, chunk_points=args.serve_chunk,
+                       batch_work=args.serve_batch_work, small_work=args.serve_small_work)
     for j in range(n_jobs):
         P = int(np.exp(rng.uniform(np.log(16384), np.log(1048576))))
         N = int(rng.integers(20, 501))
@@ -643,7 +643,8 @@ def bench_serving(args, world, rank, local):
                                     "20-500 spheres, n_bands 4 or 6, 70% fwd / 30% fwd+L2 bwd, Poisson arrivals "
                                     "at 80% of per-call capacity, 80 GB HBM budget",
                         "jobs": n_jobs, "requests": n_req, "rate_per_s": rate,
-                        "mean_per_call_service_ms": mean_service * 1e3, "slots": 3, "max_batch": 32},
+                        "mean_per_call_service_ms": mean_service * 1e3, "slots": args.serve_slots, "max_batch": 32,
+                        "small_work": srv.small_work},
                 latency_ms={"p50": sv["p50_ms"], "p99": sv["p99_ms"],
                             "under_100k_points": sv["under_100k_points"],
                             "100k_points_and_up": sv["100k_points_and_up"]},
@@ -1089,8 +1090,14 @@ def main():
     ap.add_argument("--serve-chunk", type=int, default=1 << 40,
                     help="serving: largest chunk of a request in one launch (points)")
     ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-slots", type=int, default=3, help="serving: batch slots (streams) in flight")
+    ap.add_argument("--serve-small-work", type=float, default=None,
+                    help="serving: tasks up to this estimated work fill a batch first (0: arrival order)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.serve_small_work is None:
+        from paper_2104_00359_gb300 import serve as _serve
+        args.serve_small_work = _serve.SMALL_WORK
     world, rank, local, dist = dist_init(args)
     if args.impl == "reference":
         res = bench_reference(args, world, rank)

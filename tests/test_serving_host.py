@@ -42,3 +42,25 @@ def test_budget_queue_order(monkeypatch):
     assert list(srv.jobs) == ["c", "d"]
     with pytest.raises(ValueError):
         srv.add_job("huge", [0] * 10 ** 7, [0], [0], ctr, [0], [0], cfg)
+
+
+def test_fill_order_small_tasks_first():
+    """With small_work set, a batch considers the pending tasks of estimated
+    work <= small_work first (in arrival order), then the rest (in arrival
+    order); with small_work = 0 it is arrival order alone."""
+    pytest.importorskip("torch")
+    from types import SimpleNamespace
+    from paper_2104_00359_gb300 import serve
+
+    def job(P, N, n):
+        return SimpleNamespace(P=P, N=N, config=SimpleNamespace(n_bands=n), ranges=[(0, P)])
+
+    srv = serve.Server.__new__(serve.Server)
+    srv.jobs = {"big": job(1_000_000, 400, 6), "small": job(20_000, 50, 4), "mid": job(200_000, 100, 4)}
+    reqs = [serve.Request(i, j, "fwd", 0.0) for i, j in enumerate(["big", "small", "mid", "small", "big"])]
+    srv.pending = serve.deque((r, None) for r in reqs)
+    srv.small_work = 0.0
+    assert list(srv._fill_order()) == [0, 1, 2, 3, 4]
+    srv.small_work = serve.task_work(100_000, 100, 4, "fwd")
+    assert list(srv._fill_order()) == [1, 3, 0, 2, 4]
+    assert serve.task_work(20_000, 50, 4, "fwdbwd") == 3.5 * serve.task_work(20_000, 50, 4, "fwd")
