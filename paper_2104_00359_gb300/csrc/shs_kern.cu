@@ -733,9 +733,20 @@ __device__ __forceinline__ void forward_point(const FwdArgs& a, const float4* s_
 #ifndef SHS_BWD_MINB
 #define SHS_BWD_MINB 3
 #endif
+// Minimum resident blocks above 4 bands.  From 7 bands four blocks per SM
+// (128 registers): the spills this costs are outweighed by the latency the
+// extra warps hide (height field, 8 bands: forward 5.65 -> 5.23 ms, backward
+// 18.1 -> 16.0 ms against one block's bound; 3, 5 and 6 blocks measured
+// slower).  5 and 6 bands keep the compiler's choice.
+#ifndef SHS_FWD_MINB_HI
+#define SHS_FWD_MINB_HI (SHS_NB >= 7 ? 4 : 1)
+#endif
+#ifndef SHS_BWD_MINB_HI
+#define SHS_BWD_MINB_HI (SHS_NB >= 7 ? 4 : 1)
+#endif
 
 template <int MODE>
-__global__ void __launch_bounds__(kBlock, NB <= 4 ? SHS_FWD_MINB : 1) forward_kernel_t(FwdArgs a) {
+__global__ void __launch_bounds__(kBlock, NB <= 4 ? SHS_FWD_MINB : SHS_FWD_MINB_HI) forward_kernel_t(FwdArgs a) {
     __shared__ __align__(16) float4 s_sph[kMaxSpheres];
     __shared__ __align__(16) float s_light[3 * KPAD];
     __shared__ __align__(8) uint64_t s_bar;
@@ -1050,7 +1061,7 @@ __device__ void finish_scene_sums(const BwdArgs& a, int E) {
 // Up to 4 bands: four resident blocks per SM (<= 128 registers per thread) for
 // the pair loop; above that the tail state needs the registers.
 template <bool PAIRS, int CULLM, int EXPM>
-__global__ void __launch_bounds__(kBlock, NB <= 4 ? SHS_BWD_MINB : 1) backward_kernel_t(BwdArgs a) {
+__global__ void __launch_bounds__(kBlock, NB <= 4 ? SHS_BWD_MINB : SHS_BWD_MINB_HI) backward_kernel_t(BwdArgs a) {
     extern __shared__ __align__(16) float4 dyn[];
     __shared__ __align__(16) float s_light[3 * KPAD];
     __shared__ __align__(8) uint64_t s_bar;
@@ -1118,7 +1129,17 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
-__global__ void __launch_bounds__(kBlock) bwd_pairs_t_kernel(BwdArgs a) {
+// From 7 bands the pair pass too runs four blocks per SM (8 bands: 8.8 ->
+// 7.3 ms at 1M points x 300 spheres).
+#if !defined(SHS_PAIRS_MINB) && SHS_NB >= 7
+#define SHS_PAIRS_MINB 4
+#endif
+#ifdef SHS_PAIRS_MINB
+#define SHS_PAIRS_BOUNDS __launch_bounds__(kBlock, SHS_PAIRS_MINB)
+#else
+#define SHS_PAIRS_BOUNDS __launch_bounds__(kBlock)
+#endif
+__global__ void SHS_PAIRS_BOUNDS bwd_pairs_t_kernel(BwdArgs a) {
     extern __shared__ __align__(16) float4 dyn[];
     __shared__ __align__(16) float s_light[3 * KPAD];
     __shared__ __align__(8) uint64_t s_bar;
@@ -1257,7 +1278,14 @@ __device__ __forceinline__ int find_request(const int64_t* tb, int n, int64_t ti
 // Forward for every tile of every request in the batch.  Blocks take tiles
 // from a device counter (consecutive tiles mostly share a request, so a
 // request's scene is staged once per run of its tiles).
-__global__ void __launch_bounds__(kBlock) forward_batch_kernel(const __grid_constant__ FwdBatch b) {
+// SHS_BATCH_MINB_HI: minimum resident blocks of both batch kernels above 4 bands.
+#ifdef SHS_BATCH_MINB_HI
+#define SHS_FBATCH_BOUNDS __launch_bounds__(kBlock, NB <= 4 ? 1 : SHS_BATCH_MINB_HI)
+#else
+#define SHS_BATCH_MINB_HI 1
+#define SHS_FBATCH_BOUNDS __launch_bounds__(kBlock)
+#endif
+__global__ void SHS_FBATCH_BOUNDS forward_batch_kernel(const __grid_constant__ FwdBatch b) {
     __shared__ __align__(16) float4 s_sph[kMaxSpheres];
     __shared__ __align__(16) float s_light[3 * KPAD];
     __shared__ __align__(8) uint64_t s_bar;
@@ -1289,7 +1317,7 @@ __global__ void __launch_bounds__(kBlock) forward_batch_kernel(const __grid_cons
 // L2 adjoint for every tile of every request in the batch.  Each tile's scene
 // sums go to its request's accumulator with atomics; the tile that completes a
 // request writes that request's outputs.
-__global__ void __launch_bounds__(kBlock, NB <= 4 ? 4 : 1)
+__global__ void __launch_bounds__(kBlock, NB <= 4 ? 4 : SHS_BATCH_MINB_HI)
     backward_batch_kernel(const __grid_constant__ BwdBatch b) {
     extern __shared__ __align__(16) float4 dyn[];
     __shared__ __align__(16) float s_light[3 * KPAD];
