@@ -301,7 +301,10 @@ shs_status shs_shade_batch(shs_batch_t batch, const shs_request* reqs, int32_t n
  * exact solid angle (cos t_r - cos t_{r+1}) 2 pi / width.  The sum runs in a
  * fixed order (same result on every run).  1 <= height, width <= 65536 and
  * 1 <= n_bands <= 8, else SHS_ERR_INVALID_ARG, as for NULL pointers or a
- * short workspace.  Asynchronous on `stream`. */
+ * short workspace.  Asynchronous on `stream`, except that the first call for
+ * a map width on a device builds that width's azimuth table in library-owned
+ * device memory (kept for later calls; up to 8 widths per device) and
+ * synchronises `stream` once to do so. */
 size_t shs_envmap_workspace_bytes(int32_t height, int32_t width, int32_t n_bands);
 shs_status shs_project_envmap(const float* env, int32_t height, int32_t width, int32_t n_bands, float* light,
                               void* workspace, size_t workspace_bytes, void* stream);

@@ -14,6 +14,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "shs.h"
@@ -37,6 +38,7 @@ struct EnvArgs {
     int vec4;                // 16-byte aligned map and width % 4 == 0: rows read as float4
     int sym;                 // ... and width % 16 == 0: the four-fold symmetry path (reads the
                              // azimuth table's first W / 4 columns only)
+    int trig_ready;          // host side: `trig` already holds the table (the per-width cache)
 };
 
 // P_l^m(x) without the Condon-Shortley phase, s = sqrt(1 - x^2) >= 0:
@@ -373,12 +375,14 @@ cudaError_t launch_env(EnvArgs& a, int max_grid, float* light, cudaStream_t s) {
     const long long warps = (a.H + rows_per_warp - 1) / rows_per_warp;
     long long g = (warps + kEnvWarps - 1) / kEnvWarps;
     const int grid = static_cast<int>(g < max_grid ? g : max_grid);
-    const int ntrig = a.sym ? a.W >> 2 : a.W;   // the symmetry path reads the first quarter
-    envmap_trig_kernel<<<(ntrig + kEnvTrigBlock - 1) / kEnvTrigBlock, kEnvTrigBlock, 0, s>>>(
-        a.W, ntrig, const_cast<float2*>(a.trig));
-    shs::count_launch();
-    e0 = cudaGetLastError();
-    if (e0 != cudaSuccess) return e0;
+    if (!a.trig_ready) {
+        const int ntrig = a.sym ? a.W >> 2 : a.W;   // the symmetry path reads the first quarter
+        envmap_trig_kernel<<<(ntrig + kEnvTrigBlock - 1) / kEnvTrigBlock, kEnvTrigBlock, 0, s>>>(
+            a.W, ntrig, const_cast<float2*>(a.trig));
+        shs::count_launch();
+        e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) return e0;
+    }
     envmap_rows_kernel<NB><<<grid, kEnvBlock, 0, s>>>(a);
     shs::count_launch();
     cudaError_t e = cudaGetLastError();
@@ -390,6 +394,49 @@ cudaError_t launch_env(EnvArgs& a, int max_grid, float* light, cudaStream_t s) {
 }
 
 int env_grid(int height) { return height < kEnvMaxBlocks ? height : kEnvMaxBlocks; }
+
+// Azimuth tables kept per device and map width (they depend on nothing
+// else), so repeated projections of same-width maps skip the table launch.
+// A table is built once, on the caller's stream, which is then synchronised
+// so that calls on any stream may read it; a full cache (kEnvTrigCache
+// widths per device) leaves further widths to the workspace.
+constexpr int kEnvTrigCache = 8;
+struct TrigEntry {
+    int width = 0;
+    float2* table = nullptr;
+};
+TrigEntry g_trig[64][kEnvTrigCache];
+std::mutex g_trig_mutex;
+
+const float2* cached_trig(int width, cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_trig_mutex);
+    for (auto& t : g_trig[dev])
+        if (t.table && t.width == width) return t.table;
+    for (auto& t : g_trig[dev]) {
+        if (t.table) continue;
+        float2* tab = nullptr;
+        if (cudaMalloc(&tab, sizeof(float2) * static_cast<size_t>(width)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        envmap_trig_kernel<<<(width + kEnvTrigBlock - 1) / kEnvTrigBlock, kEnvTrigBlock, 0, s>>>(width, width, tab);
+        shs::count_launch();
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(tab);
+            return nullptr;
+        }
+        t.width = width;
+        t.table = tab;
+        return tab;
+    }
+    return nullptr;
+}
 
 double factorial_ratio(int l, int m) {   // (l - m)! / (l + m)!
     double r = 1.0;
@@ -428,7 +475,10 @@ extern "C" shs_status shs_project_envmap(const float* env, int32_t height, int32
     a.env = env;
     a.H = height;
     a.W = width;
-    a.trig = static_cast<const float2*>(workspace);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const float2* cached = cached_trig(width, s);
+    a.trig = cached ? cached : static_cast<const float2*>(workspace);
+    a.trig_ready = cached ? 1 : 0;
     // cos theta_r - cos theta_{r+1} = 2 sin(theta_r) sin(pi / 2H)
     a.domega_scale = static_cast<float>(2.0 * std::sin(M_PI / (2.0 * height)) * 2.0 * M_PI / width);
     for (int l = 0; l < n_bands; ++l)
@@ -442,7 +492,6 @@ extern "C" shs_status shs_project_envmap(const float* env, int32_t height, int32
     a.vec4 = (width % 4 == 0 && (reinterpret_cast<uintptr_t>(env) & 15u) == 0) ? 1 : 0;
     a.sym = (a.vec4 && width % 16 == 0) ? 1 : 0;
     const int grid = env_grid(height);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
     switch (n_bands) {
         case 1: e = launch_env<1>(a, grid, light, s); break;
