@@ -9,10 +9,12 @@
 //
 // The basis is the only large operand (M * 3 * D floats), read once per pass:
 // one warp per row, lanes striding the D parameters, so each row's 3 D floats
-// are read as contiguous 128-byte segments.  The adjoint's sums over rows are
-// kept per lane / per warp, combined per block in a fixed order, and the
-// blocks' partial rows are added in a fixed order by a second kernel, which
-// also turns dL/dR into dL/dw.
+// are read as contiguous 128-byte segments; a warp takes two rows per step and
+// issues the next step's loads before reducing the current rows.  The
+// adjoint's sums over rows are kept per lane / per warp, combined per block in
+// a fixed order, and the blocks' partial rows are added in a fixed order by a
+// second kernel spread over SMs (one block per 32 parameters and per view),
+// which also turns dL/dR into dL/dw.
 
 #include <cmath>
 #include <cstdint>
